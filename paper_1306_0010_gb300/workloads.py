@@ -1,0 +1,343 @@
+"""Seeded synthetic inputs for the radiation subcycle (initial and frozen-gas states only).
+
+This module holds no step of the method: it only draws and shapes input fields.  Both the
+CUDA path (through the C-ABI binding) and the CPU oracle consume the plain dicts it returns:
+
+    case = {"name": str, "desc": {...grid and physics parameters...},
+            "fields": {"E", "Fx", "Fy", "Fz", "T", "rho", "vx", "vy", "vz", "kP", "kF", "j"},
+            "chat": float, "dt": float, "n_sub": int}
+
+Arrays are float64, C-ordered with shape (nz, ny, nx) (x fastest).  Absent optional fields are
+None (zero velocity, the opacity law k = kappa * rho^p, no emissivity).  Units: a_R = 1 and
+k_B/mu = 1 unless stated, so P = rho T and e = rho T / (gamma - 1).
+
+The workloads mirror the paper's radiation-subsystem tests (Section 4.1), its concentrated-source
+problem (abstract; Eq. radshell:sourceprofile) and its dusty-shell problem (Section 4.3.6); the
+paper uses no external datasets.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 13060010
+
+
+def rng(offset: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + offset))
+
+
+def base_desc(n, dx, bc="periodic", **kw):
+    d = {
+        "n": tuple(int(v) for v in n),
+        "dx": tuple(float(v) for v in dx),
+        "bc_lo": [bc] * 3 if isinstance(bc, str) else list(bc[0]),
+        "bc_hi": [bc] * 3 if isinstance(bc, str) else list(bc[1]),
+        "dirichlet_lo": [[0.0] * 4 for _ in range(3)],
+        "dirichlet_hi": [[0.0] * 4 for _ in range(3)],
+        "c": 1.0,
+        "a_rad": 1.0,
+        "gamma": 5.0 / 3.0,
+        "mu_over_kB": 1.0,
+        "theta_F": 1.0,
+        "theta_E": 1.0,
+        "E_floor": 1e-30,
+        "exchange": "equilibrium",
+        "beta_tau": False,
+        "limiter": "minmod",
+        "closure": "m1",
+        "speeds": "m1",
+        "kappa_P": 0.0,
+        "kappa_F": 0.0,
+        "kappa_rho_pow": 0,
+        "cfl": 0.4,
+        "precision": "fp64",
+    }
+    d.update(kw)
+    return d
+
+
+def cfl_dt(desc, chat, cfl=None):
+    cfl = desc.get("cfl", 0.4) if cfl is None else cfl
+    dxs = [desc["dx"][d] for d in range(3) if desc["n"][d] > 1]
+    return cfl * min(dxs) / chat if dxs else cfl / chat
+
+
+def _shape(desc):
+    nx, ny, nz = desc["n"]
+    return (nz, ny, nx)
+
+
+def cell_centres(desc, x0=(0.0, 0.0, 0.0)):
+    nx, ny, nz = desc["n"]
+    dx = desc["dx"]
+    x = x0[0] + (np.arange(nx) + 0.5) * dx[0]
+    y = x0[1] + (np.arange(ny) + 0.5) * dx[1]
+    z = x0[2] + (np.arange(nz) + 0.5) * dx[2]
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def random_directions(g: np.random.Generator, shape):
+    """Unit vectors uniform on the sphere."""
+    z = g.uniform(-1.0, 1.0, size=shape)
+    phi = g.uniform(0.0, 2.0 * math.pi, size=shape)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return r * np.cos(phi), r * np.sin(phi), z
+
+
+def random_state(desc, g: np.random.Generator, fmax=0.9, Emin=0.5, Emax=2.0, dims_active=None):
+    """Random realizable radiation state: E uniform in [Emin, Emax], F = c E f n with f uniform
+    in [0, fmax] and n uniform on the sphere (restricted to the active directions)."""
+    shp = _shape(desc)
+    E = g.uniform(Emin, Emax, size=shp)
+    f = g.uniform(0.0, fmax, size=shp)
+    nx, ny, nz = random_directions(g, shp)
+    act = [desc["n"][d] > 1 for d in range(3)] if dims_active is None else dims_active
+    comps = [nx, ny, nz]
+    for d in range(3):
+        if not act[d]:
+            comps[d] = np.zeros(shp)
+    norm = np.sqrt(comps[0] ** 2 + comps[1] ** 2 + comps[2] ** 2)
+    norm = np.where(norm > 0, norm, 1.0)
+    c = desc["c"]
+    return {
+        "E": E,
+        "Fx": c * E * f * comps[0] / norm,
+        "Fy": c * E * f * comps[1] / norm,
+        "Fz": c * E * f * comps[2] / norm,
+    }
+
+
+# ----------------------------------------------------------------------------- small parity cases
+
+def parity_case(name, n, bc="periodic", exchange="equilibrium", limiter="minmod", beta_tau=False,
+                closure="m1", speeds="m1", kappa=1.0, kappa_rho_pow=1, theta=1.0, chat=1.0, c=10.0,
+                n_sub=3, seed=0, with_j=False, with_v=None, fmax=0.9, dirichlet=None,
+                precision="fp64", kP_array=False, dx=None):
+    """Random realizable radiation state on a small grid with a random frozen gas state."""
+    g = rng(1000 + seed)
+    n = tuple(n)
+    if dx is None:
+        dx = tuple(1.0 / max(v, 1) for v in n)
+    desc = base_desc(n, dx, bc=bc, c=c, exchange=exchange, limiter=limiter, beta_tau=beta_tau,
+                     closure=closure, speeds=speeds, kappa_P=kappa, kappa_F=kappa,
+                     kappa_rho_pow=kappa_rho_pow, theta_F=theta, theta_E=theta, E_floor=1e-12,
+                     precision=precision)
+    if dirichlet is not None:
+        desc["dirichlet_lo"], desc["dirichlet_hi"] = dirichlet
+    shp = _shape(desc)
+    st = random_state(desc, g, fmax=fmax)
+    rho = np.exp(g.normal(0.0, 0.5, size=shp))
+    T = np.exp(g.normal(0.0, 0.2, size=shp))
+    if exchange == "full":
+        # start near radiative equilibrium so the coupled problem is not violently stiff
+        st["E"] = desc["a_rad"] * T ** 4 * g.uniform(0.7, 1.3, size=shp)
+        f = g.uniform(0.0, fmax, size=shp)
+        nx_, ny_, nz_ = random_directions(g, shp)
+        act = [n[d] > 1 for d in range(3)]
+        comps = [nx_ if act[0] else 0 * nx_, ny_ if act[1] else 0 * ny_, nz_ if act[2] else 0 * nz_]
+        norm = np.sqrt(sum(cc ** 2 for cc in comps))
+        norm = np.where(norm > 0, norm, 1.0)
+        for d, k in enumerate(("Fx", "Fy", "Fz")):
+            st[k] = c * st["E"] * f * comps[d] / norm
+    v = with_v if with_v is not None else beta_tau
+    fields = dict(st)
+    fields["T"] = T
+    fields["rho"] = rho
+    if v:
+        for k in ("vx", "vy", "vz"):
+            fields[k] = g.normal(0.0, 0.05 * c, size=shp)
+    else:
+        fields["vx"] = fields["vy"] = fields["vz"] = None
+    fields["kP"] = fields["kF"] = None
+    if kP_array:
+        fields["kP"] = kappa * rho * g.uniform(0.5, 1.5, size=shp)
+        fields["kF"] = kappa * rho * g.uniform(0.5, 1.5, size=shp)
+    fields["j"] = g.uniform(0.0, 2.0, size=shp) if with_j else None
+    dt = cfl_dt(desc, chat)
+    return {"name": name, "desc": desc, "fields": fields, "chat": chat, "dt": dt, "n_sub": n_sub}
+
+
+# ----------------------------------------------------------------------------- paper-shaped configs
+
+def dispersion_omega(chat, k, kF, mode):
+    """Continuum frequency of the linear radiation mode about (E0, G0 = 0) with chi = 1/3 (used only
+    to set up the eigenmode initial state; see Eqs. mixedframe:graysystem:radenergy/radmomentum)."""
+    if mode == "frozen_t":
+        return chat * k / math.sqrt(3.0) - 1j * chat * kF
+    disc = complex(-(chat * kF) ** 2 + 4.0 * chat ** 2 * k ** 2 / 3.0)
+    r = np.sqrt(disc)
+    w1 = (-1j * chat * kF + r) / 2.0
+    w2 = (-1j * chat * kF - r) / 2.0
+    # propagating branch with positive phase speed, else the slowly damped diffusion mode
+    if abs(w1.real) > 1e-14 * abs(w1):
+        return w1 if w1.real > 0 else w2
+    return w1 if abs(w1.imag) < abs(w2.imag) else w2
+
+
+def config1(tau=1.0, mode="equilibrium", limiter="minmod", N=512, n_sub=1000, eps=1e-6, theta=0.51,
+            chat=10.0):
+    """1D radiation-only linear wave: N periodic cells on [0, 1), static uniform gas (rho = 1, T = 1,
+    v = 0), E0 = 1, F0 = 0, dE = eps cos(2 pi x), F on the eigenmode, uniform absorption with optical
+    depth tau per wavelength, chat = c = 10, CFL 0.4."""
+    dx = 1.0 / N
+    desc = base_desc((N, 1, 1), (dx, 1.0, 1.0), bc="periodic", c=chat, exchange=mode, limiter=limiter,
+                     kappa_P=tau, kappa_F=tau, kappa_rho_pow=0, theta_F=theta, theta_E=theta,
+                     E_floor=1e-30)
+    x = (np.arange(N) + 0.5) * dx
+    k = 2.0 * math.pi
+    w = dispersion_omega(chat, k, tau, mode)
+    dE = eps * np.exp(1j * k * x)
+    E = 1.0 + dE.real
+    # eigenvector of the linearised radiation-energy equation: -i w dE + i chat k dG = -chat kP dE
+    # (the right-hand side is present only with an emitting gas at fixed temperature)
+    kP_eff = tau if mode == "frozen_t" else 0.0
+    G = (((w + 1j * chat * kP_eff) / (chat * k)) * dE).real
+    shp = (1, 1, N)
+    fields = {
+        "E": E.reshape(shp), "Fx": (desc["c"] * G).reshape(shp), "Fy": np.zeros(shp), "Fz": np.zeros(shp),
+        "T": np.ones(shp), "rho": np.ones(shp), "vx": None, "vy": None, "vz": None,
+        "kP": None, "kF": None, "j": None,
+    }
+    return {"name": f"config1_tau{tau}_{mode}", "desc": desc, "fields": fields, "chat": chat,
+            "dt": cfl_dt(desc, chat), "n_sub": n_sub, "omega": w, "k": k}
+
+
+def config2(N=256, n_sub=2000, L=1.0, sigma=0.05):
+    """2D concentrated source: N x N on [-1, 1]^2, outflow, static gas, Gaussian emissivity of width
+    sigma (2D normalisation) at the centre, kF = 1000 for r < 0.1 and 0.1 outside, chat = c = 1."""
+    dx = 2.0 / N
+    desc = base_desc((N, N, 1), (dx, dx, 1.0), bc="outflow", c=1.0, exchange="equilibrium",
+                     kappa_P=0.0, kappa_F=0.0, theta_F=1.0, theta_E=1.0, E_floor=1e-10)
+    X, Y, _ = cell_centres(desc, x0=(-1.0, -1.0, 0.0))
+    r2 = X ** 2 + Y ** 2
+    j = L * np.exp(-r2 / (2 * sigma ** 2)) / (2 * math.pi * sigma ** 2)
+    kF = np.where(r2 < 0.1 ** 2, 1000.0, 0.1)
+    shp = X.shape
+    fields = {
+        "E": np.full(shp, 1e-10), "Fx": np.zeros(shp), "Fy": np.zeros(shp), "Fz": np.zeros(shp),
+        "T": np.ones(shp), "rho": np.ones(shp), "vx": None, "vy": None, "vz": None,
+        "kP": np.zeros(shp), "kF": kF, "j": j,
+    }
+    return {"name": "config2_source2d", "desc": desc, "fields": fields, "chat": 1.0,
+            "dt": cfl_dt(desc, 1.0), "n_sub": n_sub, "L": L, "sigma": sigma}
+
+
+def config3(N=256, n_sub=25, precision="split"):
+    """3D dusty shell: [-0.5, 0.5]^3, outflow, rho = 1 ambient and 100 in the shell 0.3 <= r <= 0.35,
+    uniform kappa with shell optical depth 10 (k = 2 rho), Gaussian point luminosity L = 1 of width
+    2 dx, FULL exchange at T0 = 1 with E = a_R T0^4, O(beta tau) terms on, theta = 1, radial
+    expansion 1 (about the sound speed) inside the shell, chat = 50 v_max, c = 10 chat."""
+    dx = 1.0 / N
+    gamma = 5.0 / 3.0
+    cs = math.sqrt(gamma)
+    vmax = 1.0 + cs
+    chat = 50.0 * vmax
+    c = 10.0 * chat
+    desc = base_desc((N, N, N), (dx, dx, dx), bc="outflow", c=c, gamma=gamma, exchange="full",
+                     beta_tau=True, kappa_P=2.0, kappa_F=2.0, kappa_rho_pow=1, theta_F=1.0, theta_E=1.0,
+                     E_floor=1e-20, precision=precision)
+    X, Y, Z = cell_centres(desc, x0=(-0.5, -0.5, -0.5))
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    shell = (r >= 0.3) & (r <= 0.35)
+    rho = np.where(shell, 100.0, 1.0)
+    sig = 2.0 * dx
+    j = np.exp(-r ** 2 / (2 * sig ** 2)) / (2 * math.pi * sig ** 2) ** 1.5
+    rs = np.where(r > 0, r, 1.0)
+    vr = np.where(shell, 1.0, 0.0)
+    shp = X.shape
+    fields = {
+        "E": np.ones(shp), "Fx": np.zeros(shp), "Fy": np.zeros(shp), "Fz": np.zeros(shp),
+        "T": np.ones(shp), "rho": rho, "vx": vr * X / rs, "vy": vr * Y / rs, "vz": vr * Z / rs,
+        "kP": None, "kF": None, "j": j,
+    }
+    return {"name": f"config3_shell{N}", "desc": desc, "fields": fields, "chat": chat,
+            "dt": cfl_dt(desc, chat), "n_sub": n_sub}
+
+
+def lognormal_field(N, g: np.random.Generator, sigma=1.0, slope=-11.0 / 3.0):
+    """ln rho: Gaussian random field with power spectrum P(k) ~ k^slope, unit variance scaled to
+    sigma, mean -sigma^2/2 (so <rho> = 1), periodic on an N^3 grid (FFT-generated)."""
+    try:
+        import scipy.fft as sfft
+        rfftn, irfftn = (lambda a: sfft.rfftn(a, workers=-1)), (lambda a, s: sfft.irfftn(a, s=s, workers=-1))
+    except Exception:  # pragma: no cover
+        rfftn, irfftn = np.fft.rfftn, (lambda a, s: np.fft.irfftn(a, s=s))
+    white = g.standard_normal((N, N, N))
+    wk = rfftn(white)
+    kz = np.fft.fftfreq(N)[:, None, None]
+    ky = np.fft.fftfreq(N)[None, :, None]
+    kx = np.fft.rfftfreq(N)[None, None, :]
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    kk[0, 0, 0] = 1.0
+    amp = kk ** (slope / 2.0)
+    amp[0, 0, 0] = 0.0
+    wk *= amp
+    del kk, amp
+    f = irfftn(wk, (N, N, N))
+    del wk
+    f -= f.mean()
+    f *= sigma / f.std()
+    f -= 0.5 * sigma * sigma
+    return f
+
+
+def config4(N=512, n_sub=100, precision="fp64", seed_offset=4):
+    """3D throughput run: [0, 1)^3 periodic, N^3 cells; ln rho a k^{-11/3} Gaussian field with
+    sigma_ln rho = 1 and <rho> = 1; T = exp(0.2 N(0,1)); v_i ~ N(0, (0.01 c)^2); kP = kF = 512 rho^2
+    (opacity per mass proportional to rho); E = a_R T^4 (1 + 0.1 U[-1,1]); F = c E f n with f ~ U[0, 0.5]
+    and n isotropic; c = 10, chat = 1; FULL exchange, O(beta tau) on, theta = 1."""
+    g = rng(seed_offset)
+    dx = 1.0 / N
+    desc = base_desc((N, N, N), (dx, dx, dx), bc="periodic", c=10.0, exchange="full", beta_tau=True,
+                     kappa_P=512.0, kappa_F=512.0, kappa_rho_pow=2, theta_F=1.0, theta_E=1.0,
+                     E_floor=1e-30, precision=precision)
+    shp = (N, N, N)
+    rho = np.exp(lognormal_field(N, g))
+    T = np.exp(0.2 * g.standard_normal(shp))
+    c = desc["c"]
+    vx = (0.01 * c) * g.standard_normal(shp)
+    vy = (0.01 * c) * g.standard_normal(shp)
+    vz = (0.01 * c) * g.standard_normal(shp)
+    E = desc["a_rad"] * T ** 4 * (1.0 + 0.1 * g.uniform(-1.0, 1.0, size=shp))
+    f = g.uniform(0.0, 0.5, size=shp)
+    nx_, ny_, nz_ = random_directions(g, shp)
+    fields = {
+        "E": E, "Fx": c * E * f * nx_, "Fy": c * E * f * ny_, "Fz": c * E * f * nz_,
+        "T": T, "rho": rho, "vx": vx, "vy": vy, "vz": vz, "kP": None, "kF": None, "j": None,
+    }
+    return {"name": f"config4_throughput{N}", "desc": desc, "fields": fields, "chat": 1.0,
+            "dt": cfl_dt(desc, 1.0), "n_sub": n_sub}
+
+
+def config5(n_grids=64, sizes=(32, 48, 64, 96, 128), n_sub=50, precision="split", seed_offset=5):
+    """Batched ensemble: n_grids independent grids on [-0.5, 0.5]^3 with N drawn from `sizes`, outflow,
+    each with its own Gaussian source luminosity L ~ logU(1e-2, 1e2) (width 0.05) and uniform opacity
+    tau ~ logU(0.1, 1000) per box length; FULL exchange, theta = 1, c = 10 chat, chat = 1,
+    dt = 0.4 dx / chat per grid.  Gas at rest, rho = 1, T = 1, E = a_R T^4, F = 0."""
+    g = rng(seed_offset)
+    cases = []
+    Ns = g.choice(np.array(sizes), size=n_grids)
+    Ls = np.exp(g.uniform(math.log(1e-2), math.log(1e2), size=n_grids))
+    taus = np.exp(g.uniform(math.log(0.1), math.log(1000.0), size=n_grids))
+    for i in range(n_grids):
+        N = int(Ns[i])
+        dx = 1.0 / N
+        desc = base_desc((N, N, N), (dx, dx, dx), bc="outflow", c=10.0, exchange="full", beta_tau=False,
+                         kappa_P=float(taus[i]), kappa_F=float(taus[i]), kappa_rho_pow=0, theta_F=1.0,
+                         theta_E=1.0, E_floor=1e-30, precision=precision)
+        X, Y, Z = cell_centres(desc, x0=(-0.5, -0.5, -0.5))
+        r2 = X ** 2 + Y ** 2 + Z ** 2
+        sig = 0.05
+        j = float(Ls[i]) * np.exp(-r2 / (2 * sig ** 2)) / (2 * math.pi * sig ** 2) ** 1.5
+        shp = X.shape
+        fields = {
+            "E": np.ones(shp), "Fx": np.zeros(shp), "Fy": np.zeros(shp), "Fz": np.zeros(shp),
+            "T": np.ones(shp), "rho": np.ones(shp), "vx": None, "vy": None, "vz": None,
+            "kP": None, "kF": None, "j": j,
+        }
+        cases.append({"name": f"config5_grid{i}_N{N}", "desc": desc, "fields": fields, "chat": 1.0,
+                      "dt": cfl_dt(desc, 1.0), "n_sub": n_sub})
+    return cases
