@@ -159,3 +159,30 @@ def test_uniform_state_is_pure_theta_decay(mode):
         expect = E0
     assert np.allclose(out["E"], expect, rtol=4.5e-16, atol=0)
     assert st["n_realizability_fix"] == 0 and st["n_nonfinite"] == 0
+
+
+def test_beta_tau_flux_relaxes_to_comoving_value():
+    """With the O(beta tau) terms (Eq. m1:simplifiedsource) a uniform medium moving at v drives
+    G = F/c towards (4/3) E v / c, radiation carried along with the gas (the dynamic-diffusion
+    balance of -chat kF G and chat (4/3) kF E v/c); meanwhile E changes only through
+    chat kF (v/c).G, which is positive and second order in v/c."""
+    n = (4, 3, 3)
+    desc = wl.base_desc(n, tuple(1.0 / v for v in n), bc="periodic", c=100.0, exchange="equilibrium",
+                        beta_tau=True, kappa_P=50.0, kappa_F=50.0, kappa_rho_pow=0, theta_F=1.0, theta_E=1.0)
+    shp = (n[2], n[1], n[0])
+    v = np.array([0.7, -0.4, 0.2])
+    fields = {"E": np.full(shp, 2.0), "Fx": np.zeros(shp), "Fy": np.zeros(shp), "Fz": np.zeros(shp),
+              "T": np.ones(shp), "rho": np.ones(shp), "vx": np.full(shp, v[0]), "vy": np.full(shp, v[1]),
+              "vz": np.full(shp, v[2]), "kP": None, "kF": None, "j": None}
+    chat = 1.0
+    case = {"desc": desc, "fields": fields, "chat": chat, "dt": wl.cfl_dt(desc, chat), "n_sub": 400}
+    out, st = orc.subcycles(case)
+    E1 = out["E"][0, 0, 0]
+    G1 = np.array([out[k][0, 0, 0] for k in ("Fx", "Fy", "Fz")]) / desc["c"]
+    # G trails the slowly growing E by O(growth / (chat kF)) ~ 1e-4
+    assert np.allclose(G1, (4.0 / 3.0) * E1 * v / desc["c"], rtol=1e-3)
+    beta2 = float(v @ v) / desc["c"] ** 2
+    t = case["n_sub"] * case["dt"]
+    # dE/dt = chat kF (4/3) E beta^2 once G has relaxed (relaxation time 1/(chat kF) << t)
+    growth = math.log(E1 / 2.0) / t
+    assert growth == pytest.approx(chat * 50.0 * (4.0 / 3.0) * beta2, rel=0.05)
