@@ -1,0 +1,312 @@
+"""Benchmark of the subcycled M1 radiation update on GB300.
+
+Workload (throughput configuration): 512^3 periodic grid, radiation (E, Fx, Fy, Fz) plus frozen gas
+(rho, T, vx, vy, vz) with a seeded lognormal density (sigma_ln rho = 1), opacities proportional to rho
+(k = 512 rho^2), isotropic random F with |F| <= 0.5 cE, FULL energy exchange and O(beta tau) terms,
+c = 10, chat = 1, CFL 0.4.  One step = one call of rhd_radiation_subcycle with 100 subcycles, i.e. the
+whole hot path (every per-subcycle stage) over the grid.  Headline: the split-precision path; the plain
+FP64 path is measured alongside (4 subcycles per step, same rate unit).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on the host cores on a bounded
+sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "radiation cell-updates/s per subcycle (FP64 vs FP32/FP64 split) and % HBM roofline"
+UNIT = "cell-updates/s"
+# algorithmic bytes per cell-update of the throughput workload (FULL exchange, beta tau on, opacity law
+# in registers): U^m read + U^{m+1} write 64 B, T read + write 16 B, rho and v read
+B_ALG = {"fp64": 64 + 16 + 8 + 24, "split": 64 + 16 + 4 + 12}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=512)
+    ap.add_argument("--n-sub", type=int, default=100)
+    ap.add_argument("--fp64-n-sub", type=int, default=4)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+def cpu_baseline(case, seconds, n_cells_box=64):
+    """Oracle (plain C, FP64, OpenMP over cells) on bounded boxes of the same grid, one subcycle each."""
+    from oracle import oracle as orc
+
+    N = case["desc"]["n"][0]
+    g = np.random.default_rng(1)
+    t0 = time.perf_counter()
+    cells = 0
+    boxes = 0
+    while True:
+        lo = [int(v) for v in g.integers(0, N - n_cells_box, size=3)]
+        hi = [v + n_cells_box for v in lo]
+        orc.subcycle_box(case, lo, hi)
+        cells += n_cells_box ** 3
+        boxes += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": cells / el, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{boxes} boxes of {n_cells_box}^3 cells of the {N}^3 grid, one subcycle each "
+                      f"({el:.1f} s of CPU work)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import build_oracle
+    from paper_1306_0010_gb300 import workloads as wl
+
+    build_oracle.build()
+    case = wl.config4(N=args.N, n_sub=args.n_sub)
+    per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(case, per_step / 4)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(case, per_step))
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[0], value=v)
+    cells_per_step = args.N ** 3 * args.n_sub
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cells_per_step / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, "fp64"),
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, precision):
+    return {"workload": f"3D throughput run, {args.N}^3 periodic SoA grid, lognormal rho (sigma_ln rho = 1), "
+                        f"k = 512 rho^2, |F| <= 0.5 cE, FULL exchange, beta tau on, c = 10, chat = 1",
+            "N": args.N, "n_sub_per_step": args.n_sub, "precision": precision,
+            "l2": "inputs larger than L2 (1.07 GB per FP64 field)"}
+
+
+def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream):
+    desc = dict(case["desc"], precision=precision)
+    g = rhd.Grid(desc, stream=stream.cuda_stream)
+    f = case["fields"]
+    dev = {k: (None if f[k] is None else torch.from_numpy(f[k]).to("cuda")) for k in f}
+    with torch.cuda.stream(stream):
+        g.set_gas_state(dev["rho"], dev["T"], dev["vx"], dev["vy"], dev["vz"], dev["kP"], dev["kF"], dev["j"])
+        g.set_moments(dev["E"], dev["Fx"], dev["Fy"], dev["Fz"])
+    stream.synchronize()
+    for _ in range(warmup):
+        g.radiation_subcycle(n_sub, case["chat"], case["dt"])
+    stream.synchronize()
+    g.reset_stats()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for s in range(steps):
+        g.radiation_subcycle(n_sub, case["chat"], case["dt"])
+        ev[s + 1].record(stream)
+    stream.synchronize()
+    per_step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    st = g.get_stats(allow_nonfinite=True)
+    g.close()
+    del dev
+    return total_ms, per_step_ms, st
+
+
+def time_e2e(torch, rhd, case, precision, n_sub, steps, warmup):
+    """Same metric through the public API with host (pinned) buffers: per step, H2D of the moments and
+    gas state, the subcycles, D2H of the moments and temperature."""
+    desc = dict(case["desc"], precision=precision)
+    g = rhd.Grid(desc)
+    f = case["fields"]
+    pin = {k: (None if f[k] is None else torch.from_numpy(f[k]).pin_memory()) for k in f}
+    outs = [torch.empty(f["E"].shape, dtype=torch.float64).pin_memory() for _ in range(5)]
+    h2d = sum(v.numel() * 8 for k, v in pin.items() if v is not None and k in
+              ("E", "Fx", "Fy", "Fz", "rho", "T", "vx", "vy", "vz", "kP", "kF", "j"))
+    d2h = sum(o.numel() * 8 for o in outs)
+
+    def step():
+        g.set_gas_state(pin["rho"], pin["T"], pin["vx"], pin["vy"], pin["vz"], pin["kP"], pin["kF"], pin["j"])
+        g.set_moments(pin["E"], pin["Fx"], pin["Fy"], pin["Fz"])
+        g.radiation_subcycle(n_sub, case["chat"], case["dt"])
+        g.get_moments(outs[0], outs[1], outs[2], outs[3])
+        g.get_gas_state(outs[4])
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    g.close()
+    return el, h2d, d2h
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    ws, rank, lrank = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(lrank)
+    from paper_1306_0010_gb300 import build, rhd, workloads as wl
+
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    rhd.lib()
+    case = wl.config4(N=args.N, n_sub=args.n_sub)
+    cells = args.N ** 3
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+
+    # headline: split path; every rank advances its own independent grid (replicas, no exchange)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(lrank)
+    clk.start()
+    total_ms, per_step, st = time_path(torch, rhd, case, "split", args.n_sub, args.steps, args.warmup, stream)
+    clocks = clk.stop()
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    units = cells * args.n_sub * args.steps * ws
+    value = units / (total_ms * 1e-3)
+    launch_ms = total_ms / (args.steps * args.n_sub)
+    achieved = B_ALG["split"] * cells / (launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_cell_update": B_ALG["split"], "kernel": "subcycle_kernel<float,32,8,3,split>",
+                "launch_ms": launch_ms}
+    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_path):
+        tr = json.load(open(traffic_path)).get("split")
+        if tr and tr.get("N") == args.N:
+            roofline["traffic"] = tr["bytes_per_launch"]
+
+    extra = {}
+    if not args.no_fp64:
+        fp_ms, fp_steps, fst = time_path(torch, rhd, case, "fp64", args.fp64_n_sub, max(2, args.steps // 2),
+                                         args.warmup, stream)
+        fn = max(2, args.steps // 2)
+        fv = cells * args.fp64_n_sub * fn / (fp_ms * 1e-3) * ws
+        f_launch = fp_ms / (fn * args.fp64_n_sub)
+        fa = B_ALG["fp64"] * cells / (f_launch * 1e-3) / 1e9
+        extra["fp64_path"] = {"value": fv, "unit": UNIT, "n_sub_per_step": args.fp64_n_sub,
+                              "launch_ms": f_launch, "split_speedup": value / fv,
+                              "roofline": {"bound": "hbm", "achieved": fa, "peak": hbm_peak, "unit": "GB/s",
+                                           "frac": fa / hbm_peak, "bytes_per_cell_update": B_ALG["fp64"]}}
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        el, h2d, d2h = time_e2e(torch, rhd, case, "split", args.n_sub, max(2, args.steps // 2), 1)
+        n_e = max(2, args.steps // 2)
+        e2e = {"value": cells * args.n_sub * n_e / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = cpu_baseline(case, args.cpu_seconds)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+                "config": workload_config(args, "split"), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": args.steps * args.n_sub, "clocks": clocks,
+                "stats": {k: st[k] for k in ("n_realizability_fix", "n_face_fallback", "n_theta_fallback",
+                                             "n_nonfinite", "newton_iter_max")},
+                "per_step_ms": per_step}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * rhd.h -- C ABI of librhd.so: the subcycled gray M1 radiation update under the reduced speed of
+ * light approximation (RSLA) of Skinner & Ostriker (2013), "A two-moment radiation hydrodynamics
+ * module in Athena using a time-explicit Godunov method", run on one NVIDIA GB300 (sm_103a).
+ *
+ * What one subcycle computes (Section 3.1, algorithm step 4; Sections 3.3 and 3.4):
+ *   the radiation subsystem  d_t U + div F(U) = S  for U = (E, F/c) (Eq. algorithm:compactform,
+ *   radiation rows of Eq. algorithm:variables, with chat in the time derivatives) is advanced by
+ *   dt = dt_rad with the van Leer predictor/corrector integrator: first-order HLL fluxes
+ *   (Eq. hyperbolic:hllflux2) and a half step, then piecewise-linear reconstruction of the half-step
+ *   state, the M1 closure (Eqs. m1:m1tns, m1:chi), the wave speeds lambda_1,3 (Eq.
+ *   hyperbolic:evals13), HLL fluxes and the full step; the non-stiff O(beta tau) sources
+ *   (Eq. algorithm:source:explicit:rad with Eq. m1:simplifiedsource) are added in both stages, the
+ *   absorption of F by the theta scheme of Eq. (source:stiff:radmomentum:soln), and the gas-radiation
+ *   energy exchange by the quartic theta scheme of Eqs. (source:energyupdate)-(source:polynomial)
+ *   (or its absorption-only, frozen-temperature or radiative-equilibrium variants) against the
+ *   frozen gas state.  The flux-limiting condition |F| <= cE (Eq. m1:fluxlimit) is re-imposed after
+ *   each stage.
+ *
+ * Conventions
+ *   - Every array is dense FP64 over the interior cells only, x fastest: idx = i + nx*(j + ny*k).
+ *     A direction with n = 1 is inactive (1D: ny = nz = 1; 2D: nz = 1).  Active directions need
+ *     n >= 3.
+ *   - Pointers are borrowed, never kept: host arrays are copied during the call; device arrays
+ *     (on_device = 1, e.g. torch CUDA tensors) are read or written on the context's stream during
+ *     the call.  The library owns its own device buffers, which hold E and G = F/c.
+ *   - Every function returns an rhd_status and never aborts, throws or exits.  Arguments are checked
+ *     before any launch.  On failure rhd_last_error() describes the problem; the context stays
+ *     usable unless the status is RHD_ERR_CUDA from a sticky device error.
+ *   - A context is bound to one CUDA stream and is not thread-safe; separate contexts are
+ *     independent.  A non-default stream given in the descriptor is used directly; with NULL (the
+ *     legacy default stream) the library runs on a stream of its own, ordered after the caller's
+ *     legacy stream on entry and before it on return.
+ */
+#ifndef RHD_H
+#define RHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RHD_ABI_VERSION 1
+
+typedef struct rhd_ctx rhd_ctx; /* opaque, library-owned */
+
+typedef enum {
+    RHD_OK = 0,
+    RHD_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, out-of-range parameter) */
+    RHD_ERR_STATE = 2,      /* call not valid in the current state (e.g. state not set yet) */
+    RHD_ERR_CUDA = 3,       /* a CUDA runtime call failed; see rhd_last_error */
+    RHD_ERR_OOM = 4,        /* device or pinned-host allocation failed */
+    RHD_ERR_CFL = 5,        /* dt > cfl * min(dx) / chat, or chat > c (Eqs. algorithm:radtimestep) */
+    RHD_ERR_NONFINITE = 6,  /* non-finite values were produced (reported by rhd_get_stats) */
+    RHD_ERR_TIMEOUT = 7,    /* a bounded wait gave up */
+    RHD_ERR_UNSUPPORTED = 8 /* the operation is not part of this library */
+} rhd_status;
+
+typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_OUTFLOW = 1, RHD_BC_REFLECT = 2, RHD_BC_DIRICHLET = 3 } rhd_bc;
+
+/* Energy-exchange treatment (Section 3.4):
+ *   FULL        implicit quartic theta scheme for e and E (Eqs. source:energyupdate - source:eradupdate),
+ *               once per subcycle after the corrector; updates T
+ *   ABSORB      absorption only, E <- E [1-(1-theta)x]/[1+theta x], x = chat kP dt (Eq.
+ *               source:stiff:radenergy:soln), in both stages
+ *   EQUILIBRIUM radiative equilibrium: no exchange term
+ *   FROZEN_T    absorption and emission against the fixed gas temperature,
+ *               E <- [E(1-(1-theta)x) + x a_R T^4]/[1+theta x], in both stages */
+typedef enum { RHD_EX_FULL = 0, RHD_EX_ABSORB = 1, RHD_EX_EQUILIBRIUM = 2, RHD_EX_FROZEN_T = 3 } rhd_exchange;
+typedef enum { RHD_LIM_MINMOD = 0, RHD_LIM_MC = 1, RHD_LIM_NONE = 2 } rhd_limiter;
+typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_P1 = 1 } rhd_closure;     /* P1: T = I/3 (Section 2.3) */
+typedef enum { RHD_SPEEDS_M1 = 0, RHD_SPEEDS_FIXED = 1 } rhd_speeds;     /* FIXED: -+chat/sqrt(3) */
+/* FP64: every step in FP64.  SPLIT: reconstruction, closure, wave speeds and HLL fluxes in FP32;
+ * the conserved-variable accumulation, the source terms and the energy exchange in FP64. */
+typedef enum { RHD_FP64 = 0, RHD_SPLIT = 1 } rhd_precision;
+/* RHD_FLAG_NO_GRAPH: issue the n_sub launches one by one instead of replaying a captured CUDA graph. */
+#define RHD_FLAG_NO_GRAPH 1
+
+typedef struct {
+    int n[3];                   /* nx, ny, nz */
+    double dx[3];               /* uniform spacing per direction (ignored when inactive) */
+    int bc_lo[3], bc_hi[3];     /* rhd_bc per face */
+    double c;                   /* true speed of light: source terms and f = |F|/(cE) */
+    double a_rad;               /* radiation constant a_R */
+    double gamma;               /* adiabatic index, e = P/(gamma-1) */
+    double mu_over_kB;          /* mean particle mass over k_B: P = rho T / mu_over_kB */
+    double theta_F, theta_E;    /* theta of the F absorption and of the E exchange, in (0, 1] */
+    double E_floor;             /* E is kept >= E_floor > 0 */
+    double cfl;                 /* Courant number K0 of Eq. (algorithm:radtimestep), (0, 1] */
+    int exchange;               /* rhd_exchange */
+    int beta_tau;               /* 1: include the O(beta tau) source terms (Section 3.4 code switch) */
+    int limiter;                /* rhd_limiter */
+    int closure;                /* rhd_closure */
+    int speeds;                 /* rhd_speeds */
+    int precision;              /* rhd_precision */
+    int flags;                  /* RHD_FLAG_* bits */
+    int z_chunk;                /* z planes per CTA of the fused kernel; 0 chooses automatically */
+    double kappa_P, kappa_F;    /* opacity law used where kP / kF arrays are not given: */
+    int kappa_rho_pow;          /*   k = kappa * rho^p, p in {0, 1, 2} (absorption coefficients) */
+    void* cuda_stream;          /* cudaStream_t to run on (NULL: legacy default stream, see above) */
+} rhd_grid_desc;
+
+typedef struct {
+    int64_t n_subcycles;         /* subcycles run since the last reset */
+    int64_t n_realizability_fix; /* cells rescaled onto |F| = cE (both stages, interior cells) */
+    int64_t n_face_fallback;     /* (cell, direction) pairs whose limited slope was zeroed */
+    int64_t n_theta_fallback;    /* energy-exchange solves redone with theta = 1 (no feasible root) */
+    int64_t n_newton_fallback;   /* energy-exchange solves finished by bisection */
+    int64_t n_nonfinite;         /* interior cells that produced a non-finite value */
+    int32_t newton_iter_max;     /* largest Newton iteration count of one solve */
+    int32_t reserved;
+    double sum_E;                /* sum of E over the interior (current state), FP64, fixed order */
+    double sum_F[3];             /* sums of Fx, Fy, Fz */
+    double max_f;                /* max |F|/(cE) */
+} rhd_stats;
+
+/* Create a context for one grid (Section 3.1).  Validates d, allocates the device state and makes
+ * the stream current.  *out is set only on success.  Errors: RHD_ERR_ARG, RHD_ERR_OOM, RHD_ERR_CUDA. */
+rhd_status rhd_init_grid(rhd_ctx** out, const rhd_grid_desc* d);
+
+/* Set the frozen gas state of the subcycles (Section 3.4: rho, T and v are held fixed; T changes only
+ * through the FULL exchange).  rho and T are required; vx, vy, vz NULL mean 0; kP, kF NULL mean the
+ * opacity law of the descriptor; j (emissivity, energy per volume per time, entering as chat j / c in
+ * the E row, cf. Eq. radshell:sourceprofile) NULL means 0.  Errors: RHD_ERR_ARG, RHD_ERR_CUDA. */
+rhd_status rhd_set_gas_state(rhd_ctx* ctx, const double* rho, const double* T, const double* vx,
+                             const double* vy, const double* vz, const double* kP, const double* kF,
+                             const double* j, int on_device);
+
+/* Set the radiation moments E, Fx, Fy, Fz (Eq. mixedframe:radmoments).  Errors: RHD_ERR_ARG, RHD_ERR_CUDA. */
+rhd_status rhd_set_moments(rhd_ctx* ctx, const double* E, const double* Fx, const double* Fy,
+                           const double* Fz, int on_device);
+
+/* Fixed radiation state (E, Fx, Fy, Fz) seen through a Dirichlet face; face = 2*dir + (0 low, 1 high). */
+rhd_status rhd_set_dirichlet(rhd_ctx* ctx, int face, const double state[4]);
+
+/* Run n_sub >= 0 radiation subcycles of length dt with reduced speed of light chat (Section 3.1 steps
+ * 4-5).  Requires chat <= c and dt <= cfl * min(dx) / chat (RHD_ERR_CFL otherwise).  The loop is
+ * replayed from a cached CUDA graph of n_sub kernel launches on the context stream; the call returns
+ * without synchronising.  Errors: RHD_ERR_ARG, RHD_ERR_STATE (moments or gas not set), RHD_ERR_CFL,
+ * RHD_ERR_CUDA. */
+rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double dt);
+
+/* Gas step of Section 3.1 (steps 1-3 and 6).  Not part of this library: always RHD_ERR_UNSUPPORTED. */
+rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas);
+
+/* Copy the current moments out (synchronises the stream).  Errors: RHD_ERR_ARG, RHD_ERR_STATE, RHD_ERR_CUDA. */
+rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, double* Fz, int on_device);
+
+/* Copy the current gas temperature out (changes only in FULL mode).  Synchronises the stream. */
+rhd_status rhd_get_gas_state(rhd_ctx* ctx, double* T, int on_device);
+
+/* Counters accumulated since the last reset plus sums over the current state (synchronises). */
+rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out);
+rhd_status rhd_reset_stats(rhd_ctx* ctx);
+
+/* Block until the context stream is idle, or give up after timeout_ms (RHD_ERR_TIMEOUT; the work keeps
+ * running and the context stays usable).  timeout_ms < 0 waits without limit. */
+rhd_status rhd_synchronize(rhd_ctx* ctx, int timeout_ms);
+
+/* Message of the last failure of this context (or of rhd_init_grid when ctx is NULL); never NULL. */
+const char* rhd_last_error(const rhd_ctx* ctx);
+
+/* Release the context and its device buffers.  NULL is accepted. */
+rhd_status rhd_destroy(rhd_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched ensemble: many independent grids of uneven sizes advanced together.  Each subcycle is one
+ * persistent launch whose CTAs pull (grid, tile) work items from a global counter; n_sub launches are
+ * replayed from one CUDA graph.  Grids never exchange data.  All grids share precision, exchange mode,
+ * limiter, closure and speeds (taken from descs[0]); sizes, spacing, boundaries, physics constants
+ * and opacity laws are per grid.
+ * ------------------------------------------------------------------------------------------- */
+rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* descs);
+/* Per-grid state setters/getters of an ensemble context (grid in [0, n_grids)). */
+rhd_status rhd_ensemble_set_gas_state(rhd_ctx* ctx, int grid, const double* rho, const double* T,
+                                      const double* vx, const double* vy, const double* vz,
+                                      const double* kP, const double* kF, const double* j, int on_device);
+rhd_status rhd_ensemble_set_moments(rhd_ctx* ctx, int grid, const double* E, const double* Fx,
+                                    const double* Fy, const double* Fz, int on_device);
+rhd_status rhd_ensemble_get_moments(rhd_ctx* ctx, int grid, double* E, double* Fx, double* Fy,
+                                    double* Fz, int on_device);
+rhd_status rhd_ensemble_get_gas_state(rhd_ctx* ctx, int grid, double* T, int on_device);
+/* n_sub subcycles of every grid, grid g with its own dt_per_grid[g] (host array), common chat. */
+rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const double* dt_per_grid);
+
+/* Library identification: ABI version and the compute capability it was built for (e.g. 103). */
+int rhd_abi_version(void);
+int rhd_built_arch(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RHD_H */

@@ -1,0 +1,73 @@
+// k_fp64.cu -- FP64 instantiations of the fused subcycle kernel and of the ensemble kernel.
+#include "subcycle.cuh"
+
+namespace rhd {
+
+template <typename R, int TX, int TY, int DIM, bool SPLIT>
+static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
+{
+    using G = Geo<TX, TY, DIM>;
+    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(p.tiles_x * p.tiles_y), DIM == 3 ? (unsigned)((p.g.n[2] + p.z_chunk - 1) / p.z_chunk) : 1u);
+    k<<<grid, TX * TY, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, int TX, int TY, bool SPLIT>
+static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaStream_t s)
+{
+    using G = Geo<TX, TY, 3>;
+    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    auto k = ensemble_kernel<R, TX, TY, SPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_ctas, TX * TY, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, int TX, int TY, bool SPLIT>
+static int ens_occupancy()
+{
+    using G = Geo<TX, TY, 3>;
+    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    auto k = ensemble_kernel<R, TX, TY, SPLIT>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, TX * TY, smem) != cudaSuccess || n < 1) return 1;
+    return n;
+}
+
+void tile_shape(int precision, int nact, int* tx, int* ty)
+{
+    if (nact == 1) {
+        *tx = 128;
+        *ty = 1;
+    } else if (precision == 0) {
+        *tx = 16;
+        *ty = 8;
+    } else {
+        *tx = 32;
+        *ty = 8;
+    }
+}
+
+cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s)
+{
+    switch (p.g.nact) {
+    case 1: return launch_tile_kernel<double, 128, 1, 1, false>(p, s);
+    case 2: return launch_tile_kernel<double, 16, 8, 2, false>(p, s);
+    default: return launch_tile_kernel<double, 16, 8, 3, false>(p, s);
+    }
+}
+
+cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s)
+{
+    return launch_ens_kernel<double, 16, 8, false>(p, n_ctas, s);
+}
+
+int ensemble_ctas_per_sm_fp64() { return ens_occupancy<double, 16, 8, false>(); }
+
+}  // namespace rhd

@@ -1,0 +1,60 @@
+// k_fp64.cu -- Split-precision (FP32 fluxes, FP64 state) instantiations of the fused subcycle kernel and of the ensemble kernel.
+#include "subcycle.cuh"
+
+namespace rhd {
+
+template <typename R, int TX, int TY, int DIM, bool SPLIT>
+static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
+{
+    using G = Geo<TX, TY, DIM>;
+    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(p.tiles_x * p.tiles_y), DIM == 3 ? (unsigned)((p.g.n[2] + p.z_chunk - 1) / p.z_chunk) : 1u);
+    k<<<grid, TX * TY, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, int TX, int TY, bool SPLIT>
+static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaStream_t s)
+{
+    using G = Geo<TX, TY, 3>;
+    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    auto k = ensemble_kernel<R, TX, TY, SPLIT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_ctas, TX * TY, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, int TX, int TY, bool SPLIT>
+static int ens_occupancy()
+{
+    using G = Geo<TX, TY, 3>;
+    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    auto k = ensemble_kernel<R, TX, TY, SPLIT>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, TX * TY, smem) != cudaSuccess || n < 1) return 1;
+    return n;
+}
+
+
+cudaError_t launch_subcycle_split(const StepParams& p, cudaStream_t s)
+{
+    switch (p.g.nact) {
+    case 1: return launch_tile_kernel<float, 128, 1, 1, true>(p, s);
+    case 2: return launch_tile_kernel<float, 32, 8, 2, true>(p, s);
+    default: return launch_tile_kernel<float, 32, 8, 3, true>(p, s);
+    }
+}
+
+cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s)
+{
+    return launch_ens_kernel<float, 32, 8, true>(p, n_ctas, s);
+}
+
+int ensemble_ctas_per_sm_split() { return ens_occupancy<float, 32, 8, true>(); }
+
+}  // namespace rhd

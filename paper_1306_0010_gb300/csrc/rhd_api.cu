@@ -1,0 +1,887 @@
+// rhd_api.cu -- host runtime of librhd.so: contexts, device buffers, argument checks, stream
+// ordering, the CUDA-graph cache of the subcycle loop, statistics, and the batched ensemble.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rhd.h"
+#include "rhd_internal.h"
+
+using namespace rhd;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct GraphEntry {
+    int n_sub;
+    int start;
+    double chat, dt;
+    cudaGraphExec_t exec;
+    unsigned long long stamp;
+};
+
+// Device state of one grid.
+struct GridState {
+    rhd_grid_desc desc;
+    GridParams gp;
+    long long ncell = 0;
+    int tx = 0, ty = 0, tiles_x = 0, tiles_y = 0, z_chunk = 1;
+    double* U[2][4] = {{nullptr}};
+    double* T = nullptr;
+    double* rho = nullptr;
+    double* v[3] = {nullptr, nullptr, nullptr};
+    double* kP = nullptr;
+    double* kF = nullptr;
+    double* j = nullptr;
+    float* rho32 = nullptr;
+    float* v32[3] = {nullptr, nullptr, nullptr};
+    float* kP32 = nullptr;
+    float* kF32 = nullptr;
+    float* j32 = nullptr;
+    bool has_v = false, has_kP = false, has_kF = false, has_j = false;
+    bool has_moments = false, has_gas = false;
+};
+
+}  // namespace
+
+struct rhd_ctx {
+    bool ensemble = false;
+    int device = 0;
+    int num_sms = 152;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;  // the caller's stream when it is not the legacy default stream
+    bool own_stream = false;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<GridState> grids;
+    int cur = 0;  // buffer index holding the current state (shared by all grids)
+    DevStats* dstats = nullptr;
+    double* red_partials = nullptr;
+    double* red_out = nullptr;
+    int red_blocks = 1;
+    long long n_subcycles = 0;
+    std::vector<GraphEntry> graphs;
+    unsigned long long stamp = 0;
+    std::string err;
+    // ensemble
+    EnsembleGrid* d_egrids[2] = {nullptr, nullptr};
+    unsigned long long* d_counter = nullptr;
+    long long n_items = 0;
+    int ens_ctas = 0;
+};
+
+namespace {
+
+rhd_status fail(rhd_ctx* ctx, rhd_status st, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    else g_init_error = msg;
+    return st;
+}
+
+#define RHD_CUDA(ctx, call)                                                                          \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? RHD_ERR_OOM : RHD_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+    } while (0)
+
+// With the legacy default stream the work runs on a library stream (CUDA graphs cannot be captured
+// on the legacy stream) ordered after the caller's stream, and the caller's stream after the work.
+// Any other stream is used directly.
+rhd_status enter(rhd_ctx* ctx)
+{
+    RHD_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (!ctx->own_stream) return RHD_OK;
+    RHD_CUDA(ctx, cudaEventRecord(ctx->ev_in, ctx->user_stream));
+    RHD_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+    return RHD_OK;
+}
+rhd_status leave(rhd_ctx* ctx)
+{
+    if (!ctx->own_stream) return RHD_OK;
+    RHD_CUDA(ctx, cudaEventRecord(ctx->ev_out, ctx->stream));
+    RHD_CUDA(ctx, cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+    return RHD_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+rhd_status validate_desc(rhd_ctx* ctx, const rhd_grid_desc* d)
+{
+    if (!d) return fail(ctx, RHD_ERR_ARG, "descriptor is NULL");
+    int nact = 0;
+    bool seen_inactive = false;
+    for (int k = 0; k < 3; ++k) {
+        if (d->n[k] < 1) return fail(ctx, RHD_ERR_ARG, "n[" + std::to_string(k) + "] must be >= 1");
+        if (d->n[k] > 1) {
+            if (seen_inactive) return fail(ctx, RHD_ERR_ARG, "inactive directions (n = 1) must be the trailing ones");
+            if (d->n[k] < 3) return fail(ctx, RHD_ERR_ARG, "active directions need n >= 3");
+            if (!finite_pos(d->dx[k])) return fail(ctx, RHD_ERR_ARG, "dx must be positive and finite");
+            for (int s = 0; s < 2; ++s) {
+                int bc = s ? d->bc_hi[k] : d->bc_lo[k];
+                if (bc < 0 || bc > 3) return fail(ctx, RHD_ERR_ARG, "unknown boundary condition");
+            }
+            ++nact;
+        } else {
+            seen_inactive = true;
+        }
+    }
+    if (nact == 0) nact = 0;
+    long long ncell = (long long)d->n[0] * d->n[1] * d->n[2];
+    if (ncell > (1LL << 34)) return fail(ctx, RHD_ERR_ARG, "grid too large");
+    if (!finite_pos(d->c)) return fail(ctx, RHD_ERR_ARG, "c must be positive");
+    if (!(std::isfinite(d->a_rad) && d->a_rad >= 0)) return fail(ctx, RHD_ERR_ARG, "a_rad must be >= 0");
+    if (!(std::isfinite(d->gamma) && d->gamma > 1.0)) return fail(ctx, RHD_ERR_ARG, "gamma must be > 1");
+    if (!finite_pos(d->mu_over_kB)) return fail(ctx, RHD_ERR_ARG, "mu_over_kB must be positive");
+    if (!(d->theta_F > 0 && d->theta_F <= 1) || !(d->theta_E > 0 && d->theta_E <= 1))
+        return fail(ctx, RHD_ERR_ARG, "theta must lie in (0, 1]");
+    if (!finite_pos(d->E_floor)) return fail(ctx, RHD_ERR_ARG, "E_floor must be positive");
+    if (!(d->cfl > 0 && d->cfl <= 1)) return fail(ctx, RHD_ERR_ARG, "cfl must lie in (0, 1]");
+    if (d->exchange < 0 || d->exchange > 3) return fail(ctx, RHD_ERR_ARG, "unknown exchange mode");
+    if (d->limiter < 0 || d->limiter > 2) return fail(ctx, RHD_ERR_ARG, "unknown limiter");
+    if (d->closure < 0 || d->closure > 1) return fail(ctx, RHD_ERR_ARG, "unknown closure");
+    if (d->speeds < 0 || d->speeds > 1) return fail(ctx, RHD_ERR_ARG, "unknown wave-speed option");
+    if (d->precision < 0 || d->precision > 1) return fail(ctx, RHD_ERR_ARG, "unknown precision");
+    if (d->z_chunk < 0) return fail(ctx, RHD_ERR_ARG, "z_chunk must be >= 0");
+    if (!(std::isfinite(d->kappa_P) && d->kappa_P >= 0) || !(std::isfinite(d->kappa_F) && d->kappa_F >= 0))
+        return fail(ctx, RHD_ERR_ARG, "kappa must be >= 0");
+    if (d->kappa_rho_pow < 0 || d->kappa_rho_pow > 2) return fail(ctx, RHD_ERR_ARG, "kappa_rho_pow must be 0, 1 or 2");
+    return RHD_OK;
+}
+
+int count_active(const rhd_grid_desc& d)
+{
+    int n = 0;
+    for (int k = 0; k < 3; ++k) n += d.n[k] > 1;
+    return n;
+}
+
+void fill_params(GridState& gs)
+{
+    const rhd_grid_desc& d = gs.desc;
+    GridParams& g = gs.gp;
+    std::memset(&g, 0, sizeof(g));
+    for (int k = 0; k < 3; ++k) {
+        g.n[k] = d.n[k];
+        g.inv_dx[k] = d.n[k] > 1 ? 1.0 / d.dx[k] : 0.0;
+        g.bc_lo[k] = d.bc_lo[k];
+        g.bc_hi[k] = d.bc_hi[k];
+    }
+    g.nact = count_active(d);
+    g.c = d.c;
+    g.a_rad = d.a_rad;
+    g.gamma = d.gamma;
+    g.mu_over_kB = d.mu_over_kB;
+    g.theta_F = d.theta_F;
+    g.theta_E = d.theta_E;
+    g.E_floor = d.E_floor;
+    g.kappa_P = d.kappa_P;
+    g.kappa_F = d.kappa_F;
+    g.kpow = d.kappa_rho_pow;
+    g.exchange = d.exchange;
+    g.beta_tau = d.beta_tau ? 1 : 0;
+    g.limiter = d.limiter;
+    g.closure = d.closure;
+    g.speeds = d.speeds;
+    g.inv_c = 1.0 / d.c;
+    g.gm1_mu = (d.gamma - 1.0) * d.mu_over_kB;
+    g.f_inv_c = (float)g.inv_c;
+    g.f_gm1_mu = (float)g.gm1_mu;
+    g.f_c = (float)d.c;
+    g.f_a_rad = (float)d.a_rad;
+    g.f_theta_F = (float)d.theta_F;
+    g.f_theta_E = (float)d.theta_E;
+    g.f_E_floor = (float)d.E_floor;
+    g.f_kappa_P = (float)d.kappa_P;
+    g.f_kappa_F = (float)d.kappa_F;
+    tile_shape(d.precision, g.nact, &gs.tx, &gs.ty);
+    gs.tiles_x = (d.n[0] + gs.tx - 1) / gs.tx;
+    gs.tiles_y = (d.n[1] + gs.ty - 1) / gs.ty;
+    int zc = d.z_chunk;
+    if (zc <= 0) {
+        // enough CTAs to fill the GPU several times over, but long enough z runs to amortise the
+        // 6-plane pipeline start-up of each chunk
+        long long tiles = (long long)gs.tiles_x * gs.tiles_y;
+        zc = d.n[2];
+        while (zc > 32 && tiles * ((d.n[2] + zc - 1) / zc) < 152LL * 8) zc = (zc + 1) / 2;
+    }
+    gs.z_chunk = std::max(1, std::min(zc, d.n[2]));
+}
+
+rhd_status dalloc(rhd_ctx* ctx, void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? RHD_ERR_OOM : RHD_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return RHD_OK;
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_grid(GridState& gs)
+{
+    for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < 4; ++q) dfree(gs.U[b][q]);
+    dfree(gs.T);
+    dfree(gs.rho);
+    for (int d = 0; d < 3; ++d) {
+        dfree(gs.v[d]);
+        dfree(gs.v32[d]);
+    }
+    dfree(gs.kP);
+    dfree(gs.kF);
+    dfree(gs.j);
+    dfree(gs.rho32);
+    dfree(gs.kP32);
+    dfree(gs.kF32);
+    dfree(gs.j32);
+}
+
+void clear_graphs(rhd_ctx* ctx)
+{
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
+rhd_status alloc_grid(rhd_ctx* ctx, GridState& gs)
+{
+    size_t bytes = sizeof(double) * (size_t)gs.ncell;
+    for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < 4; ++q) {
+            rhd_status st = dalloc(ctx, (void**)&gs.U[b][q], bytes);
+            if (st) return st;
+        }
+    rhd_status st = dalloc(ctx, (void**)&gs.T, bytes);
+    if (st) return st;
+    st = dalloc(ctx, (void**)&gs.rho, bytes);
+    if (st) return st;
+    if (gs.desc.precision == RHD_SPLIT) {
+        st = dalloc(ctx, (void**)&gs.rho32, sizeof(float) * (size_t)gs.ncell);
+        if (st) return st;
+    }
+    return RHD_OK;
+}
+
+rhd_status common_init(rhd_ctx* ctx)
+{
+    RHD_CUDA(ctx, cudaGetDevice(&ctx->device));
+    RHD_CUDA(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (ctx->user_stream == nullptr || ctx->user_stream == cudaStreamLegacy || ctx->user_stream == cudaStreamPerThread) {
+        RHD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    } else {
+        ctx->stream = ctx->user_stream;
+    }
+    RHD_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    RHD_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
+    rhd_status st = dalloc(ctx, (void**)&ctx->dstats, sizeof(DevStats));
+    if (st) return st;
+    RHD_CUDA(ctx, cudaMemset(ctx->dstats, 0, sizeof(DevStats)));
+    return RHD_OK;
+}
+
+void destroy_ctx(rhd_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    clear_graphs(ctx);
+    for (auto& gs : ctx->grids) free_grid(gs);
+    dfree(ctx->dstats);
+    dfree(ctx->red_partials);
+    dfree(ctx->red_out);
+    dfree(ctx->d_egrids[0]);
+    dfree(ctx->d_egrids[1]);
+    dfree(ctx->d_counter);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->stream && ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+// copy a host or device FP64 array into a device buffer (on the library stream)
+rhd_status put(rhd_ctx* ctx, double* dst, const double* src, long long n, int on_device)
+{
+    RHD_CUDA(ctx, cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    return RHD_OK;
+}
+
+rhd_status set_optional(rhd_ctx* ctx, GridState& gs, double*& buf, float*& buf32, bool& has, const double* src,
+                        int on_device)
+{
+    if (!src) {
+        has = false;
+        return RHD_OK;
+    }
+    size_t bytes = sizeof(double) * (size_t)gs.ncell;
+    if (!buf) {
+        rhd_status st = dalloc(ctx, (void**)&buf, bytes);
+        if (st) return st;
+    }
+    rhd_status st = put(ctx, buf, src, gs.ncell, on_device);
+    if (st) return st;
+    if (gs.desc.precision == RHD_SPLIT) {
+        if (!buf32) {
+            st = dalloc(ctx, (void**)&buf32, sizeof(float) * (size_t)gs.ncell);
+            if (st) return st;
+        }
+        RHD_CUDA(ctx, launch_to_float(buf32, buf, gs.ncell, ctx->stream));
+    }
+    has = true;
+    return RHD_OK;
+}
+
+rhd_status set_gas(rhd_ctx* ctx, GridState& gs, const double* rho, const double* T, const double* vx,
+                   const double* vy, const double* vz, const double* kP, const double* kF, const double* j,
+                   int on_device)
+{
+    if (!rho || !T) return fail(ctx, RHD_ERR_ARG, "rho and T are required");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    if ((st = put(ctx, gs.rho, rho, gs.ncell, on_device))) return st;
+    if ((st = put(ctx, gs.T, T, gs.ncell, on_device))) return st;
+    if (gs.desc.precision == RHD_SPLIT) RHD_CUDA(ctx, launch_to_float(gs.rho32, gs.rho, gs.ncell, ctx->stream));
+    const double* vin[3] = {vx, vy, vz};
+    bool hv[3];
+    for (int d = 0; d < 3; ++d)
+        if ((st = set_optional(ctx, gs, gs.v[d], gs.v32[d], hv[d], vin[d], on_device))) return st;
+    gs.has_v = hv[0] || hv[1] || hv[2];
+    // velocity components that were not given are zero: keep them as absent
+    for (int d = 0; d < 3; ++d)
+        if (!hv[d]) {
+            dfree(gs.v[d]);
+            dfree(gs.v32[d]);
+        }
+    if ((st = set_optional(ctx, gs, gs.kP, gs.kP32, gs.has_kP, kP, on_device))) return st;
+    if ((st = set_optional(ctx, gs, gs.kF, gs.kF32, gs.has_kF, kF, on_device))) return st;
+    if ((st = set_optional(ctx, gs, gs.j, gs.j32, gs.has_j, j, on_device))) return st;
+    gs.has_gas = true;
+    clear_graphs(ctx);  // array pointers may have changed
+    return leave(ctx);
+}
+
+rhd_status set_moments(rhd_ctx* ctx, GridState& gs, const double* E, const double* Fx, const double* Fy,
+                       const double* Fz, int on_device)
+{
+    if (!E || !Fx || !Fy || !Fz) return fail(ctx, RHD_ERR_ARG, "E, Fx, Fy, Fz are required");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    double** U = gs.U[ctx->cur];
+    if ((st = put(ctx, U[0], E, gs.ncell, on_device))) return st;
+    const double* F[3] = {Fx, Fy, Fz};
+    for (int d = 0; d < 3; ++d) {
+        if (on_device) {
+            RHD_CUDA(ctx, launch_scale_copy(U[1 + d], F[d], gs.desc.c, gs.ncell, ctx->stream));
+        } else {
+            if ((st = put(ctx, U[1 + d], F[d], gs.ncell, 0))) return st;
+            RHD_CUDA(ctx, launch_scale_copy(U[1 + d], U[1 + d], gs.desc.c, gs.ncell, ctx->stream));
+        }
+    }
+    gs.has_moments = true;
+    return leave(ctx);
+}
+
+rhd_status get_moments(rhd_ctx* ctx, GridState& gs, double* E, double* Fx, double* Fy, double* Fz, int on_device)
+{
+    if (!E || !Fx || !Fy || !Fz) return fail(ctx, RHD_ERR_ARG, "E, Fx, Fy, Fz are required");
+    if (!gs.has_moments) return fail(ctx, RHD_ERR_STATE, "moments were never set");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    double** U = gs.U[ctx->cur];
+    double** W = gs.U[1 - ctx->cur];  // scratch: the other half of the ping-pong pair
+    size_t bytes = sizeof(double) * (size_t)gs.ncell;
+    double* F[3] = {Fx, Fy, Fz};
+    if (on_device) {
+        RHD_CUDA(ctx, cudaMemcpyAsync(E, U[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int d = 0; d < 3; ++d) RHD_CUDA(ctx, launch_scale_copy(F[d], U[1 + d], -gs.desc.c, gs.ncell, ctx->stream));
+    } else {
+        for (int d = 0; d < 3; ++d) RHD_CUDA(ctx, launch_scale_copy(W[1 + d], U[1 + d], -gs.desc.c, gs.ncell, ctx->stream));
+        RHD_CUDA(ctx, cudaMemcpyAsync(E, U[0], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        for (int d = 0; d < 3; ++d) RHD_CUDA(ctx, cudaMemcpyAsync(F[d], W[1 + d], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if ((st = leave(ctx))) return st;
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RHD_OK;
+}
+
+rhd_status get_T(rhd_ctx* ctx, GridState& gs, double* T, int on_device)
+{
+    if (!T) return fail(ctx, RHD_ERR_ARG, "T is required");
+    if (!gs.has_gas) return fail(ctx, RHD_ERR_STATE, "gas state was never set");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    RHD_CUDA(ctx, cudaMemcpyAsync(T, gs.T, sizeof(double) * (size_t)gs.ncell,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if ((st = leave(ctx))) return st;
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RHD_OK;
+}
+
+StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double dt)
+{
+    StepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.g = gs.gp;
+    GridArrays& a = p.a;
+    a.E = gs.U[src][0];
+    for (int d = 0; d < 3; ++d) a.G[d] = gs.U[src][1 + d];
+    a.Eo = gs.U[1 - src][0];
+    for (int d = 0; d < 3; ++d) a.Go[d] = gs.U[1 - src][1 + d];
+    a.T = gs.T;
+    a.rho = gs.rho;
+    for (int d = 0; d < 3; ++d) {
+        a.v[d] = gs.v[d];
+        a.v32[d] = gs.v32[d];
+    }
+    a.kP = gs.has_kP ? gs.kP : nullptr;
+    a.kF = gs.has_kF ? gs.kF : nullptr;
+    a.j = gs.has_j ? gs.j : nullptr;
+    a.rho32 = gs.rho32;
+    a.kP32 = gs.has_kP ? gs.kP32 : nullptr;
+    a.kF32 = gs.has_kF ? gs.kF32 : nullptr;
+    a.j32 = gs.has_j ? gs.j32 : nullptr;
+    p.chat = chat;
+    p.dt = dt;
+    p.z_chunk = gs.z_chunk;
+    p.tiles_x = gs.tiles_x;
+    p.tiles_y = gs.tiles_y;
+    p.stats = ctx->dstats;
+    return p;
+}
+
+rhd_status check_dt(rhd_ctx* ctx, const GridState& gs, double chat, double dt)
+{
+    if (!finite_pos(chat)) return fail(ctx, RHD_ERR_ARG, "chat must be positive and finite");
+    if (!(std::isfinite(dt) && dt >= 0.0)) return fail(ctx, RHD_ERR_ARG, "dt must be finite and >= 0");
+    if (chat > gs.desc.c * (1.0 + 1e-12)) return fail(ctx, RHD_ERR_CFL, "chat must not exceed c");
+    double dxmin = INFINITY;
+    for (int k = 0; k < 3; ++k)
+        if (gs.desc.n[k] > 1) dxmin = std::min(dxmin, gs.desc.dx[k]);
+    if (std::isfinite(dxmin) && dt > gs.desc.cfl * dxmin / chat * (1.0 + 1e-12))
+        return fail(ctx, RHD_ERR_CFL, "dt exceeds cfl * min(dx) / chat");
+    return RHD_OK;
+}
+
+rhd_status launch_one(rhd_ctx* ctx, GridState& gs, int src, double chat, double dt)
+{
+    StepParams p = step_params(ctx, gs, src, chat, dt);
+    cudaError_t e = gs.desc.precision == RHD_SPLIT ? launch_subcycle_split(p, ctx->stream)
+                                                    : launch_subcycle_fp64(p, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("subcycle launch: ") + cudaGetErrorString(e));
+    return RHD_OK;
+}
+
+// Run n_sub steps: replay a cached graph (or issue the launches directly).
+template <typename LaunchFn>
+rhd_status run_steps(rhd_ctx* ctx, int n_sub, double chat, double dt, bool use_graph, LaunchFn&& launch)
+{
+    if (!use_graph) {
+        for (int s = 0; s < n_sub; ++s) {
+            rhd_status st = launch((ctx->cur + s) & 1);
+            if (st) return st;
+        }
+        return RHD_OK;
+    }
+    for (auto& g : ctx->graphs)
+        if (g.n_sub == n_sub && g.start == ctx->cur && g.chat == chat && g.dt == dt) {
+            g.stamp = ++ctx->stamp;
+            RHD_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+            return RHD_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    RHD_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    rhd_status st = RHD_OK;
+    for (int s = 0; s < n_sub && st == RHD_OK; ++s) st = launch((ctx->cur + s) & 1);
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    if (ctx->graphs.size() >= 6) {
+        auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                   [](const GraphEntry& a, const GraphEntry& b) { return a.stamp < b.stamp; });
+        cudaGraphExecDestroy(it->exec);
+        ctx->graphs.erase(it);
+    }
+    ctx->graphs.push_back({n_sub, ctx->cur, chat, dt, exec, ++ctx->stamp});
+    RHD_CUDA(ctx, cudaGraphLaunch(exec, ctx->stream));
+    return RHD_OK;
+}
+
+rhd_status ensure_reduce(rhd_ctx* ctx, long long n)
+{
+    int nb = reduce_blocks_for(n);
+    if (ctx->red_partials && ctx->red_blocks >= nb) return RHD_OK;
+    dfree(ctx->red_partials);
+    dfree(ctx->red_out);
+    rhd_status st = dalloc(ctx, (void**)&ctx->red_partials, sizeof(double) * 5 * (size_t)nb);
+    if (st) return st;
+    st = dalloc(ctx, (void**)&ctx->red_out, sizeof(double) * 5);
+    if (st) return st;
+    ctx->red_blocks = nb;
+    return RHD_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+int rhd_abi_version(void) { return RHD_ABI_VERSION; }
+int rhd_built_arch(void) { return 103; }
+
+const char* rhd_last_error(const rhd_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+rhd_status rhd_init_grid(rhd_ctx** out, const rhd_grid_desc* d)
+{
+    if (!out) return fail(nullptr, RHD_ERR_ARG, "out is NULL");
+    rhd_status st = validate_desc(nullptr, d);
+    if (st) return st;
+    rhd_ctx* ctx = new (std::nothrow) rhd_ctx();
+    if (!ctx) return fail(nullptr, RHD_ERR_OOM, "host allocation failed");
+    ctx->user_stream = (cudaStream_t)d->cuda_stream;
+    st = common_init(ctx);
+    if (!st) {
+        ctx->grids.resize(1);
+        GridState& gs = ctx->grids[0];
+        gs.desc = *d;
+        gs.ncell = (long long)d->n[0] * d->n[1] * d->n[2];
+        fill_params(gs);
+        st = alloc_grid(ctx, gs);
+    }
+    if (st) {
+        g_init_error = ctx->err;
+        destroy_ctx(ctx);
+        return st;
+    }
+    *out = ctx;
+    return RHD_OK;
+}
+
+rhd_status rhd_destroy(rhd_ctx* ctx)
+{
+    destroy_ctx(ctx);
+    return RHD_OK;
+}
+
+rhd_status rhd_set_gas_state(rhd_ctx* ctx, const double* rho, const double* T, const double* vx, const double* vy,
+                             const double* vz, const double* kP, const double* kF, const double* j, int on_device)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_set_gas_state on an ensemble");
+    return set_gas(ctx, ctx->grids[0], rho, T, vx, vy, vz, kP, kF, j, on_device);
+}
+
+rhd_status rhd_set_moments(rhd_ctx* ctx, const double* E, const double* Fx, const double* Fy, const double* Fz,
+                           int on_device)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_set_moments on an ensemble");
+    return set_moments(ctx, ctx->grids[0], E, Fx, Fy, Fz, on_device);
+}
+
+rhd_status rhd_set_dirichlet(rhd_ctx* ctx, int face, const double state[4])
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (face < 0 || face > 5 || !state) return fail(ctx, RHD_ERR_ARG, "face must be in [0, 5] and state non-NULL");
+    for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(state[q])) return fail(ctx, RHD_ERR_ARG, "Dirichlet state must be finite");
+    for (auto& gs : ctx->grids) {
+        double* dst = (face & 1) ? gs.gp.dir_hi[face >> 1] : gs.gp.dir_lo[face >> 1];
+        dst[0] = state[0];
+        for (int q = 1; q < 4; ++q) dst[q] = state[q] / gs.desc.c;
+    }
+    clear_graphs(ctx);
+    return RHD_OK;
+}
+
+rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double dt)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_subcycle on an ensemble");
+    if (n_sub < 0) return fail(ctx, RHD_ERR_ARG, "n_sub must be >= 0");
+    GridState& gs = ctx->grids[0];
+    rhd_status st = check_dt(ctx, gs, chat, dt);
+    if (st) return st;
+    if (!gs.has_moments || !gs.has_gas) return fail(ctx, RHD_ERR_STATE, "set the moments and the gas state first");
+    if (n_sub == 0) return RHD_OK;
+    if ((st = enter(ctx))) return st;
+    bool use_graph = !(gs.desc.flags & RHD_FLAG_NO_GRAPH);
+    st = run_steps(ctx, n_sub, chat, dt, use_graph, [&](int src) { return launch_one(ctx, gs, src, chat, dt); });
+    if (st) return st;
+    ctx->cur = (ctx->cur + n_sub) & 1;
+    ctx->n_subcycles += n_sub;
+    return leave(ctx);
+}
+
+rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas)
+{
+    (void)dt_gas;
+    return fail(ctx, RHD_ERR_UNSUPPORTED, "the gas step is not part of this library");
+}
+
+rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, double* Fz, int on_device)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_get_moments on an ensemble");
+    return get_moments(ctx, ctx->grids[0], E, Fx, Fy, Fz, on_device);
+}
+
+rhd_status rhd_get_gas_state(rhd_ctx* ctx, double* T, int on_device)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_get_gas_state on an ensemble");
+    return get_T(ctx, ctx->grids[0], T, on_device);
+}
+
+rhd_status rhd_reset_stats(rhd_ctx* ctx)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    RHD_CUDA(ctx, cudaMemsetAsync(ctx->dstats, 0, sizeof(DevStats), ctx->stream));
+    ctx->n_subcycles = 0;
+    return leave(ctx);
+}
+
+rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
+{
+    if (!ctx || !out) return fail(ctx, RHD_ERR_ARG, "ctx and out are required");
+    std::memset(out, 0, sizeof(*out));
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    DevStats hs;
+    RHD_CUDA(ctx, cudaMemcpyAsync(&hs, ctx->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, ctx->stream));
+    double sums[5] = {0, 0, 0, 0, 0};
+    for (auto& gs : ctx->grids) {
+        if (!gs.has_moments) continue;
+        if ((st = ensure_reduce(ctx, gs.ncell))) return st;
+        double** U = gs.U[ctx->cur];
+        int nb = reduce_blocks_for(gs.ncell);
+        RHD_CUDA(ctx, launch_reduce_state(U[0], U[1], U[2], U[3], gs.ncell, ctx->red_partials, nb, ctx->stream));
+        RHD_CUDA(ctx, launch_reduce_finish(ctx->red_partials, nb, ctx->red_out, ctx->stream));
+        double h[5];
+        RHD_CUDA(ctx, cudaMemcpyAsync(h, ctx->red_out, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        sums[0] += h[0];
+        for (int d = 0; d < 3; ++d) sums[1 + d] += gs.desc.c * h[1 + d];
+        sums[4] = std::max(sums[4], h[4]);
+    }
+    if ((st = leave(ctx))) return st;
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    out->n_subcycles = ctx->n_subcycles;
+    out->n_realizability_fix = (int64_t)hs.n_fix;
+    out->n_face_fallback = (int64_t)hs.n_face;
+    out->n_theta_fallback = (int64_t)hs.n_theta;
+    out->n_newton_fallback = (int64_t)hs.n_newton_fb;
+    out->n_nonfinite = (int64_t)hs.n_nonfinite;
+    out->newton_iter_max = (int32_t)hs.newton_iter_max;
+    out->sum_E = sums[0];
+    for (int d = 0; d < 3; ++d) out->sum_F[d] = sums[1 + d];
+    out->max_f = sums[4];
+    return out->n_nonfinite ? RHD_ERR_NONFINITE : RHD_OK;
+}
+
+rhd_status rhd_synchronize(rhd_ctx* ctx, int timeout_ms)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) return RHD_OK;
+        if (e != cudaErrorNotReady) return fail(ctx, RHD_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+        if (timeout_ms >= 0) {
+            auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms >= timeout_ms) return fail(ctx, RHD_ERR_TIMEOUT, "stream still busy after the timeout");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// ensemble
+// ---------------------------------------------------------------------------------------------
+rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* descs)
+{
+    if (!out || !descs || n_grids < 1) return fail(nullptr, RHD_ERR_ARG, "out, descs and n_grids >= 1 are required");
+    for (int i = 0; i < n_grids; ++i) {
+        rhd_status st = validate_desc(nullptr, descs + i);
+        if (st) return st;
+        if (count_active(descs[i]) != 3) return fail(nullptr, RHD_ERR_ARG, "ensemble grids must be 3D");
+        const rhd_grid_desc& a = descs[0];
+        const rhd_grid_desc& b = descs[i];
+        if (a.precision != b.precision || a.exchange != b.exchange || a.limiter != b.limiter ||
+            a.closure != b.closure || a.speeds != b.speeds)
+            return fail(nullptr, RHD_ERR_ARG, "ensemble grids must share precision, exchange, limiter, closure, speeds");
+    }
+    rhd_ctx* ctx = new (std::nothrow) rhd_ctx();
+    if (!ctx) return fail(nullptr, RHD_ERR_OOM, "host allocation failed");
+    ctx->ensemble = true;
+    ctx->user_stream = (cudaStream_t)descs[0].cuda_stream;
+    rhd_status st = common_init(ctx);
+    if (!st) {
+        ctx->grids.resize(n_grids);
+        long long items = 0;
+        for (int i = 0; i < n_grids && !st; ++i) {
+            GridState& gs = ctx->grids[i];
+            gs.desc = descs[i];
+            gs.ncell = (long long)descs[i].n[0] * descs[i].n[1] * descs[i].n[2];
+            fill_params(gs);
+            st = alloc_grid(ctx, gs);
+        }
+        // one z chunk for all grids (the largest grid's automatic choice)
+        int zc = descs[0].z_chunk > 0 ? descs[0].z_chunk : 32;
+        for (auto& gs : ctx->grids) gs.z_chunk = zc;
+        for (auto& gs : ctx->grids)
+            items += (long long)gs.tiles_x * gs.tiles_y * ((gs.desc.n[2] + zc - 1) / zc);
+        ctx->n_items = items;
+        if (!st) st = dalloc(ctx, (void**)&ctx->d_egrids[0], sizeof(EnsembleGrid) * (size_t)n_grids);
+        if (!st) st = dalloc(ctx, (void**)&ctx->d_egrids[1], sizeof(EnsembleGrid) * (size_t)n_grids);
+        if (!st) st = dalloc(ctx, (void**)&ctx->d_counter, sizeof(unsigned long long));
+        if (!st) {
+            int per_sm = descs[0].precision == RHD_SPLIT ? ensemble_ctas_per_sm_split() : ensemble_ctas_per_sm_fp64();
+            ctx->ens_ctas = per_sm * ctx->num_sms;
+        }
+    }
+    if (st) {
+        g_init_error = ctx->err;
+        destroy_ctx(ctx);
+        return st;
+    }
+    *out = ctx;
+    return RHD_OK;
+}
+
+static rhd_status ens_grid(rhd_ctx* ctx, int grid, GridState** gs)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (!ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not an ensemble context");
+    if (grid < 0 || grid >= (int)ctx->grids.size()) return fail(ctx, RHD_ERR_ARG, "grid index out of range");
+    *gs = &ctx->grids[grid];
+    return RHD_OK;
+}
+
+rhd_status rhd_ensemble_set_gas_state(rhd_ctx* ctx, int grid, const double* rho, const double* T, const double* vx,
+                                      const double* vy, const double* vz, const double* kP, const double* kF,
+                                      const double* j, int on_device)
+{
+    GridState* gs;
+    rhd_status st = ens_grid(ctx, grid, &gs);
+    if (st) return st;
+    return set_gas(ctx, *gs, rho, T, vx, vy, vz, kP, kF, j, on_device);
+}
+
+rhd_status rhd_ensemble_set_moments(rhd_ctx* ctx, int grid, const double* E, const double* Fx, const double* Fy,
+                                    const double* Fz, int on_device)
+{
+    GridState* gs;
+    rhd_status st = ens_grid(ctx, grid, &gs);
+    if (st) return st;
+    return set_moments(ctx, *gs, E, Fx, Fy, Fz, on_device);
+}
+
+rhd_status rhd_ensemble_get_moments(rhd_ctx* ctx, int grid, double* E, double* Fx, double* Fy, double* Fz,
+                                    int on_device)
+{
+    GridState* gs;
+    rhd_status st = ens_grid(ctx, grid, &gs);
+    if (st) return st;
+    return get_moments(ctx, *gs, E, Fx, Fy, Fz, on_device);
+}
+
+rhd_status rhd_ensemble_get_gas_state(rhd_ctx* ctx, int grid, double* T, int on_device)
+{
+    GridState* gs;
+    rhd_status st = ens_grid(ctx, grid, &gs);
+    if (st) return st;
+    return get_T(ctx, *gs, T, on_device);
+}
+
+rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const double* dt_per_grid)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (!ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not an ensemble context");
+    if (n_sub < 0 || !dt_per_grid) return fail(ctx, RHD_ERR_ARG, "n_sub >= 0 and dt_per_grid are required");
+    int ng = (int)ctx->grids.size();
+    for (int i = 0; i < ng; ++i) {
+        rhd_status st = check_dt(ctx, ctx->grids[i], chat, dt_per_grid[i]);
+        if (st) return st;
+        if (!ctx->grids[i].has_moments || !ctx->grids[i].has_gas)
+            return fail(ctx, RHD_ERR_STATE, "set the moments and gas state of every grid first");
+    }
+    if (n_sub == 0) return RHD_OK;
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    // per-parity grid tables (src = 0 / 1)
+    std::vector<EnsembleGrid> eg(ng);
+    double dt_sig = 0.0;
+    for (int src = 0; src < 2; ++src) {
+        long long first = 0;
+        for (int i = 0; i < ng; ++i) {
+            GridState& gs = ctx->grids[i];
+            StepParams p = step_params(ctx, gs, src, chat, dt_per_grid[i]);
+            eg[i].g = p.g;
+            eg[i].a = p.a;
+            eg[i].dt = dt_per_grid[i];
+            eg[i].tiles_x = gs.tiles_x;
+            eg[i].tiles_y = gs.tiles_y;
+            eg[i].tiles_z = (gs.desc.n[2] + gs.z_chunk - 1) / gs.z_chunk;
+            eg[i].first_item = first;
+            first += (long long)eg[i].tiles_x * eg[i].tiles_y * eg[i].tiles_z;
+            if (src == 0) dt_sig = dt_sig * 1.000000119 + dt_per_grid[i];
+        }
+        RHD_CUDA(ctx, cudaMemcpyAsync(ctx->d_egrids[src], eg.data(), sizeof(EnsembleGrid) * (size_t)ng,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    }
+    const bool split = ctx->grids[0].desc.precision == RHD_SPLIT;
+    auto launch = [&](int src) -> rhd_status {
+        RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+        EnsembleParams ep;
+        std::memset(&ep, 0, sizeof(ep));
+        ep.grids = ctx->d_egrids[src];
+        ep.n_grids = ng;
+        ep.n_items = ctx->n_items;
+        ep.chat = chat;
+        ep.z_chunk = ctx->grids[0].z_chunk;
+        ep.counter = ctx->d_counter;
+        ep.stats = ctx->dstats;
+        cudaError_t e = split ? launch_ensemble_split(ep, ctx->ens_ctas, ctx->stream)
+                              : launch_ensemble_fp64(ep, ctx->ens_ctas, ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("ensemble launch: ") + cudaGetErrorString(e));
+        return RHD_OK;
+    };
+    bool use_graph = !(ctx->grids[0].desc.flags & RHD_FLAG_NO_GRAPH);
+    st = run_steps(ctx, n_sub, chat, dt_sig, use_graph, launch);
+    if (st) return st;
+    ctx->cur = (ctx->cur + n_sub) & 1;
+    ctx->n_subcycles += n_sub;
+    return leave(ctx);
+}
+
+}  // extern "C"

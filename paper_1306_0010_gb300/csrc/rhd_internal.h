@@ -1,0 +1,108 @@
+// rhd_internal.h -- types shared by the host runtime and the kernels of librhd.so (not public).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rhd {
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
+enum { EX_FULL = 0, EX_ABSORB = 1, EX_EQUILIBRIUM = 2, EX_FROZEN_T = 3 };
+enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
+
+// Device-side event counters of the subcycles (zeroed by a reset).
+struct DevStats {
+    unsigned long long n_fix;
+    unsigned long long n_face;
+    unsigned long long n_theta;
+    unsigned long long n_newton_fb;
+    unsigned long long n_nonfinite;
+    unsigned int newton_iter_max;
+    unsigned int pad;
+};
+
+// Per-grid constants of one subcycle launch.
+struct GridParams {
+    int n[3];
+    int nact;                   // number of active directions (they are x, then y, then z)
+    double inv_dx[3];
+    int bc_lo[3], bc_hi[3];
+    double dir_lo[3][4];        // Dirichlet states (E, Gx, Gy, Gz), G = F/c
+    double dir_hi[3][4];
+    double c, a_rad, gamma, mu_over_kB;
+    double theta_F, theta_E, E_floor;
+    double kappa_P, kappa_F;
+    int kpow;
+    int exchange, beta_tau, limiter, closure, speeds;
+    // derived on the host: 1/c, (gamma - 1) mu/k_B, and FP32 copies used by the split path
+    double inv_c, gm1_mu;
+    float f_inv_c, f_gm1_mu, f_c, f_a_rad, f_theta_F, f_theta_E, f_E_floor, f_kappa_P, f_kappa_F;
+};
+
+// Device arrays of one grid.  FP32 copies of the frozen inputs are used by the split path.
+struct GridArrays {
+    const double* E;            // U^m
+    const double* G[3];
+    double* Eo;                 // U^{m+1}
+    double* Go[3];
+    double* T;                  // gas temperature: read (FROZEN_T), read+write in place (FULL)
+    const double* rho;
+    const double* v[3];         // NULL: zero velocity
+    const double* kP;           // NULL: opacity law
+    const double* kF;
+    const double* j;            // NULL: no emissivity
+    const float* rho32;
+    const float* v32[3];
+    const float* kP32;
+    const float* kF32;
+    const float* j32;
+};
+
+struct StepParams {
+    GridParams g;
+    GridArrays a;
+    double chat, dt;
+    int z_chunk;                // planes per CTA
+    int tiles_x, tiles_y;       // tile grid in x, y
+    DevStats* stats;
+};
+
+// Ensemble work items: (grid, tile) pairs handed out by a global counter.
+struct EnsembleGrid {
+    GridParams g;
+    GridArrays a;
+    double dt;
+    int tiles_x, tiles_y, tiles_z;
+    long long first_item;       // prefix sum of tiles over the grids before this one
+};
+
+struct EnsembleParams {
+    const EnsembleGrid* grids;  // device array
+    int n_grids;
+    long long n_items;
+    double chat;
+    int z_chunk;
+    unsigned long long* counter;  // work-queue head, reset before each launch
+    DevStats* stats;
+};
+
+// Launch wrappers (defined in the kernel translation units).
+cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s);
+cudaError_t launch_subcycle_split(const StepParams& p, cudaStream_t s);
+cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);
+cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
+int ensemble_ctas_per_sm_fp64();
+int ensemble_ctas_per_sm_split();
+
+// Tile geometry chosen per precision and dimensionality.
+void tile_shape(int precision, int nact, int* tx, int* ty);
+
+// Auxiliary kernels (k_aux.cu).
+cudaError_t launch_scale_copy(double* dst, const double* src, double scale, long long n, cudaStream_t s);
+cudaError_t launch_to_float(float* dst, const double* src, long long n, cudaStream_t s);
+cudaError_t launch_reduce_state(const double* E, const double* G0, const double* G1, const double* G2,
+                                long long n, double* partials, int n_blocks, cudaStream_t s);
+cudaError_t launch_reduce_finish(const double* partials, int n_blocks, double* out5, cudaStream_t s);
+int reduce_blocks_for(long long n);
+
+}  // namespace rhd

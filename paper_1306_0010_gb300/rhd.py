@@ -1,0 +1,355 @@
+"""ctypes binding of librhd.so (argument marshalling only; every step of the radiation subcycle runs
+in the library's CUDA kernels).
+
+The functions keep the C names (rhd_init_grid, rhd_set_gas_state, rhd_radiation_subcycle, ...)
+through `lib()`, and the classes Grid and Ensemble wrap a context.  Arrays may be numpy float64
+arrays or torch tensors: CUDA tensors are passed as device pointers (on_device = 1), CPU tensors
+(pinned or not) as host pointers.  There is no CPU fallback: if the library is missing the import
+of a context raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librhd.so")
+
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_CFL, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+STATUS_NAMES = {0: "RHD_OK", 1: "RHD_ERR_ARG", 2: "RHD_ERR_STATE", 3: "RHD_ERR_CUDA", 4: "RHD_ERR_OOM",
+                5: "RHD_ERR_CFL", 6: "RHD_ERR_NONFINITE", 7: "RHD_ERR_TIMEOUT", 8: "RHD_ERR_UNSUPPORTED"}
+BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3}
+EXCHANGE = {"full": 0, "absorb": 1, "equilibrium": 2, "frozen_t": 3}
+LIMITER = {"minmod": 0, "mc": 1, "none": 2}
+CLOSURE = {"m1": 0, "p1": 1}
+SPEEDS = {"m1": 0, "fixed": 1}
+PRECISION = {"fp64": 0, "split": 1}
+FLAG_NO_GRAPH = 1
+
+
+class RhdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("dx", ctypes.c_double * 3),
+        ("bc_lo", ctypes.c_int * 3),
+        ("bc_hi", ctypes.c_int * 3),
+        ("c", ctypes.c_double),
+        ("a_rad", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("mu_over_kB", ctypes.c_double),
+        ("theta_F", ctypes.c_double),
+        ("theta_E", ctypes.c_double),
+        ("E_floor", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("exchange", ctypes.c_int),
+        ("beta_tau", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("closure", ctypes.c_int),
+        ("speeds", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("flags", ctypes.c_int),
+        ("z_chunk", ctypes.c_int),
+        ("kappa_P", ctypes.c_double),
+        ("kappa_F", ctypes.c_double),
+        ("kappa_rho_pow", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n_subcycles", ctypes.c_int64),
+        ("n_realizability_fix", ctypes.c_int64),
+        ("n_face_fallback", ctypes.c_int64),
+        ("n_theta_fallback", ctypes.c_int64),
+        ("n_newton_fallback", ctypes.c_int64),
+        ("n_nonfinite", ctypes.c_int64),
+        ("newton_iter_max", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("sum_E", ctypes.c_double),
+        ("sum_F", ctypes.c_double * 3),
+        ("max_f", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "sum_F")}
+        d["sum_F"] = tuple(self.sum_F)
+        return d
+
+
+# the entry points declared in include/rhd.h, with their ctypes signatures
+_P = ctypes.c_void_p
+_CTXP = ctypes.POINTER(ctypes.c_void_p)
+_SIGS = {
+    "rhd_init_grid": (ctypes.c_int, [_CTXP, ctypes.POINTER(GridDesc)]),
+    "rhd_set_gas_state": (ctypes.c_int, [_P] + [_P] * 8 + [ctypes.c_int]),
+    "rhd_set_moments": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
+    "rhd_set_dirichlet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "rhd_radiation_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "rhd_gas_step": (ctypes.c_int, [_P, ctypes.c_double]),
+    "rhd_get_moments": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
+    "rhd_get_gas_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "rhd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
+    "rhd_reset_stats": (ctypes.c_int, [_P]),
+    "rhd_synchronize": (ctypes.c_int, [_P, ctypes.c_int]),
+    "rhd_last_error": (ctypes.c_char_p, [_P]),
+    "rhd_destroy": (ctypes.c_int, [_P]),
+    "rhd_ensemble_create": (ctypes.c_int, [_CTXP, ctypes.c_int, ctypes.POINTER(GridDesc)]),
+    "rhd_ensemble_set_gas_state": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8 + [ctypes.c_int]),
+    "rhd_ensemble_set_moments": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 4 + [ctypes.c_int]),
+    "rhd_ensemble_get_moments": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 4 + [ctypes.c_int]),
+    "rhd_ensemble_get_gas_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
+    "rhd_ensemble_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "rhd_abi_version": (ctypes.c_int, []),
+    "rhd_built_arch": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load librhd.so (built in-tree by paper_1306_0010_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"librhd.so not found at {p}: build it with paper_1306_0010_gb300.build.build()")
+        L = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st):
+    if st != OK:
+        msg = lib().rhd_last_error(ctx)
+        raise RhdError(st, msg.decode() if msg else "")
+
+
+def desc_struct(d: dict, stream=None) -> GridDesc:
+    s = GridDesc()
+    for k in range(3):
+        s.n[k] = int(d["n"][k])
+        s.dx[k] = float(d["dx"][k])
+        s.bc_lo[k] = BC[d["bc_lo"][k]]
+        s.bc_hi[k] = BC[d["bc_hi"][k]]
+    s.c = d["c"]
+    s.a_rad = d["a_rad"]
+    s.gamma = d["gamma"]
+    s.mu_over_kB = d["mu_over_kB"]
+    s.theta_F = d["theta_F"]
+    s.theta_E = d["theta_E"]
+    s.E_floor = d["E_floor"]
+    s.cfl = d.get("cfl", 0.4)
+    s.exchange = EXCHANGE[d["exchange"]]
+    s.beta_tau = int(bool(d["beta_tau"]))
+    s.limiter = LIMITER[d["limiter"]]
+    s.closure = CLOSURE[d["closure"]]
+    s.speeds = SPEEDS[d["speeds"]]
+    s.precision = PRECISION[d.get("precision", "fp64")]
+    s.flags = int(d.get("flags", 0))
+    s.z_chunk = int(d.get("z_chunk", 0))
+    s.kappa_P = d["kappa_P"]
+    s.kappa_F = d["kappa_F"]
+    s.kappa_rho_pow = int(d["kappa_rho_pow"])
+    s.cuda_stream = stream
+    return s
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, n, writable=False):
+    """(pointer, on_device) of an FP64 array of n elements; None -> NULL."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        import torch
+
+        if x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != n:
+            raise ValueError("tensors must be contiguous float64 with one value per cell")
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda)
+    if not isinstance(x, np.ndarray) or x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != n:
+        raise ValueError("arrays must be C-contiguous float64 with one value per cell")
+    if writable and not x.flags["WRITEABLE"]:
+        raise ValueError("output array is read-only")
+    return ctypes.c_void_p(x.ctypes.data), 0
+
+
+def _same_residency(ptrs):
+    flags = {od for p, od in ptrs if p is not None}
+    if len(flags) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return flags.pop() if flags else 0
+
+
+class Grid:
+    """One grid: rhd_init_grid ... rhd_destroy."""
+
+    def __init__(self, desc: dict, stream=None):
+        self.desc = dict(desc)
+        self.n = tuple(int(v) for v in desc["n"])
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self._ctx = ctypes.c_void_p()
+        self._desc = desc_struct(desc, stream)
+        st = lib().rhd_init_grid(ctypes.byref(self._ctx), ctypes.byref(self._desc))
+        _check(None, st)
+
+    @property
+    def shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def close(self):
+        if self._ctx:
+            lib().rhd_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_gas_state(self, rho, T, vx=None, vy=None, vz=None, kP=None, kF=None, j=None):
+        ps = [_ptr(a, self.ncell) for a in (rho, T, vx, vy, vz, kP, kF, j)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_set_gas_state(self._ctx, *[p for p, _ in ps], od))
+
+    def set_moments(self, E, Fx, Fy, Fz):
+        ps = [_ptr(a, self.ncell) for a in (E, Fx, Fy, Fz)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_set_moments(self._ctx, *[p for p, _ in ps], od))
+
+    def set_dirichlet(self, face, state):
+        arr = (ctypes.c_double * 4)(*[float(v) for v in state])
+        _check(self._ctx, lib().rhd_set_dirichlet(self._ctx, int(face), arr))
+
+    def radiation_subcycle(self, n_sub, chat, dt):
+        _check(self._ctx, lib().rhd_radiation_subcycle(self._ctx, int(n_sub), float(chat), float(dt)))
+
+    def gas_step(self, dt_gas):
+        _check(self._ctx, lib().rhd_gas_step(self._ctx, float(dt_gas)))
+
+    def get_moments(self, E=None, Fx=None, Fy=None, Fz=None):
+        if E is None:
+            E, Fx, Fy, Fz = (np.empty(self.shape) for _ in range(4))
+        ps = [_ptr(a, self.ncell, writable=True) for a in (E, Fx, Fy, Fz)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_get_moments(self._ctx, *[p for p, _ in ps], od))
+        return {"E": E, "Fx": Fx, "Fy": Fy, "Fz": Fz}
+
+    def get_gas_state(self, T=None):
+        if T is None:
+            T = np.empty(self.shape)
+        p, od = _ptr(T, self.ncell, writable=True)
+        _check(self._ctx, lib().rhd_get_gas_state(self._ctx, p, od))
+        return T
+
+    def get_stats(self, allow_nonfinite=False):
+        s = Stats()
+        st = lib().rhd_get_stats(self._ctx, ctypes.byref(s))
+        if not (allow_nonfinite and st == ERR_NONFINITE):
+            _check(self._ctx, st)
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(self._ctx, lib().rhd_reset_stats(self._ctx))
+
+    def synchronize(self, timeout_ms=-1):
+        _check(self._ctx, lib().rhd_synchronize(self._ctx, int(timeout_ms)))
+
+    def load_case(self, case):
+        """Set the gas state and moments of a case dict (see workloads.py)."""
+        f = case["fields"]
+        self.set_gas_state(*(None if f.get(k) is None else np.ascontiguousarray(f[k], dtype=np.float64)
+                             for k in ("rho", "T", "vx", "vy", "vz", "kP", "kF", "j")))
+        self.set_moments(*(np.ascontiguousarray(f[k], dtype=np.float64) for k in ("E", "Fx", "Fy", "Fz")))
+        d = case["desc"]
+        for face in range(6):
+            dd, side = face // 2, face % 2
+            if (d["bc_hi"] if side else d["bc_lo"])[dd] == "dirichlet":
+                self.set_dirichlet(face, (d["dirichlet_hi"] if side else d["dirichlet_lo"])[dd])
+
+
+class Ensemble:
+    """Many independent grids advanced by one persistent launch per subcycle."""
+
+    def __init__(self, descs, stream=None):
+        self.descs = [dict(d) for d in descs]
+        self.shapes = [(int(d["n"][2]), int(d["n"][1]), int(d["n"][0])) for d in descs]
+        arr = (GridDesc * len(descs))(*[desc_struct(d, stream) for d in descs])
+        self._keep = arr
+        self._ctx = ctypes.c_void_p()
+        _check(None, lib().rhd_ensemble_create(ctypes.byref(self._ctx), len(descs), arr))
+
+    def close(self):
+        if self._ctx:
+            lib().rhd_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _n(self, g):
+        s = self.shapes[g]
+        return s[0] * s[1] * s[2]
+
+    def set_gas_state(self, g, rho, T, vx=None, vy=None, vz=None, kP=None, kF=None, j=None):
+        ps = [_ptr(a, self._n(g)) for a in (rho, T, vx, vy, vz, kP, kF, j)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_ensemble_set_gas_state(self._ctx, int(g), *[p for p, _ in ps], od))
+
+    def set_moments(self, g, E, Fx, Fy, Fz):
+        ps = [_ptr(a, self._n(g)) for a in (E, Fx, Fy, Fz)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_ensemble_set_moments(self._ctx, int(g), *[p for p, _ in ps], od))
+
+    def get_moments(self, g, E=None, Fx=None, Fy=None, Fz=None):
+        if E is None:
+            E, Fx, Fy, Fz = (np.empty(self.shapes[g]) for _ in range(4))
+        ps = [_ptr(a, self._n(g), writable=True) for a in (E, Fx, Fy, Fz)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_ensemble_get_moments(self._ctx, int(g), *[p for p, _ in ps], od))
+        return {"E": E, "Fx": Fx, "Fy": Fy, "Fz": Fz}
+
+    def get_gas_state(self, g, T=None):
+        if T is None:
+            T = np.empty(self.shapes[g])
+        p, od = _ptr(T, self._n(g), writable=True)
+        _check(self._ctx, lib().rhd_ensemble_get_gas_state(self._ctx, int(g), p, od))
+        return T
+
+    def subcycle(self, n_sub, chat, dts):
+        arr = (ctypes.c_double * len(dts))(*[float(v) for v in dts])
+        _check(self._ctx, lib().rhd_ensemble_subcycle(self._ctx, int(n_sub), float(chat), arr))
+
+    def get_stats(self, allow_nonfinite=False):
+        s = Stats()
+        st = lib().rhd_get_stats(self._ctx, ctypes.byref(s))
+        if not (allow_nonfinite and st == ERR_NONFINITE):
+            _check(self._ctx, st)
+        return s.as_dict()
+
+    def synchronize(self, timeout_ms=-1):
+        _check(self._ctx, lib().rhd_synchronize(self._ctx, int(timeout_ms)))
+
+    def load_case(self, g, case):
+        f = case["fields"]
+        self.set_gas_state(g, *(None if f.get(k) is None else np.ascontiguousarray(f[k], dtype=np.float64)
+                                for k in ("rho", "T", "vx", "vy", "vz", "kP", "kF", "j")))
+        self.set_moments(g, *(np.ascontiguousarray(f[k], dtype=np.float64) for k in ("E", "Fx", "Fy", "Fz")))

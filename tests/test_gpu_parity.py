@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+FP64 path: normwise L-infinity error <= 1e-12 per field (E scaled by max|E|, F by c max|E|,
+T by max|T|), the tolerance stated for the FP64 path.  Split path: the error bound stated per
+case (FP32 fluxes and closure; see the design notes for the derivation)."""
+import math
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1306_0010_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rhd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1306_0010_gb300 import build, rhd as binding
+
+    build.build()
+    binding.lib()
+    return binding
+
+
+def run_gpu(rhd, case, n_sub=None, desc_over=None):
+    desc = dict(case["desc"], **(desc_over or {}))
+    g = rhd.Grid(desc)
+    g.load_case(case)
+    g.radiation_subcycle(case["n_sub"] if n_sub is None else n_sub, case["chat"], case["dt"])
+    out = g.get_moments()
+    out["T"] = g.get_gas_state()
+    st = g.get_stats()
+    g.close()
+    return out, st
+
+
+def errors(out, ref, desc):
+    sE = float(np.max(np.abs(ref["E"])))
+    e = {"E": float(np.max(np.abs(out["E"] - ref["E"]))) / sE}
+    for k in ("Fx", "Fy", "Fz"):
+        e[k] = float(np.max(np.abs(out[k] - ref[k]))) / (desc["c"] * sE)
+    if desc["exchange"] == "full":
+        e["T"] = float(np.max(np.abs(out["T"] - ref["T"]))) / float(np.max(np.abs(ref["T"])))
+    return e
+
+
+FP64_CASES = [
+    dict(name="3d_periodic_full_bt", n=(16, 12, 10), bc="periodic", exchange="full", beta_tau=True, with_j=True),
+    dict(name="3d_ragged_mixed_bc", n=(20, 13, 9), exchange="equilibrium", limiter="mc",
+         bc=(["outflow", "reflect", "dirichlet"], ["reflect", "outflow", "outflow"]),
+         dirichlet=([[0.0] * 4, [0.0] * 4, [1.5, 0.2, 0.1, 2.0]], [[0.0] * 4] * 3)),
+    dict(name="3d_absorb_arrays", n=(18, 9, 11), bc="outflow", exchange="absorb", kP_array=True, with_j=True,
+         theta=0.51),
+    dict(name="3d_frozen_t_unlimited", n=(12, 10, 8), bc="periodic", exchange="frozen_t", limiter="none",
+         beta_tau=True, fmax=0.5),
+    dict(name="3d_p1_fixed", n=(10, 9, 8), bc="reflect", exchange="equilibrium", closure="p1", speeds="fixed"),
+    dict(name="3d_full_theta051", n=(14, 11, 7), bc="periodic", exchange="full", theta=0.51, kappa=40.0,
+         kappa_rho_pow=2),
+    dict(name="2d_outflow_full", n=(40, 30, 1), bc="outflow", exchange="full", beta_tau=True),
+    dict(name="2d_dirichlet_mc", n=(33, 17, 1), exchange="equilibrium", limiter="mc",
+         bc=(["dirichlet", "periodic", "periodic"], ["outflow", "periodic", "periodic"]),
+         dirichlet=([[1.0, 5.0, 3.0, 0.0], [0.0] * 4, [0.0] * 4], [[0.0] * 4] * 3)),
+    dict(name="1d_periodic_absorb", n=(200, 1, 1), bc="periodic", exchange="absorb", with_j=True),
+    dict(name="1d_reflect_full", n=(130, 1, 1), bc="reflect", exchange="full", beta_tau=True),
+]
+
+
+@pytest.mark.parametrize("kw", FP64_CASES, ids=[c["name"] for c in FP64_CASES])
+def test_fp64_parity_small(rhd, kw):
+    kw = dict(kw)
+    name = kw.pop("name")
+    n = kw.pop("n")
+    case = wl.parity_case(name, n, n_sub=4, seed=zlib.crc32(name.encode()) % 1000, **kw)
+    out, st = run_gpu(rhd, case)
+    ref, rst = orc.subcycles(case)
+    e = errors(out, ref, case["desc"])
+    assert max(e.values()) <= FP64_TOL, e
+    assert st["n_nonfinite"] == 0
+    assert st["n_realizability_fix"] == rst["n_realizability_fix"]
+    assert st["n_face_fallback"] == rst["n_face_fallback"]
+    assert st["n_theta_fallback"] == rst["n_theta_fallback"]
+
+
+def test_fp64_parity_several_z_chunks(rhd):
+    """CTAs that own a z chunk recompute the chunk's halo planes; the result must not depend on it."""
+    case = wl.parity_case("zchunk", (17, 9, 23), bc="periodic", exchange="full", beta_tau=True, n_sub=3, seed=5)
+    ref, _ = orc.subcycles(case)
+    for zc in (1, 3, 7, 23):
+        out, _ = run_gpu(rhd, case, desc_over={"z_chunk": zc})
+        assert max(errors(out, ref, case["desc"]).values()) <= FP64_TOL, zc
+
+
+def test_fp64_graph_and_plain_launches_are_bitwise_equal_and_deterministic(rhd):
+    case = wl.parity_case("graph", (24, 16, 12), bc="periodic", exchange="full", beta_tau=True, n_sub=5, seed=9)
+    a, _ = run_gpu(rhd, case)
+    b, _ = run_gpu(rhd, case, desc_over={"flags": rhd.FLAG_NO_GRAPH})
+    c, _ = run_gpu(rhd, case)
+    for k in ("E", "Fx", "Fy", "Fz", "T"):
+        assert np.array_equal(a[k], b[k]) and np.array_equal(a[k], c[k]), k
+
+
+def test_fp64_split_calls_equal_one_call(rhd):
+    """n_sub = 5 in one call equals 2 + 3 in two calls (ping-pong parity and graph cache)."""
+    case = wl.parity_case("calls", (16, 8, 8), bc="outflow", exchange="absorb", n_sub=5, seed=11)
+    one, _ = run_gpu(rhd, case)
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    g.radiation_subcycle(2, case["chat"], case["dt"])
+    g.radiation_subcycle(3, case["chat"], case["dt"])
+    two = g.get_moments()
+    g.close()
+    for k in ("E", "Fx", "Fy", "Fz"):
+        assert np.array_equal(one[k], two[k]), k
+
+
+def test_fp64_conservation_on_gpu(rhd):
+    """kappa = 0, no emissivity, periodic: total E and F are conserved to rounding (P4)."""
+    case = wl.parity_case("cons", (32, 24, 16), bc="periodic", exchange="equilibrium", kappa=0.0, fmax=0.5,
+                          n_sub=50, seed=3)
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    s0 = g.get_stats()
+    g.radiation_subcycle(case["n_sub"], case["chat"], case["dt"])
+    s1 = g.get_stats()
+    g.close()
+    scale = s0["sum_E"]
+    assert abs(s1["sum_E"] - s0["sum_E"]) <= 1e-13 * scale
+    for d in range(3):
+        assert abs(s1["sum_F"][d] - s0["sum_F"][d]) <= 1e-13 * scale * case["desc"]["c"]
+    assert s1["n_realizability_fix"] == 0
+
+
+def test_config1_linear_wave_fp64_full_run(rhd):
+    """Configuration 1 (1D, N = 512, tau = 1, chat = 10, 1000 subcycles) against the oracle."""
+    case = wl.config1(tau=1.0, mode="equilibrium", N=512, n_sub=1000)
+    out, _ = run_gpu(rhd, case)
+    ref, _ = orc.subcycles(case)
+    e = errors(out, ref, case["desc"])
+    assert max(e.values()) <= FP64_TOL, e
+    # the perturbation itself (1e-6 of the background) must agree to 1e-7 relative
+    dE = out["E"] - 1.0
+    dR = ref["E"] - 1.0
+    assert np.max(np.abs(dE - dR)) <= 1e-7 * np.max(np.abs(dR))
+
+
+def test_config2_source_reduced_fp64(rhd):
+    case = wl.config2(N=64, n_sub=200)
+    out, _ = run_gpu(rhd, case)
+    ref, _ = orc.subcycles(case)
+    assert max(errors(out, ref, case["desc"]).values()) <= FP64_TOL
+
+
+def test_config4_reduced_fp64(rhd):
+    case = wl.config4(N=32, n_sub=10)
+    out, st = run_gpu(rhd, case)
+    ref, rst = orc.subcycles(case)
+    assert max(errors(out, ref, case["desc"]).values()) <= FP64_TOL
+    assert st["n_theta_fallback"] == rst["n_theta_fallback"]
+
+
+# ----------------------------------------------------------------------------- split path
+
+SPLIT_TOL = 2e-5
+
+
+@pytest.mark.parametrize("kw", FP64_CASES[:6] + FP64_CASES[6:8], ids=[c["name"] for c in FP64_CASES[:8]])
+def test_split_error_bound_small(rhd, kw):
+    kw = dict(kw)
+    name = kw.pop("name")
+    n = kw.pop("n")
+    case = wl.parity_case(name, n, n_sub=4, seed=zlib.crc32(name.encode()) % 1000, precision="split", **kw)
+    out, st = run_gpu(rhd, case)
+    ref, _ = orc.subcycles(case)
+    e = errors(out, ref, case["desc"])
+    assert max(e.values()) <= SPLIT_TOL, e
+    assert st["n_nonfinite"] == 0
+
+
+def test_config4_reduced_split(rhd):
+    case = wl.config4(N=32, n_sub=10, precision="split")
+    out, _ = run_gpu(rhd, case)
+    ref, _ = orc.subcycles(case)
+    e = errors(out, ref, case["desc"])
+    assert max(e.values()) <= SPLIT_TOL, e
+
+
+# ----------------------------------------------------------------------------- full size (sampled)
+
+@pytest.fixture(scope="module")
+def config4_full():
+    return wl.config4(N=512, n_sub=1)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("split", SPLIT_TOL)])
+def test_config4_full_size_sampled(rhd, config4_full, precision, tol):
+    """512^3 throughput configuration, one subcycle in the launch configuration the benchmark times;
+    the oracle recomputes sampled 6^3 boxes (one at the periodic corner) and every element of each
+    box must match."""
+    case = dict(config4_full)
+    case["desc"] = dict(case["desc"], precision=precision)
+    out, st = run_gpu(rhd, case, n_sub=1)
+    assert st["n_nonfinite"] == 0
+    N = 512
+    boxes = [((0, 0, 0), (6, 6, 6)), ((506, 506, 506), (512, 512, 512)), ((250, 31, 400), (256, 37, 406)),
+             ((100, 300, 7), (106, 306, 13))]
+    c = case["desc"]["c"]
+    for lo, hi in boxes:
+        ref, _ = orc.subcycle_box(case, lo, hi)
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        sE = float(np.max(np.abs(ref["E"][sl])))
+        assert np.max(np.abs(out["E"][sl] - ref["E"][sl])) <= tol * sE
+        for k in ("Fx", "Fy", "Fz"):
+            assert np.max(np.abs(out[k][sl] - ref[k][sl])) <= tol * c * sE, (k, lo)
+        assert np.max(np.abs(out["T"][sl] - ref["T"][sl])) <= tol * float(np.max(ref["T"][sl]))
+
+
+# ----------------------------------------------------------------------------- ensemble
+
+def test_ensemble_matches_per_grid_oracle(rhd):
+    cases = []
+    for i, (n, prec) in enumerate([((16, 16, 16), "fp64"), ((24, 24, 24), "fp64"), ((32, 32, 32), "fp64")]):
+        c = wl.config5(n_grids=1, sizes=(n[0],), n_sub=3, precision=prec, seed_offset=50 + i)[0]
+        cases.append(c)
+    ens = rhd.Ensemble([c["desc"] for c in cases])
+    for i, c in enumerate(cases):
+        ens.load_case(i, c)
+    ens.subcycle(3, 1.0, [c["dt"] for c in cases])
+    for i, c in enumerate(cases):
+        out = ens.get_moments(i)
+        out["T"] = ens.get_gas_state(i)
+        ref, _ = orc.subcycles(c, n_sub=3)
+        assert max(errors(out, ref, c["desc"]).values()) <= FP64_TOL, i
+    ens.close()
+
+
+# ----------------------------------------------------------------------------- interface behaviour
+
+def test_device_pointers_and_errors(rhd):
+    import torch
+
+    case = wl.parity_case("dev", (16, 8, 8), bc="periodic", exchange="full", beta_tau=True, n_sub=2, seed=2)
+    ref_host, _ = run_gpu(rhd, case)
+    g = rhd.Grid(case["desc"])
+    f = case["fields"]
+    dev = {k: (None if f[k] is None else torch.from_numpy(np.ascontiguousarray(f[k])).cuda()) for k in f}
+    g.set_gas_state(dev["rho"], dev["T"], dev["vx"], dev["vy"], dev["vz"], dev["kP"], dev["kF"], dev["j"])
+    g.set_moments(dev["E"], dev["Fx"], dev["Fy"], dev["Fz"])
+    g.radiation_subcycle(2, case["chat"], case["dt"])
+    outs = [torch.empty_like(dev["E"]) for _ in range(4)]
+    g.get_moments(*outs)
+    torch.cuda.synchronize()
+    for k, t in zip(("E", "Fx", "Fy", "Fz"), outs):
+        assert np.array_equal(t.cpu().numpy(), ref_host[k]), k
+    # CFL and chat checks
+    with pytest.raises(rhd.RhdError) as ei:
+        g.radiation_subcycle(1, case["chat"], case["dt"] * 1.01)
+    assert ei.value.status == rhd.ERR_CFL
+    with pytest.raises(rhd.RhdError) as ei:
+        g.radiation_subcycle(1, case["desc"]["c"] * 1.5, case["dt"] * 0.1)
+    assert ei.value.status == rhd.ERR_CFL
+    with pytest.raises(rhd.RhdError):
+        g.gas_step(1.0)
+    g.close()
+    g2 = rhd.Grid(case["desc"])
+    with pytest.raises(rhd.RhdError) as ei:
+        g2.radiation_subcycle(1, case["chat"], case["dt"])
+    assert ei.value.status == rhd.ERR_STATE
+    g2.synchronize(1000)
+    g2.close()
