@@ -1,8 +1,9 @@
 """Benchmark of the subcycled M1 radiation update on GB300.
 
 Workload (throughput configuration): 512^3 periodic grid, radiation (E, Fx, Fy, Fz) plus frozen gas
-(rho, T, vx, vy, vz) with a seeded lognormal density (sigma_ln rho = 1), opacities proportional to rho
-(k = 512 rho^2), isotropic random F with |F| <= 0.5 cE, FULL energy exchange and O(beta tau) terms,
+(rho, T, vx, vy, vz) with a seeded lognormal density (sigma_ln rho = 1), absorption coefficients
+proportional to rho (k = 512 rho), gas speeds v ~ N(0, (0.001 c)^2), isotropic random F with
+|F| <= 0.5 cE, FULL energy exchange and O(beta tau) terms,
 c = 10, chat = 1, CFL 0.4.  One step = one call of rhd_radiation_subcycle with 100 subcycles, i.e. the
 whole hot path (every per-subcycle stage) over the grid.  Headline: the split-precision path; the plain
 FP64 path is measured alongside (4 subcycles per step, same rate unit).
@@ -27,7 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "radiation cell-updates/s per subcycle (FP64 vs FP32/FP64 split) and % HBM roofline"
 UNIT = "cell-updates/s"
 # algorithmic bytes per cell-update of the throughput workload (FULL exchange, beta tau on, opacity law
-# in registers): U^m read + U^{m+1} write 64 B, T read + write 16 B, rho and v read
+# k = 512 rho evaluated in registers): U^m read + U^{m+1} write 64 B, T read + write 16 B, rho and v read
 B_ALG = {"fp64": 64 + 16 + 8 + 24, "split": 64 + 16 + 4 + 12}
 
 
@@ -157,7 +158,8 @@ def run_reference(args):
 
 def workload_config(args, precision):
     return {"workload": f"3D throughput run, {args.N}^3 periodic SoA grid, lognormal rho (sigma_ln rho = 1), "
-                        f"k = 512 rho^2, |F| <= 0.5 cE, FULL exchange, beta tau on, c = 10, chat = 1",
+                        f"v ~ N(0, (0.001 c)^2), k = 512 rho, |F| <= 0.5 cE, FULL exchange, beta tau on, "
+                        f"c = 10, chat = 1",
             "N": args.N, "n_sub_per_step": args.n_sub, "precision": precision,
             "l2": "inputs larger than L2 (1.07 GB per FP64 field)"}
 

@@ -588,8 +588,13 @@ static void run_block(work_t* w, double* Eo, double* Gxo, double* Gyo, double* G
                     for (q = 0; q < 4; ++q) U[q] = w->Um[q][c] - dt * div[q] + dt * S[q];
                     theta_updates(w, c, dt, U);
                     double Tn = w->T[c];
-                    if (p->exchange == ORC_EX_FULL)
+                    if (p->exchange == ORC_EX_FULL) {
+                        /* the unsplit second-order transport is not positivity preserving; the
+                         * exchange acts on E floored at E_floor (reading), which keeps c0 < 0 for
+                         * theta = 1 */
+                        if (U[0] < p->E_floor) U[0] = p->E_floor;
                         n_theta += orc_exchange_full(p, chat, dt, w->rho[c], w->kP[c], &U[0], &Tn);
+                    }
                     n_fix += realizability(p, U);
                     if (!(isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]) &&
                           (p->exchange != ORC_EX_FULL || isfinite(Tn))))

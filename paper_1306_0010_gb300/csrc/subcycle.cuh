@@ -920,6 +920,8 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                     gd.v[2] = (double)gc.v[2];
                     theta_updates(g, gd, chat_d, dt_d, U);
                     if (full) {
+                        // transport can leave E <= 0 (not positivity preserving); exchange on E >= E_floor
+                        if (U[0] < g.E_floor) U[0] = g.E_floor;
                         ExchangeOut o = exchange_fp64(g, chat_d, dt_d, gc.rho, (double)gc.kP, U[0], Tn);
                         cnt.theta += o.theta_fb;
                         cnt.newton_fb += o.newton_fb;
@@ -947,19 +949,25 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                         float Tf = (float)gc.T;
                         float aT4 = g.f_a_rad * (Tf * Tf) * (Tf * Tf);
                         d[0] += xP * (aT4 - (u0f[0] + d[0])) / (1.0f + thE * xP);
-                    } else if (full) {
+                    }
+                    double Etr = U0[0] + (double)d[0];
+                    if (full) {
+                        // exchange on E >= E_floor; its change is applied to the FP64 energy
+                        if (Etr < g.E_floor) Etr = g.E_floor;
                         ExchangeOut o;
                         float qv;
                         float del = exchange_delta_fp32(g, (float)chat, (float)dt, (float)gc.rho, (float)gc.kP,
-                                                        u0f[0] + d[0], (float)gc.T, o, qv);
-                        d[0] -= ((float)chat * g.f_inv_c) * del;
+                                                        (float)Etr, (float)gc.T, o, qv);
+                        Etr -= (double)(((float)chat * g.f_inv_c) * del);
+                        d[0] = (float)(Etr - U0[0]);
                         Tn = gc.T + (double)(qv * del);
                         cnt.theta += o.theta_fb;
                         cnt.newton_fb += o.newton_fb;
                         cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
                     }
+                    Un[0] = Etr;
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) Un[qq] = U0[qq] + (double)d[qq];
+                    for (int qq = 1; qq < 4; ++qq) Un[qq] = U0[qq] + (double)d[qq];
                     // realizability: cheap FP32 screen, exact FP64 test only near the limit
                     float ef = u0f[0] + d[0];
                     float g2f = 0.f;

@@ -468,6 +468,7 @@ def _py_subcycle(case):
                 U = direct([U0[q] - dt * div[q] + dt * S[q] for q in range(4)], g_, dt)
                 T = g_[1]
                 if d["exchange"] == "full":
+                    U[0] = max(U[0], d["E_floor"])
                     e1, T1, _ = orc.exchange_full(d, chat, dt, g_[0], g_[3], U[0], T)
                     U[0], T = e1, T1
                 U = realize(U)
