@@ -7,7 +7,7 @@ template <typename R, int TX, int TY, int DIM, bool SPLIT>
 static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 {
     using G = Geo<TX, TY, DIM>;
-    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    const size_t smem = G::bytes(sizeof(R));
     auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -20,7 +20,7 @@ template <typename R, int TX, int TY, bool SPLIT>
 static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaStream_t s)
 {
     using G = Geo<TX, TY, 3>;
-    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    const size_t smem = G::bytes(sizeof(R));
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -32,7 +32,7 @@ template <typename R, int TX, int TY, bool SPLIT>
 static int ens_occupancy()
 {
     using G = Geo<TX, TY, 3>;
-    const size_t smem = sizeof(R) * (size_t)G::TOTAL;
+    const size_t smem = G::bytes(sizeof(R));
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     int n = 0;

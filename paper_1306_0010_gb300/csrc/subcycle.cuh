@@ -45,8 +45,63 @@ struct Tol<float> {
     static constexpr float face = 1e-5f;
 };
 
+// Square root and reciprocal: IEEE in FP64; in the split path the hardware approximations
+// (MUFU, about 1-2 ulp), which are well inside the FP32 error budget of the fluxes.
 __device__ __forceinline__ double rsq(double x) { return sqrt(x); }
-__device__ __forceinline__ float rsq(float x) { return sqrtf(x); }
+__device__ __forceinline__ float rsq(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// FP64 <-> FP32 conversions without the FP64 pipe (which runs at a small fraction of the FP32 rate
+// on this part): truncation of the FP64 value to FP32 (normal range; underflow to 0, overflow to
+// inf), and the exact widening of an FP32 value (denormals flushed), by integer bit operations.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    unsigned sign = hi & 0x80000000u;
+    int fe = (int)((hi >> 20) & 0x7ffu) - 896;
+    unsigned r = sign | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    r = fe <= 0 ? sign : r;
+    r = fe >= 255 ? (sign | 0x7f800000u) : r;
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    unsigned b = __float_as_uint(f);
+    unsigned sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    unsigned hi = sign | ((ex + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    hi = ex == 0u ? sign : hi;
+    lo = ex == 0u ? 0u : lo;
+    hi = ex == 255u ? (sign | 0x7ff00000u | (m >> 3)) : hi;
+    return __hiloint2double((int)hi, (int)lo);
+}
+// Asynchronous global->shared copies (cp.async): the next plane is fetched while the current one
+// is being computed; completion is awaited with cp.async.wait_all before the data are read.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ bool finite_d(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+template <typename R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return d2f_trunc(x); }
+
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmin(double a, double b) { return fmin(a, b); }
@@ -69,13 +124,13 @@ template <typename R>
 __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R gz, R chat, int p1)
 {
     ClosureScalars<R> k;
-    k.invE = R(1) / E;
+    k.invE = rcp(E);
     R g2 = gx * gx + gy * gy + gz * gz;
     R f2 = g2 * (k.invE * k.invE);
     f2 = rmin(f2, R(1));
     k.s = rsq(R(4) - R(3) * f2);
-    k.inv2ps = R(1) / (R(2) + k.s);
-    k.cs = chat / k.s;
+    k.inv2ps = rcp(R(2) + k.s);
+    k.cs = chat * rcp(k.s);
     if (p1) {
         k.a = E * R(1.0 / 3.0);
         k.b = R(0);
@@ -124,7 +179,7 @@ __device__ __forceinline__ void hll(const R UL[4], const R UR[4], const R FL[4],
     R SRp = rmax(SR, R(0)), SLm = rmin(SL, R(0));
     R den = SRp - SLm;
     if (den > R(0)) {
-        R inv = R(1) / den;
+        R inv = rcp(den);
         R pr = SRp * SLm;
 #pragma unroll
         for (int q = 0; q < 4; ++q) out[q] = (SRp * FL[q] - SLm * FR[q] + pr * (UR[q] - UL[q])) * inv;
@@ -153,37 +208,41 @@ __device__ __forceinline__ bool face_unrealizable(R E, R gx, R gy, R gz)
     return !(E > R(0)) || (g2 > (R(1) + Tol<R>::face) * (E * E));
 }
 
-// Corrector face in direction D: L = plus-state of cell i-1, R = minus-state of cell i, from
-// U^{m+1/2} at i-2, i-1, i, i+1 (indices (i-1/2, i-1/2)).  fbL/fbR report a zeroed slope.
+// Face states of one cell in direction D for the corrector: the limited slope of U^{m+1/2} from
+// cells i-1, i, i+1, the two face values U -/+ slope/2 (zero slope if either is not realizable),
+// and for each face value the flux in direction D and the wave speeds lambda_1, lambda_3.
+// Layout of out[20]: minus state (4), its flux (4), l1, l3, plus state (4), its flux (4), l1, l3.
 template <int D, typename R>
-__device__ __forceinline__ void corrector_face(const R um2[4], const R um1[4], const R u0[4], const R up1[4],
-                                               R chat, int lim, int p1, int fixed, R F[4], int& fbL, int& fbR)
+__device__ __forceinline__ int face_states(const R um[4], const R u0[4], const R up[4], R chat, int lim, int p1,
+                                           int fixed, R out[20])
 {
-    R sL[4], sR[4];
+    R sl[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        sL[q] = limited(um1[q] - um2[q], u0[q] - um1[q], lim);
-        sR[q] = limited(u0[q] - um1[q], up1[q] - u0[q], lim);
-    }
+    for (int q = 0; q < 4; ++q) sl[q] = limited(u0[q] - um[q], up[q] - u0[q], lim);
     const R h = R(0.5);
-    fbL = face_unrealizable(um1[0] - h * sL[0], um1[1] - h * sL[1], um1[2] - h * sL[2], um1[3] - h * sL[3]) ||
-          face_unrealizable(um1[0] + h * sL[0], um1[1] + h * sL[1], um1[2] + h * sL[2], um1[3] + h * sL[3]);
-    fbR = face_unrealizable(u0[0] - h * sR[0], u0[1] - h * sR[1], u0[2] - h * sR[2], u0[3] - h * sR[3]) ||
-          face_unrealizable(u0[0] + h * sR[0], u0[1] + h * sR[1], u0[2] + h * sR[2], u0[3] + h * sR[3]);
-    R UL[4], UR[4];
+    R Sm[4], Sp[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        UL[q] = fbL ? um1[q] : um1[q] + h * sL[q];
-        UR[q] = fbR ? u0[q] : u0[q] - h * sR[q];
+        Sm[q] = u0[q] - h * sl[q];
+        Sp[q] = u0[q] + h * sl[q];
     }
-    ClosureScalars<R> kL = closure_scalars(UL[0], UL[1], UL[2], UL[3], chat, p1);
-    ClosureScalars<R> kR = closure_scalars(UR[0], UR[1], UR[2], UR[3], chat, p1);
-    R FL[4], FR[4], l1L, l3L, l1R, l3R;
-    dir_flux<D>(kL, UL, chat, FL);
-    dir_flux<D>(kR, UR, chat, FR);
-    wave_speeds(kL, UL[1 + D], chat, fixed, l1L, l3L);
-    wave_speeds(kR, UR[1 + D], chat, fixed, l1R, l3R);
-    hll(UL, UR, FL, FR, l1L, l3L, l1R, l3R, F);
+    int fb = face_unrealizable(Sm[0], Sm[1], Sm[2], Sm[3]) || face_unrealizable(Sp[0], Sp[1], Sp[2], Sp[3]);
+    if (fb) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Sm[q] = Sp[q] = u0[q];
+    }
+    ClosureScalars<R> km = closure_scalars(Sm[0], Sm[1], Sm[2], Sm[3], chat, p1);
+    ClosureScalars<R> kp = closure_scalars(Sp[0], Sp[1], Sp[2], Sp[3], chat, p1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        out[q] = Sm[q];
+        out[10 + q] = Sp[q];
+    }
+    dir_flux<D>(km, Sm, chat, out + 4);
+    dir_flux<D>(kp, Sp, chat, out + 14);
+    wave_speeds(km, Sm[1 + D], chat, fixed, out[8], out[9]);
+    wave_speeds(kp, Sp[1 + D], chat, fixed, out[18], out[19]);
+    return fb;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -255,7 +314,8 @@ __device__ __forceinline__ void load_U(const GridParams& g, const GridArrays& a,
 template <typename R>
 struct GasCell {
     R kP, kF, v[3], j;
-    double T, rho;
+    double T, rho;  // rho in FP64 is loaded only where the FP64 exchange needs it
+    float rho32;
 };
 
 __device__ __forceinline__ double kappa_law(double kappa, int p, double rho)
@@ -284,6 +344,7 @@ __device__ __forceinline__ GasCell<R> load_gas(const GridParams& g, const GridAr
     c.T = need_T ? __ldg(a.T + i) : 0.0;
     if (SPLIT) {
         float r = __ldg(a.rho32 + i);
+        c.rho32 = r;
         c.rho = need_rho64 ? __ldg(a.rho + i) : 0.0;
         c.kP = a.kP32 ? __ldg(a.kP32 + i) : kappa_law_f(g.f_kappa_P, g.kpow, r);
         c.kF = a.kF32 ? __ldg(a.kF32 + i) : kappa_law_f(g.f_kappa_F, g.kpow, r);
@@ -296,6 +357,7 @@ __device__ __forceinline__ GasCell<R> load_gas(const GridParams& g, const GridAr
     } else {
         double r = __ldg(a.rho + i);
         c.rho = r;
+        c.rho32 = 0.0f;
         c.kP = a.kP ? __ldg(a.kP + i) : kappa_law(g.kappa_P, g.kpow, r);
         c.kF = a.kF ? __ldg(a.kF + i) : kappa_law(g.kappa_F, g.kpow, r);
 #pragma unroll
@@ -336,18 +398,18 @@ __device__ __forceinline__ void theta_updates(const GridParams& g, const GasCell
     const R thF = sizeof(R) == 8 ? (R)g.theta_F : (R)g.f_theta_F;
     const R thE = sizeof(R) == 8 ? (R)g.theta_E : (R)g.f_theta_E;
     R xF = chat * gc.kF * h;
-    R fF = (R(1) - (R(1) - thF) * xF) / (R(1) + thF * xF);
+    R fF = (R(1) - (R(1) - thF) * xF) * rcp(R(1) + thF * xF);
     U[1] *= fF;
     U[2] *= fF;
     U[3] *= fF;
     if (g.exchange == EX_ABSORB) {
         R xP = chat * gc.kP * h;
-        U[0] *= (R(1) - (R(1) - thE) * xP) / (R(1) + thE * xP);
+        U[0] *= (R(1) - (R(1) - thE) * xP) * rcp(R(1) + thE * xP);
     } else if (g.exchange == EX_FROZEN_T) {
         R xP = chat * gc.kP * h;
         R T = (R)gc.T;
         R aT4 = (sizeof(R) == 8 ? (R)g.a_rad : (R)g.f_a_rad) * (T * T) * (T * T);
-        U[0] = (U[0] * (R(1) - (R(1) - thE) * xP) + xP * aT4) / (R(1) + thE * xP);
+        U[0] = (U[0] * (R(1) - (R(1) - thE) * xP) + xP * aT4) * rcp(R(1) + thE * xP);
     }
 }
 
@@ -358,7 +420,7 @@ __device__ __forceinline__ int realize(R U[4], R E_floor)
     if (U[0] < E_floor) U[0] = E_floor;
     R g2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
     if (g2 > U[0] * U[0]) {
-        R s = U[0] / rsq(g2);
+        R s = U[0] / sqrt(g2);
         U[1] *= s;
         U[2] *= s;
         U[3] *= s;
@@ -453,14 +515,14 @@ __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float 
 {
     o.theta_fb = o.newton_fb = o.iters = 0;
     const float c = g.f_c;
-    const float q = g.f_gm1_mu / rho;
-    const float e = rho * T / g.f_gm1_mu;
+    const float q = g.f_gm1_mu * rcp(rho);
+    const float e = rho * T * rcp(g.f_gm1_mu);
     const float alpha = g.f_a_rad * (q * q) * (q * q);
     const float eta = c * kP * dt;
     const float r = chat * g.f_inv_c;
     float th = g.f_theta_E;
     float e4 = (e * e) * (e * e);
-    float Ebar = e + E / r;
+    float Ebar = e + E * rcp(r);
     float c0 = (1.0f - th) * eta * (alpha * e4 - E) - (e + r * eta * th * Ebar);
     if (c0 > 0.0f) {
         th = 1.0f;
@@ -470,8 +532,8 @@ __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float 
     const float A = eta * th * alpha;
     const float B = 1.0f + r * eta * th;
     const float C = eta * ((1.0f - th) * alpha * e4 - E);
-    float b = fabsf(c0 / B);
-    if (A > 0.0f) b = fminf(b, sqrtf(sqrtf(fabsf(c0 / A))));
+    float b = fabsf(c0 * rcp(B));
+    if (A > 0.0f) b = fminf(b, rsq(rsq(fabsf(c0 * rcp(A)))));
     const float dhi = b - e, dlo = -e;
     float d = 0.0f;
     bool conv = false;
@@ -481,7 +543,7 @@ __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float 
         float x2 = x * x;
         float gv = A * x2 * x2 + B * d + C;
         float gp = 4.0f * A * x2 * x + B;
-        float dn = d - gv / gp;
+        float dn = d - gv * rcp(gp);
         dn = fminf(fmaxf(dn, dlo), dhi);
         if (it > 0 && !(dn < d)) {
             conv = true;
@@ -519,18 +581,36 @@ struct Geo {
     static constexpr int N3 = W3 * H3, N2 = W2 * H2;
     static constexpr int NR2 = (N2 + NT - 1) / NT;
     static constexpr int NR3 = (N3 + NT - 1) / NT;
+    // predictor faces
     static constexpr int NFX = (W2 + 1) * H2;
-    static constexpr int NFY = HY ? W2 * (H2 + 1) : 1;
+    static constexpr int NFY = HY ? W2 * (H2 + 1) : 0;
+    // corrector: cells with face states, and faces
+    static constexpr int NSX = (TX + 2) * TY;
+    static constexpr int NSY = HY ? TX * (TY + 2) : 0;
     static constexpr int NCX = (TX + 1) * TY;
-    static constexpr int NCY = HY ? TX * (TY + 1) : 1;
-    static constexpr int RING = DIM == 3 ? 5 : 1;
-    // shared-memory layout in units of R
-    static constexpr int OFF_UM = 0;                      // 4 x N3
-    static constexpr int OFF_CC = OFF_UM + 4 * N3;        // 9 x N3 closure data
-    static constexpr int OFF_FX = OFF_CC + 9 * N3;        // 4 x NFX
-    static constexpr int OFF_FY = OFF_FX + 4 * NFX;       // 4 x NFY
-    static constexpr int OFF_UH = OFF_FY + 4 * NFY;       // RING x 4 x N2
-    static constexpr int TOTAL = OFF_UH + RING * 4 * N2;
+    static constexpr int NCY = HY ? TX * (TY + 1) : 0;
+    static constexpr int RING = DIM == 3 ? 3 : 1;
+    // shared memory (units of R): predictor buffers and corrector buffers share one region
+    static constexpr int P_UM = 0;                 // 4 x N3 U^m
+    static constexpr int P_CC = P_UM + 4 * N3;     // 9 x N3 closure data
+    static constexpr int P_FX = P_CC + 9 * N3;     // 4 x NFX
+    static constexpr int P_FY = P_FX + 4 * NFX;    // 4 x NFY
+    static constexpr int P_END = P_FY + 4 * NFY;
+    static constexpr int C_SX = 0;                 // 20 x NSX face states (x)
+    static constexpr int C_SY = C_SX + 20 * NSX;   // 20 x NSY face states (y)
+    static constexpr int C_FX = C_SY + 20 * NSY;   // 4 x NCX fluxes
+    static constexpr int C_FY = C_FX + 4 * NCX;    // 4 x NCY fluxes
+    static constexpr int C_END = C_FY + 4 * NCY;
+    static constexpr int UNION = P_END > C_END ? P_END : C_END;
+    static constexpr int OFF_UH = UNION;           // RING x 4 x N2
+    static constexpr int END_R = OFF_UH + RING * 4 * N2;
+    // FP64 staging (offsets in doubles from the 8-byte aligned end of the R region):
+    // U^m of the next plane on R3, and U^m, T of the corrector plane on the tile
+    static constexpr int ST_U = 0;                 // 4 x N3
+    static constexpr int ST_C = ST_U + 4 * N3;     // 5 x NT
+    static constexpr int ST_END = ST_C + 5 * NT;
+    __host__ __device__ static constexpr size_t r_bytes(size_t rsize) { return ((END_R * rsize + 15) / 16) * 16; }
+    __host__ __device__ static constexpr size_t bytes(size_t rsize) { return r_bytes(rsize) + 8 * (size_t)ST_END; }
 
     __device__ static __forceinline__ int i3(int lx, int ly) { return (lx + 3) + W3 * (ly + 3 * HY); }
     __device__ static __forceinline__ int i2(int lx, int ly) { return (lx + 2) + W2 * (ly + 2 * HY); }
@@ -584,6 +664,29 @@ struct Counters {
     unsigned fix, face, theta, newton_fb, nonfinite, iter_max;
 };
 
+template <typename R>
+__device__ __forceinline__ void store20(R* base, int stride, int idx, const R v[20])
+{
+#pragma unroll
+    for (int q = 0; q < 20; ++q) base[q * stride + idx] = v[q];
+}
+
+// HLL from stored face states: L = plus part of cell iL, R = minus part of cell iR
+template <typename R>
+__device__ __forceinline__ void hll_stored(const R* base, int stride, int iL, int iR, R F[4])
+{
+    R UL[4], UR[4], FL[4], FR[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        UL[q] = base[(10 + q) * stride + iL];
+        FL[q] = base[(14 + q) * stride + iL];
+        UR[q] = base[q * stride + iR];
+        FR[q] = base[(4 + q) * stride + iR];
+    }
+    hll(UL, UR, FL, FR, base[18 * stride + iL], base[19 * stride + iL], base[8 * stride + iR], base[9 * stride + iR],
+        F);
+}
+
 // ------------------------------------------------------------------------------------------------
 // one tile of one subcycle: planes [z0, z1) of the column tile at (x0, y0)
 // ------------------------------------------------------------------------------------------------
@@ -593,11 +696,17 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
 {
     using G = Geo<TX, TY, DIM>;
     const int t = threadIdx.x;
-    R* Um = sm + G::OFF_UM;
-    R* Cc = sm + G::OFF_CC;
-    R* Fx = sm + G::OFF_FX;
-    R* Fy = sm + G::OFF_FY;
+    R* Um = sm + G::P_UM;
+    R* Cc = sm + G::P_CC;
+    R* Fx = sm + G::P_FX;
+    R* Fy = sm + G::P_FY;
+    R* Sx = sm + G::C_SX;
+    R* Sy = sm + G::C_SY;
+    R* Cx = sm + G::C_FX;
+    R* Cy = sm + G::C_FY;
     R* Uh = sm + G::OFF_UH;
+    double* stU = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(sm) + G::r_bytes(sizeof(R)));
+    double* stC = stU + G::ST_C;
     const R chat = (R)chat_d;
     const R dt = (R)dt_d;
     const R hdt = R(0.5) * dt;
@@ -605,34 +714,90 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
     const int p1 = g.closure == 1, fixed = g.speeds == 1, lim = g.limiter;
     const R E_floor = sizeof(R) == 8 ? (R)g.E_floor : (R)g.f_E_floor;
     const bool needT_pred = g.exchange == EX_FROZEN_T;
+    const long long nxy = (long long)g.n[0] * g.n[1];
 
-    // per-thread z pipeline of the predictor (own R2 cells: c = t + r * NT)
-    R zU[G::NR2][4], zP[G::NR2][3], zl[G::NR2][2], dxy[G::NR2][4], zfl[G::NR2][4];
-    // corrector: lower z face of the own tile column
-    R cfl[4];
-    const int tlx = t % TX, tly = t / TX;   // own tile cell
+    // cells of the R3 region handled by this thread, fixed for all planes
+    int c_i3[G::NR3], c_off[G::NR3];
+    // the tile's halo lies inside the domain in x and y: loads need no boundary remap there
+    const bool xy_inside = x0 - 3 >= 0 && x0 + TX + 3 <= g.n[0] &&
+                           (G::HY == 0 || (y0 - 3 >= 0 && y0 + TY + 3 <= g.n[1]));
+#pragma unroll
+    for (int r = 0; r < G::NR3; ++r) {
+        int c = t + r * G::NT;
+        int lx = 0, ly = 0;
+        if (c < G::N3) G::cell_of(c, lx, ly);
+        c_i3[r] = G::i3(lx, ly);
+        c_off[r] = (x0 + lx) + g.n[0] * (y0 + ly);
+    }
 
-    const int qbeg = (DIM == 3) ? z0 - 3 : 0;
-    const int qend = (DIM == 3) ? z1 + 3 : 1;
-#pragma unroll 1
-    for (int qz = qbeg; qz < qend; ++qz) {
-        // (a) U^m of plane qz on the tile plus 3-cell halo
+    const int tlx0 = t % TX, tly0 = t / TX;
+    // fetch U^m of plane q on R3 into the staging buffer (asynchronously where no remap is needed)
+    auto issue_plane = [&](int q) {
+        const bool fast = xy_inside && (unsigned)q < (unsigned)g.n[2];
+        const long long zoff = (long long)q * nxy;
 #pragma unroll
         for (int r = 0; r < G::NR3; ++r) {
             int c = t + r * G::NT;
             if (c < G::N3) {
-                int lx, ly;
-                G::cell_of(c, lx, ly);
-                double U[4];
-                load_U(g, a, x0 + lx, y0 + ly, qz, U);
-                int i = G::i3(lx, ly);
-                Um[0 * G::N3 + i] = (R)U[0];
-                Um[1 * G::N3 + i] = (R)U[1];
-                Um[2 * G::N3 + i] = (R)U[2];
-                Um[3 * G::N3 + i] = (R)U[3];
+                if (fast) {
+                    long long i = zoff + c_off[r];
+                    cp_async8(stU + 0 * G::N3 + c, a.E + i);
+                    cp_async8(stU + 1 * G::N3 + c, a.G[0] + i);
+                    cp_async8(stU + 2 * G::N3 + c, a.G[1] + i);
+                    cp_async8(stU + 3 * G::N3 + c, a.G[2] + i);
+                } else {
+                    int lx, ly;
+                    G::cell_of(c, lx, ly);
+                    double U[4];
+                    load_U(g, a, x0 + lx, y0 + ly, q, U);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) stU[qq * G::N3 + c] = U[qq];
+                }
+            }
+        }
+    };
+    // fetch the FP64 state (and T) of the own tile cell of corrector plane k
+    const bool needT_corr = g.exchange == EX_FULL || g.exchange == EX_FROZEN_T;
+    auto issue_corr = [&](int k) {
+        if (x0 + tlx0 < g.n[0] && y0 + tly0 < g.n[1] && (unsigned)k < (unsigned)g.n[2]) {
+            long long i = lin(g, x0 + tlx0, y0 + tly0, k);
+            cp_async8(stC + 0 * G::NT + t, a.E + i);
+            cp_async8(stC + 1 * G::NT + t, a.G[0] + i);
+            cp_async8(stC + 2 * G::NT + t, a.G[1] + i);
+            cp_async8(stC + 3 * G::NT + t, a.G[2] + i);
+            if (needT_corr) cp_async8(stC + 4 * G::NT + t, a.T + i);
+        }
+    };
+
+    // per-thread z pipeline of the predictor (own R2 cells: c = t + r * NT)
+    R zU[G::NR2][4], zP[G::NR2][3], zl[G::NR2][2], dxy[G::NR2][4], zfl[G::NR2][4];
+    // corrector: lower z face and the plus face state (z) of the previous plane, own tile column
+    R cfl[4], zplus[10];
+    const int tlx = tlx0, tly = tly0;
+
+    const int qbeg = (DIM == 3) ? z0 - 3 : 0;
+    const int qend = (DIM == 3) ? z1 + 3 : 1;
+    issue_plane(qbeg);
+    cp_async_commit();
+#pragma unroll 1
+    for (int qz = qbeg; qz < qend; ++qz) {
+        // (a) U^m of plane qz on the tile plus 3-cell halo: staged copy -> R (each thread converts
+        //     the cells it fetched itself, so its own wait suffices)
+        cp_async_wait_all();
+#pragma unroll
+        for (int r = 0; r < G::NR3; ++r) {
+            int c = t + r * G::NT;
+            if (c < G::N3) {
+                int i = c_i3[r];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) Um[qq * G::N3 + i] = to_r<R>(stU[qq * G::N3 + c]);
             }
         }
         __syncthreads();
+        // prefetch the next plane and the FP64 state of this iteration's corrector plane
+        if (qz + 1 < qend) issue_plane(qz + 1);
+        if (DIM == 3) issue_corr(qz - 3); else issue_corr(qz);
+        cp_async_commit();
         // (b) closure once per cell: P and the x, y wave speeds to shared memory; z data of the
         //     own R2 cells to registers
         R nU[G::NR2][4], nP[G::NR2][3], nl[G::NR2][2];
@@ -640,9 +805,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
         for (int r = 0; r < G::NR3; ++r) {
             int c = t + r * G::NT;
             if (c < G::N3) {
-                int lx, ly;
-                G::cell_of(c, lx, ly);
-                int i = G::i3(lx, ly);
+                int i = c_i3[r];
                 R U[4] = {Um[i], Um[G::N3 + i], Um[2 * G::N3 + i], Um[3 * G::N3 + i]};
                 ClosureScalars<R> k = closure_scalars(U[0], U[1], U[2], U[3], chat, p1);
                 R Pxx = k.a + k.b * U[1] * U[1], Pxy = k.b * U[1] * U[2], Pxz = k.b * U[1] * U[3];
@@ -673,37 +836,35 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
         }
         __syncthreads();
         // (c) first-order HLL fluxes on the x and y faces of the R2 rows / columns
-        for (int f = t; f < G::NFX; f += G::NT) {
-            int row = f / (G::W2 + 1);
-            int lx = f % (G::W2 + 1) - 2;
-            int ly = row - 2 * G::HY;
-            int iL = G::i3(lx - 1, ly), iR = G::i3(lx, ly);
-            R UL[4], UR[4], FL[4], FR[4];
+        for (int f = t; f < G::NFX + G::NFY; f += G::NT) {
+            R UL[4], UR[4], FL[4], FR[4], F[4];
+            if (f < G::NFX) {
+                int row = f / (G::W2 + 1);
+                int lx = f % (G::W2 + 1) - 2;
+                int ly = row - 2 * G::HY;
+                int iL = G::i3(lx - 1, ly), iR = G::i3(lx, ly);
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                UL[qq] = Um[qq * G::N3 + iL];
-                UR[qq] = Um[qq * G::N3 + iR];
-            }
-            FL[0] = chat * UL[1];
-            FL[1] = chat * Cc[0 * G::N3 + iL];
-            FL[2] = chat * Cc[1 * G::N3 + iL];
-            FL[3] = chat * Cc[2 * G::N3 + iL];
-            FR[0] = chat * UR[1];
-            FR[1] = chat * Cc[0 * G::N3 + iR];
-            FR[2] = chat * Cc[1 * G::N3 + iR];
-            FR[3] = chat * Cc[2 * G::N3 + iR];
-            R F[4];
-            hll(UL, UR, FL, FR, Cc[5 * G::N3 + iL], Cc[6 * G::N3 + iL], Cc[5 * G::N3 + iR], Cc[6 * G::N3 + iR], F);
+                for (int qq = 0; qq < 4; ++qq) {
+                    UL[qq] = Um[qq * G::N3 + iL];
+                    UR[qq] = Um[qq * G::N3 + iR];
+                }
+                FL[0] = chat * UL[1];
+                FL[1] = chat * Cc[0 * G::N3 + iL];
+                FL[2] = chat * Cc[1 * G::N3 + iL];
+                FL[3] = chat * Cc[2 * G::N3 + iL];
+                FR[0] = chat * UR[1];
+                FR[1] = chat * Cc[0 * G::N3 + iR];
+                FR[2] = chat * Cc[1 * G::N3 + iR];
+                FR[3] = chat * Cc[2 * G::N3 + iR];
+                hll(UL, UR, FL, FR, Cc[5 * G::N3 + iL], Cc[6 * G::N3 + iL], Cc[5 * G::N3 + iR], Cc[6 * G::N3 + iR],
+                    F);
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) Fx[qq * G::NFX + f] = F[qq];
-        }
-        if (G::HY) {
-            for (int f = t; f < G::NFY; f += G::NT) {
-                int fy = f / G::W2;
-                int lx = f % G::W2 - 2;
+                for (int qq = 0; qq < 4; ++qq) Fx[qq * G::NFX + f] = F[qq];
+            } else {
+                int fy = (f - G::NFX) / G::W2;
+                int lx = (f - G::NFX) % G::W2 - 2;
                 int ly = fy - 2;
                 int iL = G::i3(lx, ly - 1), iR = G::i3(lx, ly);
-                R UL[4], UR[4], FL[4], FR[4];
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     UL[qq] = Um[qq * G::N3 + iL];
@@ -717,11 +878,10 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                 FR[1] = chat * Cc[1 * G::N3 + iR];
                 FR[2] = chat * Cc[3 * G::N3 + iR];
                 FR[3] = chat * Cc[4 * G::N3 + iR];
-                R F[4];
                 hll(UL, UR, FL, FR, Cc[7 * G::N3 + iL], Cc[8 * G::N3 + iL], Cc[7 * G::N3 + iR], Cc[8 * G::N3 + iR],
                     F);
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) Fy[qq * G::NFY + f] = F[qq];
+                for (int qq = 0; qq < 4; ++qq) Fy[qq * G::NFY + (f - G::NFX)] = F[qq];
             }
         }
         __syncthreads();
@@ -745,7 +905,6 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                 }
                 R zfh[4] = {R(0), R(0), R(0), R(0)};
                 if (DIM == 3 && qz > qbeg) {
-                    // z face between plane qz-1 (stored) and qz (new)
                     R FL[4] = {chat * zU[r][3], chat * zP[r][0], chat * zP[r][1], chat * zP[r][2]};
                     R FR[4] = {chat * nU[r][3], chat * nP[r][0], chat * nP[r][1], chat * nP[r][2]};
                     hll(zU[r], nU[r], FL, FR, zl[r][0], zl[r][1], nl[r][0], nl[r][1], zfh);
@@ -776,7 +935,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                     bool owned = lx >= 0 && lx < TX && ly >= 0 && ly < TY && x0 + lx < g.n[0] &&
                                  y0 + ly < g.n[1] && p >= z0 && p < z1;
                     if (owned) cnt.fix += fx_;
-                    int slot = (DIM == 3) ? ((p + 10) % 5) : 0;
+                    int slot = (DIM == 3) ? ((p + 3) % 3) : 0;
                     R* dst = Uh + slot * 4 * G::N2;
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) dst[qq * G::N2 + c] = U[qq];
@@ -798,96 +957,135 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
         __syncthreads();
         // (e) corrector for plane k
         const int k = (DIM == 3) ? qz - 3 : qz;
+        const bool own_col = x0 + tlx < g.n[0] && y0 + tly < g.n[1];
+        if (DIM == 3 && qz == z0 + 1) {
+            // plus face state (z) of cell z0-1, from U^{m+1/2} at z0-2, z0-1, z0
+            const int i = G::i2(tlx, tly);
+            R u[3][4], fs[20];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const R* sl = Uh + ((z0 - 2 + m + 3) % 3) * 4 * G::N2;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) u[m][qq] = sl[qq * G::N2 + i];
+            }
+            face_states<2>(u[0], u[1], u[2], chat, lim, p1, fixed, fs);
+#pragma unroll
+            for (int qq = 0; qq < 10; ++qq) zplus[qq] = fs[10 + qq];
+        }
         if (DIM == 3 && qz == z0 + 2) {
-            // lower z face of the first plane: (z0 - 1 | z0) from U^{m+1/2} at z0-2 .. z0+1
-            const R* s0 = Uh + ((z0 - 2 + 10) % 5) * 4 * G::N2;
-            const R* s1 = Uh + ((z0 - 1 + 10) % 5) * 4 * G::N2;
-            const R* s2 = Uh + ((z0 + 10) % 5) * 4 * G::N2;
-            const R* s3 = Uh + ((z0 + 1 + 10) % 5) * 4 * G::N2;
-            int i = G::i2(tlx, tly);
-            R a0[4], a1[4], a2[4], a3[4];
+            // face states (z) of cell z0 and the lower face (z0 - 1 | z0)
+            const int i = G::i2(tlx, tly);
+            R u[3][4], fs[20];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const R* sl = Uh + ((z0 - 1 + m + 3) % 3) * 4 * G::N2;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) u[m][qq] = sl[qq * G::N2 + i];
+            }
+            int fb = face_states<2>(u[0], u[1], u[2], chat, lim, p1, fixed, fs);
+            if (fb && own_col) cnt.face += 1;
+            R UL[4], UR[4], FL[4], FR[4];
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
-                a0[qq] = s0[qq * G::N2 + i];
-                a1[qq] = s1[qq * G::N2 + i];
-                a2[qq] = s2[qq * G::N2 + i];
-                a3[qq] = s3[qq * G::N2 + i];
+                UL[qq] = zplus[qq];
+                FL[qq] = zplus[4 + qq];
+                UR[qq] = fs[qq];
+                FR[qq] = fs[4 + qq];
             }
-            int fbL, fbR;
-            corrector_face<2>(a0, a1, a2, a3, chat, lim, p1, fixed, cfl, fbL, fbR);
-            if (fbR && x0 + tlx < g.n[0] && y0 + tly < g.n[1]) cnt.face += 1;
+            hll(UL, UR, FL, FR, zplus[8], zplus[9], fs[8], fs[9], cfl);
+#pragma unroll
+            for (int qq = 0; qq < 10; ++qq) zplus[qq] = fs[10 + qq];
         }
         const bool do_corr = (DIM == 3) ? (k >= z0 && k < z1) : true;
         if (do_corr) {
-            const R* Uk = Uh + ((DIM == 3) ? ((k + 10) % 5) : 0) * 4 * G::N2;
-            // x faces of the tile rows
-            for (int f = t; f < G::NCX; f += G::NT) {
-                int ly = f / (TX + 1), lx = f % (TX + 1);
-                R u[4][4];
+            const R* Uk = Uh + ((DIM == 3) ? ((k + 3) % 3) : 0) * 4 * G::N2;
+            // (e1) face states of the tile cells and their neighbours along x and y
+            for (int c = t; c < G::NSX + G::NSY; c += G::NT) {
+                R fs[20];
+                if (c < G::NSX) {
+                    int ly = c / (TX + 2), lx = c % (TX + 2) - 1;
+                    R u[3][4];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    int i = G::i2(lx - 2 + m, ly);
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) u[m][qq] = Uk[qq * G::N2 + i];
-                }
-                R F[4];
-                int fbL, fbR;
-                corrector_face<0>(u[0], u[1], u[2], u[3], chat, lim, p1, fixed, F, fbL, fbR);
-                if (fbR && lx < TX && x0 + lx < g.n[0] && y0 + ly < g.n[1]) cnt.face += 1;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) Fx[qq * G::NFX + f] = F[qq];
-            }
-            if (G::HY) {
-                for (int f = t; f < G::NCY; f += G::NT) {
-                    int ly = f / TX, lx = f % TX;
-                    R u[4][4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        int i = G::i2(lx, ly - 2 + m);
+                    for (int m = 0; m < 3; ++m) {
+                        int i = G::i2(lx - 1 + m, ly);
 #pragma unroll
                         for (int qq = 0; qq < 4; ++qq) u[m][qq] = Uk[qq * G::N2 + i];
                     }
-                    R F[4];
-                    int fbL, fbR;
-                    corrector_face<1>(u[0], u[1], u[2], u[3], chat, lim, p1, fixed, F, fbL, fbR);
-                    if (fbR && ly < TY && x0 + lx < g.n[0] && y0 + ly < g.n[1]) cnt.face += 1;
+                    int fb = face_states<0>(u[0], u[1], u[2], chat, lim, p1, fixed, fs);
+                    if (fb && lx >= 0 && lx < TX && x0 + lx < g.n[0] && y0 + ly < g.n[1]) cnt.face += 1;
+                    store20(Sx, G::NSX, c, fs);
+                } else {
+                    int cy = c - G::NSX;
+                    int ly = cy / TX - 1, lx = cy % TX;
+                    R u[3][4];
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) Fy[qq * G::NFY + f] = F[qq];
+                    for (int m = 0; m < 3; ++m) {
+                        int i = G::i2(lx, ly - 1 + m);
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) u[m][qq] = Uk[qq * G::N2 + i];
+                    }
+                    int fb = face_states<1>(u[0], u[1], u[2], chat, lim, p1, fixed, fs);
+                    if (fb && ly >= 0 && ly < TY && x0 + lx < g.n[0] && y0 + ly < g.n[1]) cnt.face += 1;
+                    store20(Sy, G::NSY, cy, fs);
                 }
             }
-            // z face (k | k+1) of the own column
+            // z face (k | k+1) of the own column: face states of cell k+1, plus state of cell k kept
             R cfh[4] = {R(0), R(0), R(0), R(0)};
             if (DIM == 3) {
-                int i = G::i2(tlx, tly);
-                R a0[4], a1[4], a2[4], a3[4];
-                const R* s0 = Uh + ((k - 1 + 10) % 5) * 4 * G::N2;
-                const R* s1 = Uk;
-                const R* s2 = Uh + ((k + 1 + 10) % 5) * 4 * G::N2;
-                const R* s3 = Uh + ((k + 2 + 10) % 5) * 4 * G::N2;
+                const int i = G::i2(tlx, tly);
+                R u[3][4], fs[20];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const R* sl = Uh + ((k + m + 3) % 3) * 4 * G::N2;
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) u[m][qq] = sl[qq * G::N2 + i];
+                }
+                int fb = face_states<2>(u[0], u[1], u[2], chat, lim, p1, fixed, fs);
+                if (fb && k + 1 < z1 && own_col) cnt.face += 1;
+                R FL[4], FR[4], UL[4], UR[4];
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
-                    a0[qq] = s0[qq * G::N2 + i];
-                    a1[qq] = s1[qq * G::N2 + i];
-                    a2[qq] = s2[qq * G::N2 + i];
-                    a3[qq] = s3[qq * G::N2 + i];
+                    UL[qq] = zplus[qq];
+                    FL[qq] = zplus[4 + qq];
+                    UR[qq] = fs[qq];
+                    FR[qq] = fs[4 + qq];
                 }
-                int fbL, fbR;
-                corrector_face<2>(a0, a1, a2, a3, chat, lim, p1, fixed, cfh, fbL, fbR);
-                if (fbR && k + 1 < z1 && x0 + tlx < g.n[0] && y0 + tly < g.n[1]) cnt.face += 1;
+                hll(UL, UR, FL, FR, zplus[8], zplus[9], fs[8], fs[9], cfh);
+#pragma unroll
+                for (int qq = 0; qq < 10; ++qq) zplus[qq] = fs[10 + qq];
             }
             __syncthreads();
-            // accumulation for the own tile cell
-            const int gx = x0 + tlx, gy = y0 + tly;
-            if (gx < g.n[0] && gy < g.n[1]) {
+            // (e2) HLL fluxes on the tile's x and y faces
+            for (int f = t; f < G::NCX + G::NCY; f += G::NT) {
+                R F[4];
+                if (f < G::NCX) {
+                    int ly = f / (TX + 1), lx = f % (TX + 1);
+                    int iL = lx + (TX + 2) * ly;   // cell lx-1
+                    hll_stored(Sx, G::NSX, iL, iL + 1, F);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) Cx[qq * G::NCX + f] = F[qq];
+                } else {
+                    int fc = f - G::NCX;
+                    int ly = fc / TX, lx = fc % TX;
+                    int iL = lx + TX * ly;         // cell ly-1
+                    hll_stored(Sy, G::NSY, iL, iL + TX, F);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) Cy[qq * G::NCY + fc] = F[qq];
+                }
+            }
+            __syncthreads();
+            // (e3) accumulation for the own tile cell
+            if (own_col) {
+                const int gx = x0 + tlx, gy = y0 + tly;
                 R div[4];
                 int fl = tly * (TX + 1) + tlx;
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) div[qq] = (Fx[qq * G::NFX + fl + 1] - Fx[qq * G::NFX + fl]) * idx;
+                for (int qq = 0; qq < 4; ++qq) div[qq] = (Cx[qq * G::NCX + fl + 1] - Cx[qq * G::NCX + fl]) * idx;
                 if (G::HY) {
                     int fb = tly * TX + tlx;
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq)
-                        div[qq] = div[qq] + (Fy[qq * G::NFY + fb + TX] - Fy[qq * G::NFY + fb]) * idy;
+                        div[qq] = div[qq] + (Cy[qq * G::NCY + fb + TX] - Cy[qq * G::NCY + fb]) * idy;
                 }
                 if (DIM == 3) {
 #pragma unroll
@@ -898,13 +1096,15 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) Uhk[qq] = Uk[qq * G::N2 + ih];
                 const bool full = g.exchange == EX_FULL;
-                GasCell<R> gc = load_gas<R, SPLIT>(g, a, gx, gy, k, full || needT_pred, full);
+                GasCell<R> gc = load_gas<R, SPLIT>(g, a, gx, gy, k, false, full && !SPLIT);
                 R S[4];
                 explicit_sources(g, gc, Uhk, chat, S);
                 long long li = lin(g, gx, gy, k);
-                double U0[4] = {a.E[li], a.G[0][li], a.G[1][li], a.G[2][li]};
+                cp_async_wait_all();  // own staged copies of U^m and T for this cell
+                double U0[4] = {stC[t], stC[G::NT + t], stC[2 * G::NT + t], stC[3 * G::NT + t]};
                 double Un[4];
-                double Tn = gc.T;
+                double Tn = needT_corr ? stC[4 * G::NT + t] : 0.0;
+                gc.T = Tn;
                 if constexpr (!SPLIT) {
                     double U[4];
 #pragma unroll
@@ -932,42 +1132,48 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                     for (int qq = 0; qq < 4; ++qq) Un[qq] = U[qq];
                 } else {
                     // FP32 increment relative to the FP64 state
-                    float u0f[4] = {(float)U0[0], (float)U0[1], (float)U0[2], (float)U0[3]};
+                    float u0f[4];
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) u0f[qq] = d2f_trunc(U0[qq]);
                     float d[4];
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) d[qq] = (float)(-dt * div[qq] + dt * S[qq]);
+                    for (int qq = 0; qq < 4; ++qq) d[qq] = -dt * div[qq] + dt * S[qq];
                     const float thF = g.f_theta_F, thE = g.f_theta_E;
                     float xF = (float)chat * (float)gc.kF * (float)dt;
-                    float wF = xF / (1.0f + thF * xF);
+                    float wF = xF * rcp(1.0f + thF * xF);
 #pragma unroll
                     for (int qq = 1; qq < 4; ++qq) d[qq] -= (u0f[qq] + d[qq]) * wF;
                     if (g.exchange == EX_ABSORB) {
                         float xP = (float)chat * (float)gc.kP * (float)dt;
-                        d[0] -= (u0f[0] + d[0]) * (xP / (1.0f + thE * xP));
+                        d[0] -= (u0f[0] + d[0]) * (xP * rcp(1.0f + thE * xP));
                     } else if (g.exchange == EX_FROZEN_T) {
                         float xP = (float)chat * (float)gc.kP * (float)dt;
-                        float Tf = (float)gc.T;
+                        float Tf = d2f_trunc(gc.T);
                         float aT4 = g.f_a_rad * (Tf * Tf) * (Tf * Tf);
-                        d[0] += xP * (aT4 - (u0f[0] + d[0])) / (1.0f + thE * xP);
+                        d[0] += xP * (aT4 - (u0f[0] + d[0])) * rcp(1.0f + thE * xP);
                     }
-                    double Etr = U0[0] + (double)d[0];
+                    double Etr = U0[0] + f2d_exact(d[0]);
                     if (full) {
                         // exchange on E >= E_floor; its change is applied to the FP64 energy
-                        if (Etr < g.E_floor) Etr = g.E_floor;
+                        float Ef = u0f[0] + d[0];
+                        if (!(Ef > 2.0f * g.f_E_floor)) {
+                            if (Etr < g.E_floor) Etr = g.E_floor;
+                            Ef = d2f_trunc(Etr);
+                        }
                         ExchangeOut o;
                         float qv;
-                        float del = exchange_delta_fp32(g, (float)chat, (float)dt, (float)gc.rho, (float)gc.kP,
-                                                        (float)Etr, (float)gc.T, o, qv);
-                        Etr -= (double)(((float)chat * g.f_inv_c) * del);
-                        d[0] = (float)(Etr - U0[0]);
-                        Tn = gc.T + (double)(qv * del);
+                        float del = exchange_delta_fp32(g, (float)chat, (float)dt, gc.rho32, (float)gc.kP, Ef,
+                                                        d2f_trunc(gc.T), o, qv);
+                        Etr = Etr - f2d_exact(((float)chat * g.f_inv_c) * del);
+                        d[0] = Ef - ((float)chat * g.f_inv_c) * del - u0f[0];
+                        Tn = gc.T + f2d_exact(qv * del);
                         cnt.theta += o.theta_fb;
                         cnt.newton_fb += o.newton_fb;
                         cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
                     }
                     Un[0] = Etr;
 #pragma unroll
-                    for (int qq = 1; qq < 4; ++qq) Un[qq] = U0[qq] + (double)d[qq];
+                    for (int qq = 1; qq < 4; ++qq) Un[qq] = U0[qq] + f2d_exact(d[qq]);
                     // realizability: cheap FP32 screen, exact FP64 test only near the limit
                     float ef = u0f[0] + d[0];
                     float g2f = 0.f;
@@ -978,8 +1184,8 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                     }
                     if (!(ef > g.f_E_floor * 1.001f) || g2f > 0.9999f * ef * ef) cnt.fix += realize(Un, g.E_floor);
                 }
-                bool bad = !(isfinite(Un[0]) && isfinite(Un[1]) && isfinite(Un[2]) && isfinite(Un[3]) &&
-                             (!full || isfinite(Tn)));
+                bool bad = !(finite_d(Un[0]) && finite_d(Un[1]) && finite_d(Un[2]) && finite_d(Un[3]) &&
+                             (!full || finite_d(Tn)));
                 cnt.nonfinite += bad;
                 a.Eo[li] = Un[0];
                 a.Go[0][li] = Un[1];
@@ -994,6 +1200,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
         }
         __syncthreads();
     }
+    cp_async_wait_all();  // no copy may outlive the tile
 }
 
 template <typename R, int TX, int TY, int DIM, bool SPLIT>
