@@ -184,6 +184,35 @@ rhd_status rhd_ensemble_get_gas_state(rhd_ctx* ctx, int grid, double* T, int on_
 /* n_sub subcycles of every grid, grid g with its own dt_per_grid[g] (host array), common chat. */
 rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const double* dt_per_grid);
 
+/* ---------------------------------------------------------------------------------------------
+ * Subcycles without device allocation.  The paper has no counterpart: this is an interface for
+ * callers that cannot call cudaMalloc, for example code running while another component owns the
+ * device memory through its own pool allocator, or an application that must keep the device
+ * footprint fixed once the library is loaded.  It runs n_sub FP64 subcycles exactly as
+ * rhd_radiation_subcycle does, reading and writing only the caller's DEVICE arrays (interior cells,
+ * x fastest) plus one static scratch array that librhd.so reserves on every GPU that loads it, held
+ * until the process exits: 32 MiB for the working state, so grids of at most RHD_NOALLOC_MAX_CELLS
+ * cells (larger grids return RHD_ERR_ARG).  It calls no cudaMalloc, cudaFree or allocating routine.
+ *   d         grid descriptor; precision must be RHD_FP64; d->cuda_stream is the stream used (NULL:
+ *             legacy default stream); the call returns without synchronising unless stats != NULL
+ *   dirichlet 6 x 4 values (E, Fx, Fy, Fz) for faces 2*dir + side, or NULL (zeros)
+ *   E..Fz     input moments; rho, T required; vx, vy, vz, kP, kF, j may be NULL (as in
+ *             rhd_set_gas_state)
+ *   *_out     output moments and gas temperature (may equal the inputs: the inputs are read first)
+ *   stats     NULL, or counters of this call (sums are not computed; synchronises the stream)
+ * The first call on a device looks up the scratch address on that device (make it before any stream
+ * capture).  The scratch is shared by all calls and keeps the last call's contents; each call resets
+ * what must start at zero.  Calls whose work overlaps on the GPU (other streams or threads) race on
+ * the scratch and must be serialised by the caller.  Errors: RHD_ERR_ARG, RHD_ERR_CFL, RHD_ERR_CUDA,
+ * RHD_ERR_NONFINITE (with stats); the message is in rhd_last_error(NULL). */
+#define RHD_NOALLOC_MAX_CELLS 1048576
+rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double dirichlet[24], int n_sub, double chat,
+                                double dt, const double* E, const double* Fx, const double* Fy, const double* Fz,
+                                const double* rho, const double* T, const double* vx, const double* vy,
+                                const double* vz, const double* kP, const double* kF, const double* j,
+                                double* E_out, double* Fx_out, double* Fy_out, double* Fz_out, double* T_out,
+                                rhd_stats* stats);
+
 /* Library identification: ABI version and the compute capability it was built for (e.g. 103). */
 int rhd_abi_version(void);
 int rhd_built_arch(void);

@@ -885,3 +885,29 @@ rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const dou
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// helpers shared with the no-allocation entry point (rhd_noalloc.cu)
+// ---------------------------------------------------------------------------------------------
+namespace rhd {
+
+// Validate a descriptor and derive the launch parameters of one grid (no allocation).
+rhd_status noalloc_prepare(const rhd_grid_desc* d, GridParams* gp, int* tiles_x, int* tiles_y, int* z_chunk)
+{
+    rhd_status st = validate_desc(nullptr, d);
+    if (st) return st;
+    GridState gs;
+    gs.desc = *d;
+    gs.ncell = (long long)d->n[0] * d->n[1] * d->n[2];
+    fill_params(gs);
+    *gp = gs.gp;
+    *tiles_x = gs.tiles_x;
+    *tiles_y = gs.tiles_y;
+    *z_chunk = gs.z_chunk;
+    return RHD_OK;
+}
+
+// Record the message returned by rhd_last_error(NULL) and pass the status through.
+rhd_status noalloc_fail(rhd_status st, const std::string& msg) { return fail(nullptr, st, msg); }
+
+}  // namespace rhd

@@ -108,6 +108,8 @@ _SIGS = {
     "rhd_ensemble_get_moments": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 4 + [ctypes.c_int]),
     "rhd_ensemble_get_gas_state": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int]),
     "rhd_ensemble_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "rhd_subcycle_noalloc": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double] + [_P] * 17 + [ctypes.POINTER(Stats)]),
     "rhd_abi_version": (ctypes.c_int, []),
     "rhd_built_arch": (ctypes.c_int, []),
 }
@@ -353,3 +355,30 @@ class Ensemble:
         self.set_gas_state(g, *(None if f.get(k) is None else np.ascontiguousarray(f[k], dtype=np.float64)
                                 for k in ("rho", "T", "vx", "vy", "vz", "kP", "kF", "j")))
         self.set_moments(g, *(np.ascontiguousarray(f[k], dtype=np.float64) for k in ("E", "Fx", "Fy", "Fz")))
+
+
+NOALLOC_MAX_CELLS = 1048576
+
+
+def subcycle_noalloc(desc: dict, n_sub, chat, dt, E, Fx, Fy, Fz, rho, T, E_out, Fx_out, Fy_out, Fz_out, T_out,
+                     vx=None, vy=None, vz=None, kP=None, kF=None, j=None, stream=None, want_stats=True):
+    """rhd_subcycle_noalloc: n_sub FP64 subcycles on caller-owned device arrays (torch CUDA tensors)
+    with no device allocation by the library (for callers that cannot allocate)."""
+    n = int(desc["n"][0]) * int(desc["n"][1]) * int(desc["n"][2])
+    ins = [E, Fx, Fy, Fz, rho, T, vx, vy, vz, kP, kF, j, E_out, Fx_out, Fy_out, Fz_out, T_out]
+    ps = [_ptr(a, n, writable=(i >= 12)) for i, a in enumerate(ins)]
+    if any(p is not None and not od for p, od in ps):
+        raise ValueError("rhd_subcycle_noalloc takes device arrays only")
+    d = desc_struct(desc, stream)
+    dirs = None
+    if any(b == "dirichlet" for b in list(desc["bc_lo"]) + list(desc["bc_hi"])):
+        vals = []
+        for f in range(6):
+            dd, side = f // 2, f % 2
+            vals += [float(v) for v in (desc["dirichlet_hi"] if side else desc["dirichlet_lo"])[dd]]
+        dirs = (ctypes.c_double * 24)(*vals)
+    st = Stats()
+    status = lib().rhd_subcycle_noalloc(ctypes.byref(d), dirs, int(n_sub), float(chat), float(dt),
+                                        *[p for p, _ in ps], ctypes.byref(st) if want_stats else None)
+    _check(None, status)
+    return st.as_dict() if want_stats else None
