@@ -76,6 +76,11 @@ typedef enum { RHD_SPEEDS_M1 = 0, RHD_SPEEDS_FIXED = 1 } rhd_speeds;     /* FIXE
 typedef enum { RHD_FP64 = 0, RHD_SPLIT = 1 } rhd_precision;
 /* RHD_FLAG_NO_GRAPH: issue the n_sub launches one by one instead of replaying a captured CUDA graph. */
 #define RHD_FLAG_NO_GRAPH 1
+/* RHD_FLAG_SPLIT_FUSED: for RHD_SPLIT grids with three active directions, run each subcycle as one
+ * fused kernel (predictor recomputed on the tile halo) instead of the default predictor + corrector
+ * pair, which keeps U^{m+1/2} in an extra FP32 buffer of (n0+4)(n1+4)(n2+4) x 16 bytes.  Ignored
+ * elsewhere (ensembles always run fused). */
+#define RHD_FLAG_SPLIT_FUSED 2
 
 typedef struct {
     int n[3];                   /* nx, ny, nz */

@@ -6,8 +6,7 @@ namespace rhd {
 template <typename R, int TX, int TY, int DIM, bool SPLIT>
 static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 {
-    using G = Geo<TX, TY, DIM>;
-    const size_t smem = G::bytes(sizeof(R));
+    const size_t smem = tile_smem_bytes<R, TX, TY, DIM, SPLIT>();
     auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -19,8 +18,7 @@ static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 template <typename R, int TX, int TY, bool SPLIT>
 static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaStream_t s)
 {
-    using G = Geo<TX, TY, 3>;
-    const size_t smem = G::bytes(sizeof(R));
+    const size_t smem = tile_smem_bytes<R, TX, TY, 3, SPLIT>();
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -31,8 +29,7 @@ static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaSt
 template <typename R, int TX, int TY, bool SPLIT>
 static int ens_occupancy()
 {
-    using G = Geo<TX, TY, 3>;
-    const size_t smem = G::bytes(sizeof(R));
+    const size_t smem = tile_smem_bytes<R, TX, TY, 3, SPLIT>();
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     int n = 0;
@@ -52,6 +49,16 @@ void tile_shape(int precision, int nact, int* tx, int* ty)
         *tx = 32;
         *ty = 8;
     }
+}
+
+bool tile_supported(int precision, int nact, int tx, int ty)
+{
+    int dx, dy;
+    tile_shape(precision, nact, &dx, &dy);
+    if (tx == dx && ty == dy) return true;
+    if (nact != 3) return false;
+    if (precision == 0) return false;
+    return (tx == 32 && ty == 16) || (tx == 64 && ty == 8);
 }
 
 cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s)

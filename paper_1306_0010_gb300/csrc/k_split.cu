@@ -6,8 +6,7 @@ namespace rhd {
 template <typename R, int TX, int TY, int DIM, bool SPLIT>
 static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 {
-    using G = Geo<TX, TY, DIM>;
-    const size_t smem = G::bytes(sizeof(R));
+    const size_t smem = tile_smem_bytes<R, TX, TY, DIM, SPLIT>();
     auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -19,8 +18,7 @@ static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 template <typename R, int TX, int TY, bool SPLIT>
 static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaStream_t s)
 {
-    using G = Geo<TX, TY, 3>;
-    const size_t smem = G::bytes(sizeof(R));
+    const size_t smem = tile_smem_bytes<R, TX, TY, 3, SPLIT>();
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -31,8 +29,7 @@ static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaSt
 template <typename R, int TX, int TY, bool SPLIT>
 static int ens_occupancy()
 {
-    using G = Geo<TX, TY, 3>;
-    const size_t smem = G::bytes(sizeof(R));
+    const size_t smem = tile_smem_bytes<R, TX, TY, 3, SPLIT>();
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
     int n = 0;
@@ -46,13 +43,47 @@ cudaError_t launch_subcycle_split(const StepParams& p, cudaStream_t s)
     switch (p.g.nact) {
     case 1: return launch_tile_kernel<float, 128, 1, 1, true>(p, s);
     case 2: return launch_tile_kernel<float, 32, 8, 2, true>(p, s);
-    default: return launch_tile_kernel<float, 32, 8, 3, true>(p, s);
+    default:
+        if (p.ty == 16) return launch_tile_kernel<float, 32, 16, 3, true>(p, s);
+        if (p.tx == 64) return launch_tile_kernel<float, 64, 8, 3, true>(p, s);
+        return launch_tile_kernel<float, 32, 8, 3, true>(p, s);
     }
 }
 
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s)
 {
     return launch_ens_kernel<float, 32, 8, true>(p, n_ctas, s);
+}
+
+// Two-pass split subcycle (3D): predictor over the grid padded by two ghost layers, then corrector.
+cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s)
+{
+    constexpr int TX = 32, TY = 8;
+    const int zc = p.z_chunk;
+    StepParams pp = p;
+    pp.tiles_x = (p.g.n[0] + 4 + TX - 1) / TX;
+    pp.tiles_y = (p.g.n[1] + 4 + TY - 1) / TY;
+    {
+        auto k = predictor_kernel<TX, TY>;
+        const size_t smem = GeoPred<TX, TY>::bytes();
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(pp.tiles_x * pp.tiles_y), (unsigned)((p.g.n[2] + 4 + zc - 1) / zc));
+        k<<<grid, TX * TY, smem, s>>>(pp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    StepParams pc = p;
+    pc.tiles_x = (p.g.n[0] + TX - 1) / TX;
+    pc.tiles_y = (p.g.n[1] + TY - 1) / TY;
+    {
+        auto k = corrector_kernel<TX, TY>;
+        const size_t smem = GeoCorr<TX, TY>::bytes();
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(pc.tiles_x * pc.tiles_y), (unsigned)((p.g.n[2] + zc - 1) / zc));
+        k<<<grid, TX * TY, smem, s>>>(pc);
+        return cudaGetLastError();
+    }
 }
 
 int ensemble_ctas_per_sm_split() { return ens_occupancy<float, 32, 8, true>(); }

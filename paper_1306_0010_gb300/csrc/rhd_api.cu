@@ -49,6 +49,8 @@ struct GridState {
     float* j32 = nullptr;
     bool has_v = false, has_kP = false, has_kF = false, has_j = false;
     bool has_moments = false, has_gas = false;
+    int variant = 0;              // split 3D: 0 fused kernel, 1 two-pass (predictor + corrector)
+    float4* uhalf = nullptr;      // two-pass: padded U^{m+1/2}
 };
 
 }  // namespace
@@ -205,6 +207,13 @@ void fill_params(GridState& gs)
     g.f_kappa_P = (float)d.kappa_P;
     g.f_kappa_F = (float)d.kappa_F;
     tile_shape(d.precision, g.nact, &gs.tx, &gs.ty);
+    if (const char* ov = std::getenv("RHD_TILE")) {  // "TXxTY": measurement override of the tile shape
+        int tx = 0, ty = 0;
+        if (std::sscanf(ov, "%dx%d", &tx, &ty) == 2 && tile_supported(d.precision, g.nact, tx, ty)) {
+            gs.tx = tx;
+            gs.ty = ty;
+        }
+    }
     gs.tiles_x = (d.n[0] + gs.tx - 1) / gs.tx;
     gs.tiles_y = (d.n[1] + gs.ty - 1) / gs.ty;
     int zc = d.z_chunk;
@@ -254,6 +263,7 @@ void free_grid(GridState& gs)
     dfree(gs.kP32);
     dfree(gs.kF32);
     dfree(gs.j32);
+    dfree(gs.uhalf);
 }
 
 void clear_graphs(rhd_ctx* ctx)
@@ -276,6 +286,11 @@ rhd_status alloc_grid(rhd_ctx* ctx, GridState& gs)
     if (st) return st;
     if (gs.desc.precision == RHD_SPLIT) {
         st = dalloc(ctx, (void**)&gs.rho32, sizeof(float) * (size_t)gs.ncell);
+        if (st) return st;
+    }
+    if (gs.variant == 1) {
+        size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
+        st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np);
         if (st) return st;
     }
     return RHD_OK;
@@ -461,7 +476,10 @@ StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double
     a.j32 = gs.has_j ? gs.j32 : nullptr;
     p.chat = chat;
     p.dt = dt;
+    p.uhalf = gs.uhalf;
     p.z_chunk = gs.z_chunk;
+    p.tx = gs.tx;
+    p.ty = gs.ty;
     p.tiles_x = gs.tiles_x;
     p.tiles_y = gs.tiles_y;
     p.stats = ctx->dstats;
@@ -484,8 +502,9 @@ rhd_status check_dt(rhd_ctx* ctx, const GridState& gs, double chat, double dt)
 rhd_status launch_one(rhd_ctx* ctx, GridState& gs, int src, double chat, double dt)
 {
     StepParams p = step_params(ctx, gs, src, chat, dt);
-    cudaError_t e = gs.desc.precision == RHD_SPLIT ? launch_subcycle_split(p, ctx->stream)
-                                                    : launch_subcycle_fp64(p, ctx->stream);
+    cudaError_t e = gs.desc.precision != RHD_SPLIT ? launch_subcycle_fp64(p, ctx->stream)
+                    : gs.variant == 1              ? launch_twopass_split(p, ctx->stream)
+                                                   : launch_subcycle_split(p, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("subcycle launch: ") + cudaGetErrorString(e));
     return RHD_OK;
 }
@@ -573,6 +592,14 @@ rhd_status rhd_init_grid(rhd_ctx** out, const rhd_grid_desc* d)
         gs.desc = *d;
         gs.ncell = (long long)d->n[0] * d->n[1] * d->n[2];
         fill_params(gs);
+        // split 3D grids: the two-pass kernels unless the fused kernel is asked for
+        if (d->precision == RHD_SPLIT && gs.gp.nact == 3) {
+            gs.variant = (d->flags & RHD_FLAG_SPLIT_FUSED) ? 0 : 1;
+            if (const char* v = std::getenv("RHD_VARIANT")) gs.variant = std::strcmp(v, "fused") == 0 ? 0 : 1;
+            // the two kernels recompute nothing across z chunks but two predictor planes: short chunks
+            // cost little and fill the GPU evenly
+            if (gs.variant == 1 && d->z_chunk == 0) gs.z_chunk = std::min(32, d->n[2]);
+        }
         st = alloc_grid(ctx, gs);
     }
     if (st) {

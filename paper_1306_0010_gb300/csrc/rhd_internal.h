@@ -62,7 +62,9 @@ struct StepParams {
     GridParams g;
     GridArrays a;
     double chat, dt;
+    float4* uhalf;              // two-pass split path: U^{m+1/2} on the grid padded by 2 ghost layers
     int z_chunk;                // planes per CTA
+    int tx, ty;                 // tile shape (selects the kernel instantiation)
     int tiles_x, tiles_y;       // tile grid in x, y
     DevStats* stats;
 };
@@ -89,13 +91,15 @@ struct EnsembleParams {
 // Launch wrappers (defined in the kernel translation units).
 cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s);
 cudaError_t launch_subcycle_split(const StepParams& p, cudaStream_t s);
+cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s);
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 int ensemble_ctas_per_sm_fp64();
 int ensemble_ctas_per_sm_split();
 
-// Tile geometry chosen per precision and dimensionality.
+// Tile geometry: the default per precision and dimensionality, and the shapes compiled for 3D.
 void tile_shape(int precision, int nact, int* tx, int* ty);
+bool tile_supported(int precision, int nact, int tx, int ty);
 
 // Auxiliary kernels (k_aux.cu).
 cudaError_t launch_scale_copy(double* dst, const double* src, double scale, long long n, cudaStream_t s);

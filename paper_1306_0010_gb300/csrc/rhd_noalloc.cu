@@ -126,6 +126,8 @@ extern "C" rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double 
     p.chat = chat;
     p.dt = dt;
     p.z_chunk = z_chunk;
+    p.tx = 16;
+    p.ty = 8;
     p.tiles_x = tiles_x;
     p.tiles_y = tiles_y;
     p.stats = dstats;

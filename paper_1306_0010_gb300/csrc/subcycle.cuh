@@ -1203,8 +1203,22 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
     cp_async_wait_all();  // no copy may outlive the tile
 }
 
+}  // namespace rhd
+
+#include "subcycle_pair.cuh"
+#include "subcycle_twopass.cuh"
+
+namespace rhd {
+
+// shared-memory bytes of a tile routine
 template <typename R, int TX, int TY, int DIM, bool SPLIT>
-__global__ void __launch_bounds__(TX* TY, 2) subcycle_kernel(const __grid_constant__ StepParams P)
+constexpr size_t tile_smem_bytes()
+{
+    return Geo<TX, TY, DIM>::bytes(sizeof(R));
+}
+
+template <typename R, int TX, int TY, int DIM, bool SPLIT>
+__global__ void __launch_bounds__(TX* TY, (TX * TY > 256) ? 1 : 2) subcycle_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
@@ -1229,7 +1243,7 @@ __global__ void __launch_bounds__(TX* TY, 2) subcycle_kernel(const __grid_consta
 // Persistent ensemble kernel: CTAs pull (grid, tile) items from a global counter until the queue is
 // empty; the item-to-grid map is a prefix sum over the grids' tile counts (binary search).
 template <typename R, int TX, int TY, bool SPLIT>
-__global__ void __launch_bounds__(TX* TY, 2) ensemble_kernel(const __grid_constant__ EnsembleParams P)
+__global__ void __launch_bounds__(TX* TY, (TX * TY > 256) ? 1 : 2) ensemble_kernel(const __grid_constant__ EnsembleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);

@@ -27,6 +27,7 @@ CLOSURE = {"m1": 0, "p1": 1}
 SPEEDS = {"m1": 0, "fixed": 1}
 PRECISION = {"fp64": 0, "split": 1}
 FLAG_NO_GRAPH = 1
+FLAG_SPLIT_FUSED = 2
 
 
 class RhdError(RuntimeError):

@@ -170,25 +170,45 @@ def test_config4_reduced_fp64(rhd):
 SPLIT_TOL = 2e-5
 
 
+# split 3D grids run as a predictor + corrector kernel pair by default, or as one fused kernel
+SPLIT_VARIANTS = [("twopass", 0), ("fused", 2)]
+
+
+@pytest.mark.parametrize("variant,flags", SPLIT_VARIANTS, ids=[v for v, _ in SPLIT_VARIANTS])
 @pytest.mark.parametrize("kw", FP64_CASES[:6] + FP64_CASES[6:8], ids=[c["name"] for c in FP64_CASES[:8]])
-def test_split_error_bound_small(rhd, kw):
+def test_split_error_bound_small(rhd, kw, variant, flags):
     kw = dict(kw)
     name = kw.pop("name")
     n = kw.pop("n")
     case = wl.parity_case(name, n, n_sub=4, seed=zlib.crc32(name.encode()) % 1000, precision="split", **kw)
-    out, st = run_gpu(rhd, case)
+    out, st = run_gpu(rhd, case, desc_over={"flags": flags})
     ref, _ = orc.subcycles(case)
     e = errors(out, ref, case["desc"])
     assert max(e.values()) <= SPLIT_TOL, e
     assert st["n_nonfinite"] == 0
 
 
-def test_config4_reduced_split(rhd):
+@pytest.mark.parametrize("variant,flags", SPLIT_VARIANTS, ids=[v for v, _ in SPLIT_VARIANTS])
+def test_config4_reduced_split(rhd, variant, flags):
     case = wl.config4(N=32, n_sub=10, precision="split")
-    out, _ = run_gpu(rhd, case)
+    out, _ = run_gpu(rhd, case, desc_over={"flags": flags})
     ref, _ = orc.subcycles(case)
     e = errors(out, ref, case["desc"])
     assert max(e.values()) <= SPLIT_TOL, e
+
+
+def test_split_twopass_z_chunks(rhd):
+    """Predictor chunks cover the padded z range [-2, n+2) and corrector chunks the interior; ragged
+    chunks of either kernel must not change the result beyond the split bound."""
+    case = wl.parity_case("zchunk_split", (37, 11, 23), bc=(["periodic", "outflow", "reflect"],
+                                                            ["periodic", "outflow", "outflow"]),
+                          exchange="full", beta_tau=True, n_sub=3, seed=9, precision="split")
+    ref, _ = orc.subcycles(case)
+    for zc in (1, 3, 7, 23, 40):
+        out, st = run_gpu(rhd, case, desc_over={"z_chunk": zc})
+        e = errors(out, ref, case["desc"])
+        assert max(e.values()) <= SPLIT_TOL, (zc, e)
+        assert st["n_nonfinite"] == 0
 
 
 # ----------------------------------------------------------------------------- full size (sampled)
@@ -198,13 +218,14 @@ def config4_full():
     return wl.config4(N=512, n_sub=1)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("split", SPLIT_TOL)])
-def test_config4_full_size_sampled(rhd, config4_full, precision, tol):
+@pytest.mark.parametrize("precision,tol,flags", [("fp64", FP64_TOL, 0), ("split", SPLIT_TOL, 0),
+                                                 ("split", SPLIT_TOL, 2)], ids=["fp64", "split", "split_fused"])
+def test_config4_full_size_sampled(rhd, config4_full, precision, tol, flags):
     """512^3 throughput configuration, one subcycle in the launch configuration the benchmark times;
     the oracle recomputes sampled 6^3 boxes (one at the periodic corner) and every element of each
     box must match."""
     case = dict(config4_full)
-    case["desc"] = dict(case["desc"], precision=precision)
+    case["desc"] = dict(case["desc"], precision=precision, flags=flags)
     out, st = run_gpu(rhd, case, n_sub=1)
     assert st["n_nonfinite"] == 0
     N = 512
