@@ -35,6 +35,9 @@ B_ALG = {"fp64": 64 + 16 + 8 + 24, "split": 64 + 16 + 4 + 12}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--launch", default="auto",
+                    help="split-path launch configuration: 'auto' (autotune before timing) or "
+                         "VARIANT:TXxTY:zZCHUNK:STAGING, e.g. twopass:32x8:z32:cpasync")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -156,6 +159,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def launch_key(launch):
+    return f"{launch['variant']}:{launch['tile'][0]}x{launch['tile'][1]}:z{launch['z_chunk']}:{launch['staging']}"
+
+
 def workload_config(args, precision):
     return {"workload": f"3D throughput run, {args.N}^3 periodic SoA grid, lognormal rho (sigma_ln rho = 1), "
                         f"v ~ N(0, (0.001 c)^2), k = 512 rho, |F| <= 0.5 cE, FULL exchange, beta tau on, "
@@ -164,7 +171,16 @@ def workload_config(args, precision):
             "l2": "inputs larger than L2 (1.07 GB per FP64 field)"}
 
 
-def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream):
+def parse_launch(spec):
+    v, t, z, stg = spec.split(":")
+    tx, ty = (int(x) for x in t.split("x"))
+    return {"variant": v, "tile": (tx, ty), "z_chunk": int(z.lstrip("z")), "staging": stg}
+
+
+def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=True, launch_spec="auto"):
+    """Device-resident run: autotune the launch configuration (untimed), warm up, then time `steps`
+    calls of n_sub subcycles with CUDA events on the library's stream.  The kernel timer brackets
+    every kernel of the timed region with events on the same stream (plain launches)."""
     desc = dict(case["desc"], precision=precision)
     g = rhd.Grid(desc, stream=stream.cuda_stream)
     f = case["fields"]
@@ -173,9 +189,18 @@ def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream):
         g.set_gas_state(dev["rho"], dev["T"], dev["vx"], dev["vy"], dev["vz"], dev["kP"], dev["kF"], dev["j"])
         g.set_moments(dev["E"], dev["Fx"], dev["Fy"], dev["Fz"])
     stream.synchronize()
+    tuning = None
+    if tune and launch_spec != "auto":
+        g.set_launch_config(parse_launch(launch_spec))
+    elif tune:
+        chosen, table = g.autotune(case["chat"], case["dt"], reps=3)
+        tuning = {"chosen": chosen, "candidates": table}
+    launch = g.launch_config()
+    g.set_kernel_timing(True)
     for _ in range(warmup):
         g.radiation_subcycle(n_sub, case["chat"], case["dt"])
     stream.synchronize()
+    g.kernel_times()  # discard the warm-up interval
     g.reset_stats()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     ev[0].record(stream)
@@ -185,17 +210,35 @@ def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream):
     stream.synchronize()
     per_step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
+    kt = g.kernel_times()
     st = g.get_stats(allow_nonfinite=True)
     g.close()
     del dev
-    return total_ms, per_step_ms, st
+    return total_ms, per_step_ms, st, kt, launch, tuning
 
 
-def time_e2e(torch, rhd, case, precision, n_sub, steps, warmup):
+def kernel_roofline(kt, peak, peak_kind):
+    """Roofline of the kernel with the largest share of the timed region: algorithmic bytes of one
+    launch over its mean event-measured duration."""
+    name = max(kt, key=lambda k: kt[k]["total_ms"])
+    k = kt[name]
+    mean_ms = k["total_ms"] / k["launches"]
+    achieved = k["alg_bytes_per_launch"] / (mean_ms * 1e-3) / 1e9
+    total = sum(v["total_ms"] for v in kt.values())
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind, "kernel": name, "launch_ms": mean_ms,
+            "alg_bytes_per_launch": k["alg_bytes_per_launch"], "share_of_kernel_time": k["total_ms"] / total}
+
+
+def time_e2e(torch, rhd, case, precision, n_sub, steps, warmup, launch_spec="auto"):
     """Same metric through the public API with host (pinned) buffers: per step, H2D of the moments and
-    gas state, the subcycles, D2H of the moments and temperature."""
-    desc = dict(case["desc"], precision=precision)
+    gas state, the subcycles, D2H of the moments and temperature.  The launch configuration is the
+    autotuner's (RHD_FLAG_AUTOTUNE: reused from the device-resident run's tuning of the same shape)
+    or the one given."""
+    desc = dict(case["desc"], precision=precision, flags=rhd.FLAG_AUTOTUNE if launch_spec == "auto" else 0)
     g = rhd.Grid(desc)
+    if launch_spec != "auto":
+        g.set_launch_config(parse_launch(launch_spec))
     f = case["fields"]
     pin = {k: (None if f[k] is None else torch.from_numpy(f[k]).pin_memory()) for k in f}
     outs = [torch.empty(f["E"].shape, dtype=torch.float64).pin_memory() for _ in range(5)]
@@ -252,7 +295,8 @@ def main():
     torch.cuda.synchronize()
     clk = ClockSampler(lrank)
     clk.start()
-    total_ms, per_step, st = time_path(torch, rhd, case, "split", args.n_sub, args.steps, args.warmup, stream)
+    total_ms, per_step, st, kt, launch, tuning = time_path(torch, rhd, case, "split", args.n_sub, args.steps,
+                                                           args.warmup, stream, launch_spec=args.launch)
     clocks = clk.stop()
     if ws > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -261,33 +305,32 @@ def main():
         dist.barrier()
     units = cells * args.n_sub * args.steps * ws
     value = units / (total_ms * 1e-3)
-    launch_ms = total_ms / (args.steps * args.n_sub)
-    achieved = B_ALG["split"] * cells / (launch_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "bytes_per_cell_update": B_ALG["split"], "kernel": "subcycle_kernel<float,32,8,3,split>",
-                "launch_ms": launch_ms}
+    sub_ms = total_ms / (args.steps * args.n_sub)
+    roofline = kernel_roofline(kt, hbm_peak, peak_kind)
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_path):
-        tr = json.load(open(traffic_path)).get("split")
-        if tr and tr.get("N") == args.N:
+        tr = json.load(open(traffic_path)).get(roofline["kernel"])
+        if tr and tr.get("N") == args.N and tr.get("launch") == launch_key(launch):
             roofline["traffic"] = tr["bytes_per_launch"]
+    # the whole subcycle against the method's own bytes per cell-update (U^m, gas, T in; U^{m+1}, T out)
+    sub_achieved = B_ALG["split"] * cells / (sub_ms * 1e-3) / 1e9
+    subcycle_roofline = {"bound": "hbm", "achieved": sub_achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": sub_achieved / hbm_peak, "bytes_per_cell_update": B_ALG["split"],
+                         "subcycle_ms": sub_ms}
 
     extra = {}
     if not args.no_fp64:
-        fp_ms, fp_steps, fst = time_path(torch, rhd, case, "fp64", args.fp64_n_sub, max(2, args.steps // 2),
-                                         args.warmup, stream)
+        fp_ms, fp_steps, fst, fkt, flaunch, _ = time_path(torch, rhd, case, "fp64", args.fp64_n_sub,
+                                                          max(2, args.steps // 2), args.warmup, stream, tune=False)
         fn = max(2, args.steps // 2)
         fv = cells * args.fp64_n_sub * fn / (fp_ms * 1e-3) * ws
         f_launch = fp_ms / (fn * args.fp64_n_sub)
-        fa = B_ALG["fp64"] * cells / (f_launch * 1e-3) / 1e9
         extra["fp64_path"] = {"value": fv, "unit": UNIT, "n_sub_per_step": args.fp64_n_sub,
-                              "launch_ms": f_launch, "split_speedup": value / fv,
-                              "roofline": {"bound": "hbm", "achieved": fa, "peak": hbm_peak, "unit": "GB/s",
-                                           "frac": fa / hbm_peak, "bytes_per_cell_update": B_ALG["fp64"]}}
+                              "launch_ms": f_launch, "split_speedup": value / fv, "launch": flaunch,
+                              "roofline": kernel_roofline(fkt, hbm_peak, peak_kind)}
     e2e = None
     if not args.no_e2e and rank == 0:
-        el, h2d, d2h = time_e2e(torch, rhd, case, "split", args.n_sub, max(2, args.steps // 2), 1)
+        el, h2d, d2h = time_e2e(torch, rhd, case, "split", args.n_sub, max(2, args.steps // 2), 1, args.launch)
         n_e = max(2, args.steps // 2)
         e2e = {"value": cells * args.n_sub * n_e / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
@@ -298,8 +341,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-                "config": workload_config(args, "split"), "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": args.steps * args.n_sub, "clocks": clocks,
+                "config": dict(workload_config(args, "split"), launch=launch),
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clocks,
+                "subcycle_roofline": subcycle_roofline, "kernels": kt, "autotune": tuning,
                 "stats": {k: st[k] for k in ("n_realizability_fix", "n_face_fallback", "n_theta_fallback",
                                              "n_nonfinite", "newton_iter_max")},
                 "per_step_ms": per_step}

@@ -81,6 +81,11 @@ typedef enum { RHD_FP64 = 0, RHD_SPLIT = 1 } rhd_precision;
  * pair, which keeps U^{m+1/2} in an extra FP32 buffer of (n0+4)(n1+4)(n2+4) x 16 bytes.  Ignored
  * elsewhere (ensembles always run fused). */
 #define RHD_FLAG_SPLIT_FUSED 2
+/* RHD_FLAG_AUTOTUNE: the first rhd_radiation_subcycle / rhd_ensemble_subcycle call runs the
+ * autotuner (rhd_autotune / rhd_ensemble_autotune, 3 timed subcycles per candidate) on the state
+ * then loaded, unless a context of the same shape and mode was tuned before in this process, whose
+ * choice is reused. */
+#define RHD_FLAG_AUTOTUNE 4
 
 typedef struct {
     int n[3];                   /* nx, ny, nz */
@@ -188,6 +193,66 @@ rhd_status rhd_ensemble_get_moments(rhd_ctx* ctx, int grid, double* E, double* F
 rhd_status rhd_ensemble_get_gas_state(rhd_ctx* ctx, int grid, double* T, int on_device);
 /* n_sub subcycles of every grid, grid g with its own dt_per_grid[g] (host array), common chat. */
 rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const double* dt_per_grid);
+
+/* ---------------------------------------------------------------------------------------------
+ * Launch configuration and autotuner.  The paper has no counterpart (its code runs on CPUs); these
+ * pick how the subcycle kernels are laid out on the GPU, never what they compute: every candidate
+ * gives results within the error bound of its precision.
+ *   variant   RHD_VARIANT_FUSED: one kernel per subcycle; the predictor (U^{m+1/2}) is recomputed
+ *             on the 2-cell halo of each x-y tile.  RHD_VARIANT_TWOPASS (RHD_SPLIT, 3D grids only):
+ *             a predictor kernel writes U^{m+1/2} (FP32) for the grid plus 2 ghost layers, then a
+ *             corrector kernel reads it back; extra device memory (n0+4)(n1+4)(n2+4) x 16 bytes.
+ *   tile_x, tile_y   cells per CTA tile in x and y (the supported shapes are those the tuner lists)
+ *   z_chunk   planes per CTA along z (each CTA marches its tile through a chunk of planes)
+ *   staging   RHD_STAGING_CPASYNC: the tile and its halo are staged into shared memory with per-
+ *             thread asynchronous copies.  RHD_STAGING_TMA (two-pass corrector): the tile + 2-cell
+ *             halo of U^{m+1/2} is fetched with one tensor-memory-accelerator copy per plane.
+ * ------------------------------------------------------------------------------------------- */
+#define RHD_VARIANT_FUSED 0
+#define RHD_VARIANT_TWOPASS 1
+#define RHD_STAGING_CPASYNC 0
+#define RHD_STAGING_TMA 1
+typedef struct {
+    int variant, tile_x, tile_y, z_chunk, staging;
+    double ms_per_subcycle;     /* rhd_autotune: measured mean time per subcycle; < 0: candidate failed */
+} rhd_launch_config;
+
+/* Time every candidate configuration of a single-grid context on its current state (moments and
+ * gas must be set; chat and dt as for rhd_radiation_subcycle) with reps >= 1 timed subcycles each
+ * (plain launches, after one warm-up), then keep the fastest.  The grid's state (E, F, T) and the
+ * statistics are left exactly as they were; captured graphs are dropped.  table (may be NULL)
+ * receives up to capacity entries, *n_entries (may be NULL) the number of candidates, *chosen (may
+ * be NULL) the configuration kept.  Synchronises the context's stream.  Errors: RHD_ERR_ARG,
+ * RHD_ERR_STATE (state not set, or an ensemble context), RHD_ERR_OOM / RHD_ERR_CUDA. */
+rhd_status rhd_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_launch_config* table, int capacity,
+                        int* n_entries, rhd_launch_config* chosen);
+/* The same for an ensemble context: candidates are the z_chunk values shared by all grids. */
+rhd_status rhd_ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_grid, int reps,
+                                 rhd_launch_config* table, int capacity, int* n_entries,
+                                 rhd_launch_config* chosen);
+/* Read the configuration in use (ms_per_subcycle is that of the last tuning, or -1). */
+rhd_status rhd_get_launch_config(rhd_ctx* ctx, rhd_launch_config* out);
+/* Select a configuration explicitly (single-grid contexts); RHD_ERR_ARG if it is not supported for
+ * this grid's precision and dimension.  Drops captured graphs. */
+rhd_status rhd_set_launch_config(rhd_ctx* ctx, const rhd_launch_config* cfg);
+
+/* ---------------------------------------------------------------------------------------------
+ * Kernel timer.  While enabled, subcycles are issued as plain launches (no graph) with a CUDA event
+ * recorded on the context's stream before and after every kernel.  rhd_get_kernel_times
+ * synchronises the stream and returns, per kernel, the launches and their summed event-measured
+ * duration since the timer was enabled or last read (then starts a new interval), and the
+ * algorithmic bytes of one launch: every input array read once and every output written once
+ * (U^m and U^{m+1} 32 B/cell in FP64, U^{m+1/2} 16 B/cell in FP32, gas arrays 4 B (split) or 8 B
+ * (FP64) each, T 8 B read and / or written as the exchange mode needs).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+    char name[48];              /* e.g. "twopass_corrector_split" */
+    int64_t launches;
+    double total_ms;
+    double alg_bytes_per_launch;
+} rhd_kernel_time;
+rhd_status rhd_set_kernel_timing(rhd_ctx* ctx, int enable);
+rhd_status rhd_get_kernel_times(rhd_ctx* ctx, rhd_kernel_time* out, int capacity, int* n_entries);
 
 /* ---------------------------------------------------------------------------------------------
  * Subcycles without device allocation.  The paper has no counterpart: this is an interface for

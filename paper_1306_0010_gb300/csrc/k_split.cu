@@ -56,35 +56,45 @@ cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStrea
 }
 
 // Two-pass split subcycle (3D): predictor over the grid padded by two ghost layers, then corrector.
-cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s)
+cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s)
 {
     constexpr int TX = 32, TY = 8;
     const int zc = p.z_chunk;
     StepParams pp = p;
     pp.tiles_x = (p.g.n[0] + 4 + TX - 1) / TX;
     pp.tiles_y = (p.g.n[1] + 4 + TY - 1) / TY;
-    {
-        auto k = predictor_kernel<TX, TY>;
-        const size_t smem = GeoPred<TX, TY>::bytes();
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)(pp.tiles_x * pp.tiles_y), (unsigned)((p.g.n[2] + 4 + zc - 1) / zc));
-        k<<<grid, TX * TY, smem, s>>>(pp);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    auto k = predictor_kernel<TX, TY>;
+    const size_t smem = GeoPred<TX, TY>::bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(pp.tiles_x * pp.tiles_y), (unsigned)((p.g.n[2] + 4 + zc - 1) / zc));
+    k<<<grid, TX * TY, smem, s>>>(pp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s)
+{
+    constexpr int TX = 32, TY = 8;
+    const int zc = p.z_chunk;
     StepParams pc = p;
     pc.tiles_x = (p.g.n[0] + TX - 1) / TX;
     pc.tiles_y = (p.g.n[1] + TY - 1) / TY;
-    {
-        auto k = corrector_kernel<TX, TY>;
-        const size_t smem = GeoCorr<TX, TY>::bytes();
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)(pc.tiles_x * pc.tiles_y), (unsigned)((p.g.n[2] + zc - 1) / zc));
-        k<<<grid, TX * TY, smem, s>>>(pc);
-        return cudaGetLastError();
-    }
+    auto k = corrector_kernel<TX, TY>;
+    const size_t smem = GeoCorr<TX, TY>::bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(pc.tiles_x * pc.tiles_y), (unsigned)((p.g.n[2] + zc - 1) / zc));
+    k<<<grid, TX * TY, smem, s>>>(pc);
+    return cudaGetLastError();
 }
+
+cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s)
+{
+    cudaError_t e = launch_twopass_predictor(p, s);
+    return e != cudaSuccess ? e : launch_twopass_corrector(p, s);
+}
+
+bool tma_available() { return false; }
 
 int ensemble_ctas_per_sm_split() { return ens_occupancy<float, 32, 8, true>(); }
 

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -49,8 +51,11 @@ struct GridState {
     float* j32 = nullptr;
     bool has_v = false, has_kP = false, has_kF = false, has_j = false;
     bool has_moments = false, has_gas = false;
-    int variant = 0;              // split 3D: 0 fused kernel, 1 two-pass (predictor + corrector)
+    int variant = 0;              // RHD_VARIANT_FUSED / RHD_VARIANT_TWOPASS
+    int staging = 0;              // RHD_STAGING_*
     float4* uhalf = nullptr;      // two-pass: padded U^{m+1/2}
+    bool tuned = false;           // RHD_FLAG_AUTOTUNE handled
+    double tuned_ms = -1.0;       // time per subcycle measured by the last tuning
 };
 
 }  // namespace
@@ -73,6 +78,12 @@ struct rhd_ctx {
     std::vector<GraphEntry> graphs;
     unsigned long long stamp = 0;
     std::string err;
+    // kernel timing: events recorded around each kernel launch (plain launches while enabled)
+    bool ktiming = false;
+    std::vector<cudaEvent_t> kev;          // event pool, reused after each read
+    size_t kev_used = 0;
+    struct KRec { int kernel; size_t e0, e1; double alg_bytes; };
+    std::vector<KRec> krec;
     // ensemble
     EnsembleGrid* d_egrids[2] = {nullptr, nullptr};
     unsigned long long* d_counter = nullptr;
@@ -328,6 +339,7 @@ void destroy_ctx(rhd_ctx* ctx)
     dfree(ctx->d_counter);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    for (auto e : ctx->kev) cudaEventDestroy(e);
     if (ctx->stream && ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -499,14 +511,72 @@ rhd_status check_dt(rhd_ctx* ctx, const GridState& gs, double chat, double dt)
     return RHD_OK;
 }
 
+// kernels reported by the kernel timer
+enum KernelId { K_FUSED_FP64 = 0, K_FUSED_SPLIT, K_PREDICTOR, K_CORRECTOR, K_ENS_FP64, K_ENS_SPLIT, K_COUNT };
+const char* const kKernelNames[K_COUNT] = {"subcycle_fused_fp64", "subcycle_fused_split", "twopass_predictor_split",
+                                           "twopass_corrector_split", "ensemble_fp64", "ensemble_split"};
+
+// Algorithmic bytes per interior cell of one launch of kernel k: every input read once, every output
+// written once (U = 4 FP64 moments, U^{m+1/2} = 4 FP32, gas arrays in the kernel's precision).
+double alg_bytes_per_cell(const GridState& gs, int k)
+{
+    const bool split = gs.desc.precision == RHD_SPLIT;
+    const double w = split ? 4.0 : 8.0;
+    const double gas = w * (1 + (gs.has_v ? 3 : 0) + (gs.has_kP ? 1 : 0) + (gs.has_kF ? 1 : 0) + (gs.has_j ? 1 : 0));
+    const int ex = gs.desc.exchange;
+    const double Tr = (ex == RHD_EX_FULL || ex == RHD_EX_FROZEN_T) ? 8.0 : 0.0, Tw = ex == RHD_EX_FULL ? 8.0 : 0.0;
+    switch (k) {
+    case K_PREDICTOR: return 32.0 + gas + (ex == RHD_EX_FROZEN_T ? 8.0 : 0.0) + 16.0;
+    case K_CORRECTOR: return 16.0 + 32.0 + gas + Tr + 32.0 + Tw;
+    default: return 32.0 + gas + Tr + 32.0 + Tw;
+    }
+}
+
+rhd_status kev_record(rhd_ctx* ctx, size_t* idx)
+{
+    if (ctx->kev_used == ctx->kev.size()) {
+        cudaEvent_t e = nullptr;
+        RHD_CUDA(ctx, cudaEventCreate(&e));
+        ctx->kev.push_back(e);
+    }
+    *idx = ctx->kev_used++;
+    RHD_CUDA(ctx, cudaEventRecord(ctx->kev[*idx], ctx->stream));
+    return RHD_OK;
+}
+
+// Launch fn, bracketed by timing events when the kernel timer is on.
+template <typename Fn>
+rhd_status timed_launch(rhd_ctx* ctx, int kernel, double alg_bytes, Fn&& fn)
+{
+    size_t e0 = 0, e1 = 0;
+    rhd_status st;
+    if (ctx->ktiming && (st = kev_record(ctx, &e0))) return st;
+    cudaError_t e = fn();
+    if (e != cudaSuccess)
+        return fail(ctx, RHD_ERR_CUDA, std::string(kKernelNames[kernel]) + " launch: " + cudaGetErrorString(e));
+    if (ctx->ktiming) {
+        if ((st = kev_record(ctx, &e1))) return st;
+        ctx->krec.push_back({kernel, e0, e1, alg_bytes});
+    }
+    return RHD_OK;
+}
+
 rhd_status launch_one(rhd_ctx* ctx, GridState& gs, int src, double chat, double dt)
 {
     StepParams p = step_params(ctx, gs, src, chat, dt);
-    cudaError_t e = gs.desc.precision != RHD_SPLIT ? launch_subcycle_fp64(p, ctx->stream)
-                    : gs.variant == 1              ? launch_twopass_split(p, ctx->stream)
-                                                   : launch_subcycle_split(p, ctx->stream);
-    if (e != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("subcycle launch: ") + cudaGetErrorString(e));
-    return RHD_OK;
+    cudaStream_t s = ctx->stream;
+    const double nc = (double)gs.ncell;
+    if (gs.desc.precision != RHD_SPLIT)
+        return timed_launch(ctx, K_FUSED_FP64, nc * alg_bytes_per_cell(gs, K_FUSED_FP64),
+                            [&] { return launch_subcycle_fp64(p, s); });
+    if (gs.variant != RHD_VARIANT_TWOPASS)
+        return timed_launch(ctx, K_FUSED_SPLIT, nc * alg_bytes_per_cell(gs, K_FUSED_SPLIT),
+                            [&] { return launch_subcycle_split(p, s); });
+    rhd_status st = timed_launch(ctx, K_PREDICTOR, nc * alg_bytes_per_cell(gs, K_PREDICTOR),
+                                 [&] { return launch_twopass_predictor(p, s); });
+    if (st) return st;
+    return timed_launch(ctx, K_CORRECTOR, nc * alg_bytes_per_cell(gs, K_CORRECTOR),
+                        [&] { return launch_twopass_corrector(p, s); });
 }
 
 // Run n_sub steps: replay a cached graph (or issue the launches directly).
@@ -563,6 +633,366 @@ rhd_status ensure_reduce(rhd_ctx* ctx, long long n)
     if (st) return st;
     ctx->red_blocks = nb;
     return RHD_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// ensemble launch helpers
+// ---------------------------------------------------------------------------------------------
+
+// Per-parity grid tables (src = 0 / 1) and the work-item count for the current z chunk.
+rhd_status ens_prepare(rhd_ctx* ctx, double chat, const double* dt_per_grid, double* dt_sig)
+{
+    const int ng = (int)ctx->grids.size();
+    std::vector<EnsembleGrid> eg(ng);
+    *dt_sig = 0.0;
+    for (int src = 0; src < 2; ++src) {
+        long long first = 0;
+        for (int i = 0; i < ng; ++i) {
+            GridState& gs = ctx->grids[i];
+            StepParams p = step_params(ctx, gs, src, chat, dt_per_grid[i]);
+            eg[i].g = p.g;
+            eg[i].a = p.a;
+            eg[i].dt = dt_per_grid[i];
+            eg[i].tiles_x = gs.tiles_x;
+            eg[i].tiles_y = gs.tiles_y;
+            eg[i].tiles_z = (gs.desc.n[2] + gs.z_chunk - 1) / gs.z_chunk;
+            eg[i].first_item = first;
+            first += (long long)eg[i].tiles_x * eg[i].tiles_y * eg[i].tiles_z;
+            if (src == 0) *dt_sig = *dt_sig * 1.000000119 + dt_per_grid[i];
+        }
+        ctx->n_items = first;
+        RHD_CUDA(ctx, cudaMemcpyAsync(ctx->d_egrids[src], eg.data(), sizeof(EnsembleGrid) * (size_t)ng,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return RHD_OK;
+}
+
+// One persistent ensemble launch reading buffer src.
+rhd_status ens_launch(rhd_ctx* ctx, double chat, int src)
+{
+    const bool split = ctx->grids[0].desc.precision == RHD_SPLIT;
+    RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+    EnsembleParams ep;
+    std::memset(&ep, 0, sizeof(ep));
+    ep.grids = ctx->d_egrids[src];
+    ep.n_grids = (int)ctx->grids.size();
+    ep.n_items = ctx->n_items;
+    ep.chat = chat;
+    ep.z_chunk = ctx->grids[0].z_chunk;
+    ep.counter = ctx->d_counter;
+    ep.stats = ctx->dstats;
+    double bytes = 0.0;
+    for (auto& gs : ctx->grids) bytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_FUSED_FP64);
+    return timed_launch(ctx, split ? K_ENS_SPLIT : K_ENS_FP64, bytes, [&] {
+        return split ? launch_ensemble_split(ep, ctx->ens_ctas, ctx->stream)
+                     : launch_ensemble_fp64(ep, ctx->ens_ctas, ctx->stream);
+    });
+}
+
+// ---------------------------------------------------------------------------------------------
+// launch configurations and the autotuner
+// ---------------------------------------------------------------------------------------------
+
+rhd_launch_config current_config(const GridState& gs)
+{
+    rhd_launch_config c;
+    c.variant = gs.variant;
+    c.tile_x = gs.variant == RHD_VARIANT_TWOPASS ? 32 : gs.tx;
+    c.tile_y = gs.variant == RHD_VARIANT_TWOPASS ? 8 : gs.ty;
+    c.z_chunk = gs.z_chunk;
+    c.staging = gs.staging;
+    c.ms_per_subcycle = gs.tuned_ms;
+    return c;
+}
+
+bool config_supported(const GridState& gs, const rhd_launch_config& c)
+{
+    const int nact = gs.gp.nact, prec = gs.desc.precision;
+    if (c.z_chunk < 1) return false;
+    if (c.variant == RHD_VARIANT_TWOPASS)
+        return prec == RHD_SPLIT && nact == 3 && c.tile_x == 32 && c.tile_y == 8 &&
+               (c.staging == RHD_STAGING_CPASYNC || (c.staging == RHD_STAGING_TMA && tma_available()));
+    if (c.variant != RHD_VARIANT_FUSED || c.staging != RHD_STAGING_CPASYNC) return false;
+    return tile_supported(prec, nact, c.tile_x, c.tile_y);
+}
+
+// Make c the configuration of gs (c must be supported); allocates or frees the U^{m+1/2} buffer.
+rhd_status apply_config(rhd_ctx* ctx, GridState& gs, const rhd_launch_config& c)
+{
+    if (c.variant == RHD_VARIANT_TWOPASS && !gs.uhalf) {
+        size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
+        rhd_status st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np);
+        if (st) return st;
+    }
+    if (c.variant != RHD_VARIANT_TWOPASS) dfree(gs.uhalf);
+    gs.variant = c.variant;
+    gs.staging = c.staging;
+    gs.tx = c.tile_x;
+    gs.ty = c.tile_y;
+    gs.tiles_x = (gs.desc.n[0] + gs.tx - 1) / gs.tx;
+    gs.tiles_y = (gs.desc.n[1] + gs.ty - 1) / gs.ty;
+    gs.z_chunk = std::max(1, std::min(c.z_chunk, gs.desc.n[2]));
+    clear_graphs(ctx);
+    return RHD_OK;
+}
+
+std::vector<rhd_launch_config> grid_candidates(const GridState& gs)
+{
+    std::vector<rhd_launch_config> v;
+    auto add = [&](int variant, int tx, int ty, int zc, int staging) {
+        rhd_launch_config c = {variant, tx, ty, std::max(1, std::min(zc, gs.desc.n[2])), staging, -1.0};
+        if (!config_supported(gs, c)) return;
+        for (auto& o : v)
+            if (o.variant == c.variant && o.tile_x == c.tile_x && o.tile_y == c.tile_y && o.z_chunk == c.z_chunk &&
+                o.staging == c.staging)
+                return;
+        v.push_back(c);
+    };
+    if (gs.gp.nact < 3) {
+        rhd_launch_config c = current_config(gs);
+        add(c.variant, c.tile_x, c.tile_y, c.z_chunk, c.staging);
+    } else if (gs.desc.precision == RHD_FP64) {
+        for (int zc : {8, 16, 32, 64, 128}) add(RHD_VARIANT_FUSED, 16, 8, zc, RHD_STAGING_CPASYNC);
+    } else {
+        for (int stg : {RHD_STAGING_CPASYNC, RHD_STAGING_TMA})
+            for (int zc : {16, 32, 64}) add(RHD_VARIANT_TWOPASS, 32, 8, zc, stg);
+        const int tiles[3][2] = {{32, 8}, {32, 16}, {64, 8}};
+        for (auto& t : tiles)
+            for (int zc : {32, 64, 128}) add(RHD_VARIANT_FUSED, t[0], t[1], zc, RHD_STAGING_CPASYNC);
+    }
+    return v;
+}
+
+// Copies of what a timed candidate run overwrites: the temperature (updated in place by the FULL
+// exchange) of every grid, and the statistics.
+struct TuneBackup {
+    std::vector<double*> T;
+    DevStats* stats = nullptr;
+};
+
+rhd_status tune_backup(rhd_ctx* ctx, TuneBackup& b)
+{
+    b.T.assign(ctx->grids.size(), nullptr);
+    for (size_t i = 0; i < ctx->grids.size(); ++i) {
+        GridState& gs = ctx->grids[i];
+        if (gs.desc.exchange != RHD_EX_FULL) continue;
+        rhd_status st = dalloc(ctx, (void**)&b.T[i], sizeof(double) * (size_t)gs.ncell);
+        if (st) return st;
+        RHD_CUDA(ctx, cudaMemcpyAsync(b.T[i], gs.T, sizeof(double) * (size_t)gs.ncell, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    }
+    rhd_status st = dalloc(ctx, (void**)&b.stats, sizeof(DevStats));
+    if (st) return st;
+    RHD_CUDA(ctx, cudaMemcpyAsync(b.stats, ctx->dstats, sizeof(DevStats), cudaMemcpyDeviceToDevice, ctx->stream));
+    return RHD_OK;
+}
+
+rhd_status tune_restore(rhd_ctx* ctx, TuneBackup& b)
+{
+    for (size_t i = 0; i < ctx->grids.size(); ++i)
+        if (b.T[i])
+            RHD_CUDA(ctx, cudaMemcpyAsync(ctx->grids[i].T, b.T[i], sizeof(double) * (size_t)ctx->grids[i].ncell,
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+    if (b.stats)
+        RHD_CUDA(ctx, cudaMemcpyAsync(ctx->dstats, b.stats, sizeof(DevStats), cudaMemcpyDeviceToDevice, ctx->stream));
+    return RHD_OK;
+}
+
+void tune_free(TuneBackup& b)
+{
+    for (auto& p : b.T) dfree(p);
+    dfree(b.stats);
+}
+
+// Mean milliseconds per launch of reps launches of fn (after one warm-up), on the context's stream;
+// every launch reads the current buffer, so the state does not advance.
+template <typename Fn>
+rhd_status time_launches(rhd_ctx* ctx, int reps, Fn&& fn, double* ms)
+{
+    *ms = -1.0;
+    rhd_status st = fn();
+    if (st) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RHD_CUDA(ctx, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, RHD_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+    }
+    ce = cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < reps && ce == cudaSuccess && st == RHD_OK; ++r) st = fn();
+    if (ce == cudaSuccess && st == RHD_OK) ce = cudaEventRecord(e1, ctx->stream);
+    if (ce == cudaSuccess && st == RHD_OK) ce = cudaEventSynchronize(e1);
+    float f = 0.0f;
+    if (ce == cudaSuccess && st == RHD_OK) ce = cudaEventElapsedTime(&f, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (ce != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("tuning timer: ") + cudaGetErrorString(ce));
+    *ms = (double)f / reps;
+    return RHD_OK;
+}
+
+void report(const std::vector<rhd_launch_config>& all, const rhd_launch_config& best, rhd_launch_config* table,
+            int capacity, int* n_entries, rhd_launch_config* chosen)
+{
+    if (table)
+        for (int i = 0; i < (int)all.size() && i < capacity; ++i) table[i] = all[i];
+    if (n_entries) *n_entries = (int)all.size();
+    if (chosen) *chosen = best;
+}
+
+// Choices already made in this process, by grid shape and mode.
+std::mutex g_tune_mutex;
+std::map<std::string, rhd_launch_config> g_tune_cache;
+
+std::string tune_key(rhd_ctx* ctx)
+{
+    std::string k = std::to_string(ctx->device) + (ctx->ensemble ? "E" : "G");
+    for (auto& gs : ctx->grids) {
+        const rhd_grid_desc& d = gs.desc;
+        k += ":" + std::to_string(d.n[0]) + "x" + std::to_string(d.n[1]) + "x" + std::to_string(d.n[2]) + "/" +
+             std::to_string(d.precision) + std::to_string(d.exchange) + std::to_string(d.beta_tau) +
+             std::to_string(d.limiter) + std::to_string(d.closure) + std::to_string(d.speeds) +
+             std::to_string(gs.has_v) + std::to_string(gs.has_kP) + std::to_string(gs.has_kF) +
+             std::to_string(gs.has_j);
+    }
+    return k;
+}
+
+rhd_status grid_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_launch_config* table, int capacity,
+                         int* n_entries, rhd_launch_config* chosen)
+{
+    GridState& gs = ctx->grids[0];
+    std::vector<rhd_launch_config> cand = grid_candidates(gs);
+    const rhd_launch_config before = current_config(gs);
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    TuneBackup b;
+    if ((st = tune_backup(ctx, b))) {
+        tune_free(b);
+        return st;
+    }
+    int best = -1;
+    for (size_t i = 0; i < cand.size() && !st; ++i) {
+        if ((st = apply_config(ctx, gs, cand[i]))) {
+            if (st != RHD_ERR_OOM) break;
+            st = RHD_OK;  // e.g. no room for the U^{m+1/2} buffer: the candidate is skipped
+            continue;
+        }
+        double ms = -1.0;
+        st = time_launches(ctx, reps, [&] { return launch_one(ctx, gs, ctx->cur, chat, dt); }, &ms);
+        if (!st) st = tune_restore(ctx, b);
+        cand[i].ms_per_subcycle = ms;
+        if (!st && ms >= 0.0 && (best < 0 || ms < cand[best].ms_per_subcycle)) best = (int)i;
+    }
+    rhd_status st2 = RHD_OK;
+    if (!st) st2 = apply_config(ctx, gs, best >= 0 ? cand[best] : before);
+    if (!st && !st2) st2 = tune_restore(ctx, b);
+    cudaError_t ce = cudaStreamSynchronize(ctx->stream);
+    tune_free(b);
+    if (st) return st;
+    if (st2) return st2;
+    if (ce != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    gs.tuned = true;
+    gs.tuned_ms = best >= 0 ? cand[best].ms_per_subcycle : -1.0;
+    report(cand, current_config(gs), table, capacity, n_entries, chosen);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[tune_key(ctx)] = current_config(gs);
+    }
+    return leave(ctx);
+}
+
+rhd_status grid_tune_once(rhd_ctx* ctx, double chat, double dt)
+{
+    GridState& gs = ctx->grids[0];
+    rhd_launch_config c;
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(tune_key(ctx));
+        if (it != g_tune_cache.end()) {
+            c = it->second;
+            hit = true;
+        }
+    }
+    if (hit && config_supported(gs, c)) {
+        rhd_status st = apply_config(ctx, gs, c);
+        if (st) return st;
+        gs.tuned = true;
+        gs.tuned_ms = c.ms_per_subcycle;
+        return RHD_OK;
+    }
+    return grid_autotune(ctx, chat, dt, 3, nullptr, 0, nullptr, nullptr);
+}
+
+rhd_status ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_grid, int reps,
+                             rhd_launch_config* table, int capacity, int* n_entries, rhd_launch_config* chosen)
+{
+    GridState& g0 = ctx->grids[0];
+    int max_nz = 1;
+    for (auto& gs : ctx->grids) max_nz = std::max(max_nz, gs.desc.n[2]);
+    std::vector<rhd_launch_config> cand;
+    for (int zc : {8, 16, 32, 64, 128}) {
+        if (zc > max_nz && !cand.empty()) break;
+        cand.push_back({RHD_VARIANT_FUSED, g0.tx, g0.ty, zc, RHD_STAGING_CPASYNC, -1.0});
+    }
+    const int zc_before = g0.z_chunk;
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    TuneBackup b;
+    if ((st = tune_backup(ctx, b))) {
+        tune_free(b);
+        return st;
+    }
+    auto set_zc = [&](int zc) {
+        for (auto& gs : ctx->grids) gs.z_chunk = zc;  // one chunk length for all grids, as at creation
+    };
+    int best = -1;
+    for (size_t i = 0; i < cand.size() && !st; ++i) {
+        set_zc(cand[i].z_chunk);
+        double dt_sig = 0.0, ms = -1.0;
+        st = ens_prepare(ctx, chat, dt_per_grid, &dt_sig);
+        if (!st) st = time_launches(ctx, reps, [&] { return ens_launch(ctx, chat, ctx->cur); }, &ms);
+        if (!st) st = tune_restore(ctx, b);
+        cand[i].ms_per_subcycle = ms;
+        if (!st && ms >= 0.0 && (best < 0 || ms < cand[best].ms_per_subcycle)) best = (int)i;
+    }
+    set_zc(best >= 0 ? cand[best].z_chunk : zc_before);
+    clear_graphs(ctx);
+    rhd_status st2 = st ? RHD_OK : tune_restore(ctx, b);
+    cudaError_t ce = cudaStreamSynchronize(ctx->stream);
+    tune_free(b);
+    if (st) return st;
+    if (st2) return st2;
+    if (ce != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    g0.tuned = true;
+    g0.tuned_ms = best >= 0 ? cand[best].ms_per_subcycle : -1.0;
+    rhd_launch_config cur = current_config(g0);
+    report(cand, cur, table, capacity, n_entries, chosen);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[tune_key(ctx)] = cur;
+    }
+    return leave(ctx);
+}
+
+rhd_status ensemble_tune_once(rhd_ctx* ctx, double chat, const double* dt_per_grid)
+{
+    GridState& g0 = ctx->grids[0];
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(tune_key(ctx));
+        if (it != g_tune_cache.end()) {
+            for (auto& gs : ctx->grids) gs.z_chunk = it->second.z_chunk;
+            g0.tuned = true;
+            g0.tuned_ms = it->second.ms_per_subcycle;
+            clear_graphs(ctx);
+            return RHD_OK;
+        }
+    }
+    return ensemble_autotune(ctx, chat, dt_per_grid, 3, nullptr, 0, nullptr, nullptr);
 }
 
 }  // namespace
@@ -658,8 +1088,9 @@ rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double d
     if (st) return st;
     if (!gs.has_moments || !gs.has_gas) return fail(ctx, RHD_ERR_STATE, "set the moments and the gas state first");
     if (n_sub == 0) return RHD_OK;
+    if ((gs.desc.flags & RHD_FLAG_AUTOTUNE) && !gs.tuned && (st = grid_tune_once(ctx, chat, dt))) return st;
     if ((st = enter(ctx))) return st;
-    bool use_graph = !(gs.desc.flags & RHD_FLAG_NO_GRAPH);
+    bool use_graph = !(gs.desc.flags & RHD_FLAG_NO_GRAPH) && !ctx->ktiming;
     st = run_steps(ctx, n_sub, chat, dt, use_graph, [&](int src) { return launch_one(ctx, gs, src, chat, dt); });
     if (st) return st;
     ctx->cur = (ctx->cur + n_sub) & 1;
@@ -863,51 +1294,113 @@ rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const dou
             return fail(ctx, RHD_ERR_STATE, "set the moments and gas state of every grid first");
     }
     if (n_sub == 0) return RHD_OK;
-    rhd_status st = enter(ctx);
-    if (st) return st;
-    // per-parity grid tables (src = 0 / 1)
-    std::vector<EnsembleGrid> eg(ng);
+    rhd_status st = RHD_OK;
+    if ((ctx->grids[0].desc.flags & RHD_FLAG_AUTOTUNE) && !ctx->grids[0].tuned &&
+        (st = ensemble_tune_once(ctx, chat, dt_per_grid)))
+        return st;
+    if ((st = enter(ctx))) return st;
     double dt_sig = 0.0;
-    for (int src = 0; src < 2; ++src) {
-        long long first = 0;
-        for (int i = 0; i < ng; ++i) {
-            GridState& gs = ctx->grids[i];
-            StepParams p = step_params(ctx, gs, src, chat, dt_per_grid[i]);
-            eg[i].g = p.g;
-            eg[i].a = p.a;
-            eg[i].dt = dt_per_grid[i];
-            eg[i].tiles_x = gs.tiles_x;
-            eg[i].tiles_y = gs.tiles_y;
-            eg[i].tiles_z = (gs.desc.n[2] + gs.z_chunk - 1) / gs.z_chunk;
-            eg[i].first_item = first;
-            first += (long long)eg[i].tiles_x * eg[i].tiles_y * eg[i].tiles_z;
-            if (src == 0) dt_sig = dt_sig * 1.000000119 + dt_per_grid[i];
-        }
-        RHD_CUDA(ctx, cudaMemcpyAsync(ctx->d_egrids[src], eg.data(), sizeof(EnsembleGrid) * (size_t)ng,
-                                      cudaMemcpyHostToDevice, ctx->stream));
-    }
-    const bool split = ctx->grids[0].desc.precision == RHD_SPLIT;
-    auto launch = [&](int src) -> rhd_status {
-        RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
-        EnsembleParams ep;
-        std::memset(&ep, 0, sizeof(ep));
-        ep.grids = ctx->d_egrids[src];
-        ep.n_grids = ng;
-        ep.n_items = ctx->n_items;
-        ep.chat = chat;
-        ep.z_chunk = ctx->grids[0].z_chunk;
-        ep.counter = ctx->d_counter;
-        ep.stats = ctx->dstats;
-        cudaError_t e = split ? launch_ensemble_split(ep, ctx->ens_ctas, ctx->stream)
-                              : launch_ensemble_fp64(ep, ctx->ens_ctas, ctx->stream);
-        if (e != cudaSuccess) return fail(ctx, RHD_ERR_CUDA, std::string("ensemble launch: ") + cudaGetErrorString(e));
-        return RHD_OK;
-    };
-    bool use_graph = !(ctx->grids[0].desc.flags & RHD_FLAG_NO_GRAPH);
-    st = run_steps(ctx, n_sub, chat, dt_sig, use_graph, launch);
+    if ((st = ens_prepare(ctx, chat, dt_per_grid, &dt_sig))) return st;
+    bool use_graph = !(ctx->grids[0].desc.flags & RHD_FLAG_NO_GRAPH) && !ctx->ktiming;
+    st = run_steps(ctx, n_sub, chat, dt_sig, use_graph, [&](int src) { return ens_launch(ctx, chat, src); });
     if (st) return st;
     ctx->cur = (ctx->cur + n_sub) & 1;
     ctx->n_subcycles += n_sub;
+    return leave(ctx);
+}
+
+// ---------------------------------------------------------------------------------------------
+// launch configuration and autotuner
+// ---------------------------------------------------------------------------------------------
+rhd_status rhd_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_launch_config* table, int capacity,
+                        int* n_entries, rhd_launch_config* chosen)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_autotune on an ensemble");
+    if (reps < 1 || capacity < 0) return fail(ctx, RHD_ERR_ARG, "reps >= 1 and capacity >= 0 are required");
+    GridState& gs = ctx->grids[0];
+    rhd_status st = check_dt(ctx, gs, chat, dt);
+    if (st) return st;
+    if (!gs.has_moments || !gs.has_gas) return fail(ctx, RHD_ERR_STATE, "set the moments and the gas state first");
+    return grid_autotune(ctx, chat, dt, reps, table, capacity, n_entries, chosen);
+}
+
+rhd_status rhd_ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_grid, int reps,
+                                 rhd_launch_config* table, int capacity, int* n_entries, rhd_launch_config* chosen)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (!ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not an ensemble context");
+    if (reps < 1 || capacity < 0 || !dt_per_grid)
+        return fail(ctx, RHD_ERR_ARG, "reps >= 1, capacity >= 0 and dt_per_grid are required");
+    for (size_t i = 0; i < ctx->grids.size(); ++i) {
+        rhd_status st = check_dt(ctx, ctx->grids[i], chat, dt_per_grid[i]);
+        if (st) return st;
+        if (!ctx->grids[i].has_moments || !ctx->grids[i].has_gas)
+            return fail(ctx, RHD_ERR_STATE, "set the moments and gas state of every grid first");
+    }
+    return ensemble_autotune(ctx, chat, dt_per_grid, reps, table, capacity, n_entries, chosen);
+}
+
+rhd_status rhd_set_kernel_timing(rhd_ctx* ctx, int enable)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->ktiming = enable != 0;
+    ctx->kev_used = 0;
+    ctx->krec.clear();
+    return RHD_OK;
+}
+
+rhd_status rhd_get_kernel_times(rhd_ctx* ctx, rhd_kernel_time* out, int capacity, int* n_entries)
+{
+    if (!ctx || capacity < 0 || (capacity > 0 && !out)) return fail(ctx, RHD_ERR_ARG, "ctx and out are required");
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    long long launches[K_COUNT] = {0};
+    double ms[K_COUNT] = {0.0}, bytes[K_COUNT] = {0.0};
+    for (auto& r : ctx->krec) {
+        float f = 0.0f;
+        RHD_CUDA(ctx, cudaEventElapsedTime(&f, ctx->kev[r.e0], ctx->kev[r.e1]));
+        launches[r.kernel] += 1;
+        ms[r.kernel] += f;
+        bytes[r.kernel] = r.alg_bytes;
+    }
+    ctx->kev_used = 0;
+    ctx->krec.clear();
+    int n = 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (!launches[k]) continue;
+        if (n < capacity) {
+            rhd_kernel_time& o = out[n];
+            std::memset(&o, 0, sizeof(o));
+            std::snprintf(o.name, sizeof(o.name), "%s", kKernelNames[k]);
+            o.launches = launches[k];
+            o.total_ms = ms[k];
+            o.alg_bytes_per_launch = bytes[k];
+        }
+        ++n;
+    }
+    if (n_entries) *n_entries = n;
+    return RHD_OK;
+}
+
+rhd_status rhd_get_launch_config(rhd_ctx* ctx, rhd_launch_config* out)
+{
+    if (!ctx || !out) return fail(ctx, RHD_ERR_ARG, "ctx and out are required");
+    *out = current_config(ctx->grids[0]);
+    return RHD_OK;
+}
+
+rhd_status rhd_set_launch_config(rhd_ctx* ctx, const rhd_launch_config* cfg)
+{
+    if (!ctx || !cfg) return fail(ctx, RHD_ERR_ARG, "ctx and cfg are required");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not available on an ensemble context");
+    GridState& gs = ctx->grids[0];
+    if (!config_supported(gs, *cfg)) return fail(ctx, RHD_ERR_ARG, "launch configuration not supported for this grid");
+    rhd_status st = enter(ctx);  // frees / allocates device memory: order after the caller's work
+    if (st) return st;
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((st = apply_config(ctx, gs, *cfg))) return st;
+    gs.tuned_ms = -1.0;
     return leave(ctx);
 }
 

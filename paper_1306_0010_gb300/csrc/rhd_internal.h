@@ -92,6 +92,9 @@ struct EnsembleParams {
 cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s);
 cudaError_t launch_subcycle_split(const StepParams& p, cudaStream_t s);
 cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s);
+cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s);
+cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s);
+bool tma_available();  // tensor-map staging of the two-pass corrector can be used on this device
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 int ensemble_ctas_per_sm_fp64();

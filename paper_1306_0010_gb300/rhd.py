@@ -28,6 +28,9 @@ SPEEDS = {"m1": 0, "fixed": 1}
 PRECISION = {"fp64": 0, "split": 1}
 FLAG_NO_GRAPH = 1
 FLAG_SPLIT_FUSED = 2
+FLAG_AUTOTUNE = 4
+VARIANT = {"fused": 0, "twopass": 1}
+STAGING = {"cpasync": 0, "tma": 1}
 
 
 class RhdError(RuntimeError):
@@ -86,6 +89,49 @@ class Stats(ctypes.Structure):
         return d
 
 
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("z_chunk", ctypes.c_int), ("staging", ctypes.c_int), ("ms_per_subcycle", ctypes.c_double)]
+
+    def as_dict(self):
+        inv_v = {v: k for k, v in VARIANT.items()}
+        inv_s = {v: k for k, v in STAGING.items()}
+        return {"variant": inv_v.get(self.variant, self.variant), "tile": (self.tile_x, self.tile_y),
+                "z_chunk": self.z_chunk, "staging": inv_s.get(self.staging, self.staging),
+                "ms_per_subcycle": self.ms_per_subcycle}
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(VARIANT[d["variant"]] if isinstance(d["variant"], str) else int(d["variant"]),
+                   int(d["tile"][0]), int(d["tile"][1]), int(d["z_chunk"]),
+                   STAGING[d["staging"]] if isinstance(d["staging"], str) else int(d["staging"]), -1.0)
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("alg_bytes_per_launch", ctypes.c_double)]
+
+
+_TUNE_CAP = 64
+
+
+def _kernel_times(ctx):
+    out = (KernelTime * 16)()
+    n = ctypes.c_int(0)
+    _check(ctx, lib().rhd_get_kernel_times(ctx, out, 16, ctypes.byref(n)))
+    return {out[i].name.decode(): {"launches": int(out[i].launches), "total_ms": float(out[i].total_ms),
+                                   "alg_bytes_per_launch": float(out[i].alg_bytes_per_launch)}
+            for i in range(min(n.value, 16))}
+
+
+def _tune_result(fn, *args):
+    table = (LaunchConfig * _TUNE_CAP)()
+    n = ctypes.c_int(0)
+    chosen = LaunchConfig()
+    st = fn(*args, table, _TUNE_CAP, ctypes.byref(n), ctypes.byref(chosen))
+    return st, chosen.as_dict(), [table[i].as_dict() for i in range(min(n.value, _TUNE_CAP))]
+
+
 # the entry points declared in include/rhd.h, with their ctypes signatures
 _P = ctypes.c_void_p
 _CTXP = ctypes.POINTER(ctypes.c_void_p)
@@ -111,6 +157,15 @@ _SIGS = {
     "rhd_ensemble_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "rhd_subcycle_noalloc": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                             ctypes.c_double, ctypes.c_double] + [_P] * 17 + [ctypes.POINTER(Stats)]),
+    "rhd_autotune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(LaunchConfig),
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(LaunchConfig)]),
+    "rhd_ensemble_autotune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                             ctypes.POINTER(LaunchConfig), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(LaunchConfig)]),
+    "rhd_get_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
+    "rhd_set_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
+    "rhd_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "rhd_get_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "rhd_abi_version": (ctypes.c_int, []),
     "rhd_built_arch": (ctypes.c_int, []),
 }
@@ -273,6 +328,30 @@ class Grid:
     def synchronize(self, timeout_ms=-1):
         _check(self._ctx, lib().rhd_synchronize(self._ctx, int(timeout_ms)))
 
+    def autotune(self, chat, dt, reps=3):
+        """Time every candidate launch configuration on the current state and keep the fastest;
+        returns (chosen, table) as dicts (see rhd_autotune)."""
+        st, chosen, table = _tune_result(lib().rhd_autotune, self._ctx, float(chat), float(dt), int(reps))
+        _check(self._ctx, st)
+        return chosen, table
+
+    def launch_config(self):
+        c = LaunchConfig()
+        _check(self._ctx, lib().rhd_get_launch_config(self._ctx, ctypes.byref(c)))
+        return c.as_dict()
+
+    def set_kernel_timing(self, enable=True):
+        """Bracket every kernel with CUDA events (plain launches while on); see kernel_times()."""
+        _check(self._ctx, lib().rhd_set_kernel_timing(self._ctx, int(bool(enable))))
+
+    def kernel_times(self):
+        """{kernel name: {launches, total_ms, alg_bytes_per_launch}} since the timer was enabled or last read."""
+        return _kernel_times(self._ctx)
+
+    def set_launch_config(self, cfg: dict):
+        c = LaunchConfig.from_dict(cfg)
+        _check(self._ctx, lib().rhd_set_launch_config(self._ctx, ctypes.byref(c)))
+
     def load_case(self, case):
         """Set the gas state and moments of a case dict (see workloads.py)."""
         f = case["fields"]
@@ -340,6 +419,23 @@ class Ensemble:
     def subcycle(self, n_sub, chat, dts):
         arr = (ctypes.c_double * len(dts))(*[float(v) for v in dts])
         _check(self._ctx, lib().rhd_ensemble_subcycle(self._ctx, int(n_sub), float(chat), arr))
+
+    def autotune(self, chat, dts, reps=3):
+        arr = (ctypes.c_double * len(dts))(*[float(v) for v in dts])
+        st, chosen, table = _tune_result(lib().rhd_ensemble_autotune, self._ctx, float(chat), arr, int(reps))
+        _check(self._ctx, st)
+        return chosen, table
+
+    def launch_config(self):
+        c = LaunchConfig()
+        _check(self._ctx, lib().rhd_get_launch_config(self._ctx, ctypes.byref(c)))
+        return c.as_dict()
+
+    def set_kernel_timing(self, enable=True):
+        _check(self._ctx, lib().rhd_set_kernel_timing(self._ctx, int(bool(enable))))
+
+    def kernel_times(self):
+        return _kernel_times(self._ctx)
 
     def get_stats(self, allow_nonfinite=False):
         s = Stats()

@@ -44,13 +44,17 @@ def test_struct_layout_matches_header(tmp_path):
 
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rhd.h"\nint main(void){'
-                    'printf("%zu %zu %zu %zu\\n", sizeof(rhd_grid_desc), offsetof(rhd_grid_desc, cuda_stream),'
-                    ' sizeof(rhd_stats), offsetof(rhd_stats, max_f)); return 0;}\n')
+                    'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rhd_grid_desc), offsetof(rhd_grid_desc, cuda_stream),'
+                    ' sizeof(rhd_stats), offsetof(rhd_stats, max_f), sizeof(rhd_launch_config),'
+                    ' offsetof(rhd_launch_config, ms_per_subcycle)); printf("%zu %zu\\n", sizeof(rhd_kernel_time),'
+                    ' offsetof(rhd_kernel_time, alg_bytes_per_launch)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
-    a, b, c, d = (int(v) for v in subprocess.check_output([str(exe)]).split())
+    a, b, c, d, e, f, g, h = (int(v) for v in subprocess.check_output([str(exe)]).split())
+    assert g == ctypes.sizeof(rhd.KernelTime) and h == rhd.KernelTime.alg_bytes_per_launch.offset
     assert a == ctypes.sizeof(rhd.GridDesc) and b == rhd.GridDesc.cuda_stream.offset
     assert c == ctypes.sizeof(rhd.Stats) and d == rhd.Stats.max_f.offset
+    assert e == ctypes.sizeof(rhd.LaunchConfig) and f == rhd.LaunchConfig.ms_per_subcycle.offset
 
 
 def test_identification_and_argument_errors(lib):
@@ -83,3 +87,10 @@ def test_identification_and_argument_errors(lib):
     assert lib.rhd_radiation_subcycle(None, 1, 1.0, 0.1) == rhd.ERR_ARG
     assert lib.rhd_destroy(None) == rhd.OK
     assert lib.rhd_gas_step(None, 1.0) == rhd.ERR_UNSUPPORTED
+    cfg = rhd.LaunchConfig()
+    assert lib.rhd_autotune(None, 1.0, 0.1, 1, None, 0, None, None) == rhd.ERR_ARG
+    assert lib.rhd_ensemble_autotune(None, 1.0, None, 1, None, 0, None, None) == rhd.ERR_ARG
+    assert lib.rhd_get_launch_config(None, ctypes.byref(cfg)) == rhd.ERR_ARG
+    assert lib.rhd_set_launch_config(None, ctypes.byref(cfg)) == rhd.ERR_ARG
+    assert lib.rhd_set_kernel_timing(None, 1) == rhd.ERR_ARG
+    assert lib.rhd_get_kernel_times(None, None, 0, None) == rhd.ERR_ARG
