@@ -171,6 +171,22 @@ def workload_config(args, precision):
             "l2": "inputs larger than L2 (1.07 GB per FP64 field)"}
 
 
+def max_over_ranks(local_ms, dist=None, device=None):
+    """Slowest rank's time (every rank gets it); local_ms itself on one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(local_ms)
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells, n_sub, steps, world_size, max_ms):
+    """Cell-updates of all ranks (each advances its own grid of `cells` cells) over the slowest rank's time."""
+    return cells * n_sub * steps * world_size / (max_ms * 1e-3)
+
+
 def parse_launch(spec):
     v, t, z, stg = spec.split(":")
     tx, ty = (int(x) for x in t.split("x"))
@@ -299,12 +315,9 @@ def main():
                                                            args.warmup, stream, launch_spec=args.launch)
     clocks = clk.stop()
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, device="cuda")
         dist.barrier()
-    units = cells * args.n_sub * args.steps * ws
-    value = units / (total_ms * 1e-3)
+    value = whole_job_rate(cells, args.n_sub, args.steps, ws, total_ms)
     sub_ms = total_ms / (args.steps * args.n_sub)
     roofline = kernel_roofline(kt, hbm_peak, peak_kind)
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -323,7 +336,9 @@ def main():
         fp_ms, fp_steps, fst, fkt, flaunch, _ = time_path(torch, rhd, case, "fp64", args.fp64_n_sub,
                                                           max(2, args.steps // 2), args.warmup, stream, tune=False)
         fn = max(2, args.steps // 2)
-        fv = cells * args.fp64_n_sub * fn / (fp_ms * 1e-3) * ws
+        if ws > 1:
+            fp_ms = max_over_ranks(fp_ms, dist, device="cuda")
+        fv = whole_job_rate(cells, args.fp64_n_sub, fn, ws, fp_ms)
         f_launch = fp_ms / (fn * args.fp64_n_sub)
         extra["fp64_path"] = {"value": fv, "unit": UNIT, "n_sub_per_step": args.fp64_n_sub,
                               "launch_ms": f_launch, "split_speedup": value / fv, "launch": flaunch,
