@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "ensemble"],
+                    help="throughput: one 512^3 grid (the headline); ensemble: 64 independent grids of "
+                         "32^3..128^3, one persistent launch per subcycle, against per-grid plain launches")
+    ap.add_argument("--n-grids", type=int, default=64)
+    ap.add_argument("--ens-n-sub", type=int, default=50, help="subcycles per step of the ensemble workload")
     return ap.parse_args()
 
 
@@ -233,6 +238,23 @@ def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=Tr
     return total_ms, per_step_ms, st, kt, launch, tuning
 
 
+# FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def alu_roofline(rate):
+    """The split path against the FP32 arithmetic peak: the oracle's operation count per cell-update
+    (add + mul + div + sqrt of the plain FP64 algorithm, from its counting build) times the rate."""
+    path = os.path.join(ROOT, "profiles", "opcounts.json")
+    if not os.path.exists(path):
+        return None
+    ops = float(json.load(open(path))["arith_per_cell_update"])
+    achieved = ops * rate / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "ops_per_cell_update": ops,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz"}
+
+
 def kernel_roofline(kt, peak, peak_kind):
     """Roofline of the kernel with the largest share of the timed region: algorithmic bytes of one
     launch over its mean event-measured duration."""
@@ -281,10 +303,129 @@ def time_e2e(torch, rhd, case, precision, n_sub, steps, warmup, launch_spec="aut
     return el, h2d, d2h
 
 
+def ensemble_workload_config(args, cases):
+    sizes = sorted({c["desc"]["n"][0] for c in cases})
+    return {"workload": f"ensemble of {len(cases)} independent 3D grids, N drawn from {sizes}, outflow, "
+                        f"Gaussian source j with L ~ logU(1e-2, 1e2), uniform opacity tau ~ logU(0.1, 1e3), "
+                        f"FULL exchange, theta = 1, c = 10, chat = 1, dt = 0.4 dx / chat per grid",
+            "n_grids": len(cases), "cells": sum(int(np.prod(c["desc"]["n"])) for c in cases),
+            "n_sub_per_step": args.n_sub, "l2": "inputs larger than L2"}
+
+
+def time_ensemble(torch, rhd, cases, precision, n_sub, steps, warmup, stream):
+    """One persistent launch per subcycle over all grids (tile-to-grid work queue), n_sub subcycles per
+    call replayed from a CUDA graph; z chunk autotuned first (untimed)."""
+    descs = [dict(c["desc"], precision=precision) for c in cases]
+    ens = rhd.Ensemble(descs, stream=stream.cuda_stream)
+    for i, c in enumerate(cases):
+        ens.load_case(i, c)
+    dts = [c["dt"] for c in cases]
+    chosen, _ = ens.autotune(1.0, dts, reps=3)
+    for _ in range(warmup):
+        ens.subcycle(n_sub, 1.0, dts)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ens.subcycle(n_sub, 1.0, dts)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    # kernel timer over one more step (plain launches) for the roofline of the ensemble kernel
+    ens.set_kernel_timing(True)
+    ens.subcycle(n_sub, 1.0, dts)
+    kt = ens.kernel_times()
+    st = ens.get_stats(allow_nonfinite=True)
+    ens.close()
+    return ms, chosen, kt, st
+
+
+def time_per_grid(torch, rhd, cases, precision, n_sub, steps, warmup, stream):
+    """Baseline: each grid its own context, its n_sub subcycles as plain launches (no graph), one grid
+    after the other on one stream."""
+    grids = []
+    for c in cases:
+        g = rhd.Grid(dict(c["desc"], precision=precision, flags=rhd.FLAG_NO_GRAPH), stream=stream.cuda_stream)
+        g.load_case(c)
+        grids.append((g, c["dt"]))
+    for _ in range(warmup):
+        for g, dt in grids:
+            g.radiation_subcycle(n_sub, 1.0, dt)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for g, dt in grids:
+            g.radiation_subcycle(n_sub, 1.0, dt)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    for g, _ in grids:
+        g.close()
+    return ms
+
+
+def run_ensemble(args):
+    import torch
+
+    ws, rank, lrank = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(lrank)
+    from paper_1306_0010_gb300 import build, rhd, workloads as wl
+
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    rhd.lib()
+    n_sub = args.ens_n_sub
+    cases = wl.config5(n_grids=args.n_grids, n_sub=n_sub, precision="split")
+    cells = sum(int(np.prod(c["desc"]["n"])) for c in cases)
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+    res = {}
+    clk = ClockSampler(lrank)
+    clk.start()
+    # the FP64 path is ~30x slower: fewer subcycles and steps keep the run within minutes
+    plan = {"split": (n_sub, args.steps, args.warmup), "fp64": (max(1, n_sub // 5), 2, 1)}
+    for prec in ("split", "fp64"):
+        ns, steps, warm = plan[prec]
+        ms, chosen, kt, st = time_ensemble(torch, rhd, cases, prec, ns, steps, warm, stream)
+        base_ms = time_per_grid(torch, rhd, cases, prec, ns, steps, 1, stream)
+        if ws > 1:
+            ms = max_over_ranks(ms, dist, device="cuda")
+            base_ms = max_over_ranks(base_ms, dist, device="cuda")
+        res[prec] = {"value": whole_job_rate(cells, ns, steps, ws, ms), "ms_per_step": ms / steps,
+                     "n_sub_per_step": ns, "steps": steps,
+                     "per_grid_plain_launches": whole_job_rate(cells, ns, steps, ws, base_ms),
+                     "launch": chosen, "roofline": kernel_roofline(kt, hbm_peak, peak_kind),
+                     "stats": {k: st[k] for k in ("n_realizability_fix", "n_theta_fallback", "n_nonfinite",
+                                                  "newton_iter_max")}}
+        res[prec]["speedup_vs_per_grid"] = res[prec]["value"] / res[prec]["per_grid_plain_launches"]
+    clocks = clk.stop()
+    if rank == 0:
+        sp = res["split"]
+        line = {"metric": METRIC, "value": sp["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sp["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+                "config": dict(ensemble_workload_config(args, cases), precision="split"),
+                "roofline": sp["roofline"], "clocks": clocks,
+                "gpu_launches": args.steps * n_sub, "split": sp, "fp64": res["fp64"]}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
     import torch
 
     ws, rank, lrank = dist_env()
@@ -359,7 +500,8 @@ def main():
                 "config": dict(workload_config(args, "split"), launch=launch),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clocks,
-                "subcycle_roofline": subcycle_roofline, "kernels": kt, "autotune": tuning,
+                "subcycle_roofline": subcycle_roofline, "alu_roofline": alu_roofline(value / ws),
+                "kernels": kt, "autotune": tuning,
                 "stats": {k: st[k] for k in ("n_realizability_fix", "n_face_fallback", "n_theta_fallback",
                                              "n_nonfinite", "newton_iter_max")},
                 "per_step_ms": per_step}

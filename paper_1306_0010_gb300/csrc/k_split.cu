@@ -96,6 +96,38 @@ cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s)
 
 bool tma_available() { return false; }
 
+template <typename K>
+static int occupancy_of(K k, size_t smem, int threads)
+{
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess || n < 1) return 1;
+    return n;
+}
+
+cudaError_t launch_ensemble_predictor(const EnsembleParams& p, int n_ctas, cudaStream_t s)
+{
+    auto k = predictor_ens_kernel<32, 8>;
+    const size_t smem = GeoPred<32, 8>::bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_ctas, 256, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_corrector(const EnsembleParams& p, int n_ctas, cudaStream_t s)
+{
+    auto k = corrector_ens_kernel<32, 8>;
+    const size_t smem = GeoCorr<32, 8>::bytes();
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_ctas, 256, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+int ensemble_ctas_per_sm_predictor() { return occupancy_of(predictor_ens_kernel<32, 8>, GeoPred<32, 8>::bytes(), 256); }
+int ensemble_ctas_per_sm_corrector() { return occupancy_of(corrector_ens_kernel<32, 8>, GeoCorr<32, 8>::bytes(), 256); }
+
 int ensemble_ctas_per_sm_split() { return ens_occupancy<float, 32, 8, true>(); }
 
 }  // namespace rhd

@@ -87,8 +87,8 @@ struct rhd_ctx {
     // ensemble
     EnsembleGrid* d_egrids[2] = {nullptr, nullptr};
     unsigned long long* d_counter = nullptr;
-    long long n_items = 0;
-    int ens_ctas = 0;
+    long long n_items = 0, n_pitems = 0;
+    int ens_ctas = 0, ens_pctas = 0, ens_cctas = 0;  // fused / predictor / corrector persistent CTAs
 };
 
 namespace {
@@ -512,9 +512,13 @@ rhd_status check_dt(rhd_ctx* ctx, const GridState& gs, double chat, double dt)
 }
 
 // kernels reported by the kernel timer
-enum KernelId { K_FUSED_FP64 = 0, K_FUSED_SPLIT, K_PREDICTOR, K_CORRECTOR, K_ENS_FP64, K_ENS_SPLIT, K_COUNT };
+enum KernelId {
+    K_FUSED_FP64 = 0, K_FUSED_SPLIT, K_PREDICTOR, K_CORRECTOR, K_ENS_FP64, K_ENS_SPLIT, K_ENS_PRED, K_ENS_CORR,
+    K_COUNT
+};
 const char* const kKernelNames[K_COUNT] = {"subcycle_fused_fp64", "subcycle_fused_split", "twopass_predictor_split",
-                                           "twopass_corrector_split", "ensemble_fp64", "ensemble_split"};
+                                           "twopass_corrector_split", "ensemble_fp64", "ensemble_split",
+                                           "ensemble_predictor_split", "ensemble_corrector_split"};
 
 // Algorithmic bytes per interior cell of one launch of kernel k: every input read once, every output
 // written once (U = 4 FP64 moments, U^{m+1/2} = 4 FP32, gas arrays in the kernel's precision).
@@ -646,47 +650,77 @@ rhd_status ens_prepare(rhd_ctx* ctx, double chat, const double* dt_per_grid, dou
     std::vector<EnsembleGrid> eg(ng);
     *dt_sig = 0.0;
     for (int src = 0; src < 2; ++src) {
-        long long first = 0;
+        long long first = 0, pfirst = 0;
         for (int i = 0; i < ng; ++i) {
             GridState& gs = ctx->grids[i];
+            const bool twopass = gs.variant == RHD_VARIANT_TWOPASS;
             StepParams p = step_params(ctx, gs, src, chat, dt_per_grid[i]);
+            std::memset(&eg[i], 0, sizeof(EnsembleGrid));
             eg[i].g = p.g;
             eg[i].a = p.a;
             eg[i].dt = dt_per_grid[i];
-            eg[i].tiles_x = gs.tiles_x;
-            eg[i].tiles_y = gs.tiles_y;
+            // corrector (two-pass) or fused items: tiles of the interior; the two-pass kernels use 32 x 8
+            eg[i].tiles_x = twopass ? (gs.desc.n[0] + 31) / 32 : gs.tiles_x;
+            eg[i].tiles_y = twopass ? (gs.desc.n[1] + 7) / 8 : gs.tiles_y;
             eg[i].tiles_z = (gs.desc.n[2] + gs.z_chunk - 1) / gs.z_chunk;
             eg[i].first_item = first;
             first += (long long)eg[i].tiles_x * eg[i].tiles_y * eg[i].tiles_z;
+            if (twopass) {  // predictor items: 32 x 8 tiles of the grid padded by two ghost layers
+                eg[i].uhalf = gs.uhalf;
+                eg[i].ptiles_x = (gs.desc.n[0] + 4 + 31) / 32;
+                eg[i].ptiles_y = (gs.desc.n[1] + 4 + 7) / 8;
+                eg[i].ptiles_z = (gs.desc.n[2] + 4 + gs.z_chunk - 1) / gs.z_chunk;
+                eg[i].first_pitem = pfirst;
+                pfirst += (long long)eg[i].ptiles_x * eg[i].ptiles_y * eg[i].ptiles_z;
+            }
             if (src == 0) *dt_sig = *dt_sig * 1.000000119 + dt_per_grid[i];
         }
         ctx->n_items = first;
+        ctx->n_pitems = pfirst;
         RHD_CUDA(ctx, cudaMemcpyAsync(ctx->d_egrids[src], eg.data(), sizeof(EnsembleGrid) * (size_t)ng,
                                       cudaMemcpyHostToDevice, ctx->stream));
     }
     return RHD_OK;
 }
 
-// One persistent ensemble launch reading buffer src.
+// One subcycle of every grid reading buffer src: one persistent launch (fused), or a persistent
+// predictor launch followed by a persistent corrector launch (two-pass).
 rhd_status ens_launch(rhd_ctx* ctx, double chat, int src)
 {
     const bool split = ctx->grids[0].desc.precision == RHD_SPLIT;
-    RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+    const bool twopass = ctx->grids[0].variant == RHD_VARIANT_TWOPASS;
     EnsembleParams ep;
     std::memset(&ep, 0, sizeof(ep));
     ep.grids = ctx->d_egrids[src];
     ep.n_grids = (int)ctx->grids.size();
     ep.n_items = ctx->n_items;
+    ep.n_pitems = ctx->n_pitems;
     ep.chat = chat;
     ep.z_chunk = ctx->grids[0].z_chunk;
-    ep.counter = ctx->d_counter;
     ep.stats = ctx->dstats;
-    double bytes = 0.0;
-    for (auto& gs : ctx->grids) bytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_FUSED_FP64);
-    return timed_launch(ctx, split ? K_ENS_SPLIT : K_ENS_FP64, bytes, [&] {
-        return split ? launch_ensemble_split(ep, ctx->ens_ctas, ctx->stream)
-                     : launch_ensemble_fp64(ep, ctx->ens_ctas, ctx->stream);
-    });
+    if (!twopass) {
+        double bytes = 0.0;
+        for (auto& gs : ctx->grids) bytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_FUSED_FP64);
+        ep.counter = ctx->d_counter;
+        RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
+        return timed_launch(ctx, split ? K_ENS_SPLIT : K_ENS_FP64, bytes, [&] {
+            return split ? launch_ensemble_split(ep, ctx->ens_ctas, ctx->stream)
+                         : launch_ensemble_fp64(ep, ctx->ens_ctas, ctx->stream);
+        });
+    }
+    double pbytes = 0.0, cbytes = 0.0;
+    for (auto& gs : ctx->grids) {
+        pbytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_PREDICTOR);
+        cbytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_CORRECTOR);
+    }
+    RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    ep.counter = ctx->d_counter;
+    rhd_status st = timed_launch(ctx, K_ENS_PRED, pbytes,
+                                 [&] { return launch_ensemble_predictor(ep, ctx->ens_pctas, ctx->stream); });
+    if (st) return st;
+    ep.counter = ctx->d_counter + 1;
+    return timed_launch(ctx, K_ENS_CORR, cbytes,
+                        [&] { return launch_ensemble_corrector(ep, ctx->ens_cctas, ctx->stream); });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -927,18 +961,42 @@ rhd_status grid_tune_once(rhd_ctx* ctx, double chat, double dt)
     return grid_autotune(ctx, chat, dt, 3, nullptr, 0, nullptr, nullptr);
 }
 
+// Make every grid of an ensemble use variant v with z chunk zc (allocating or freeing U^{m+1/2}).
+rhd_status ens_apply(rhd_ctx* ctx, int v, int zc)
+{
+    for (auto& gs : ctx->grids) {
+        if (v == RHD_VARIANT_TWOPASS && !gs.uhalf) {
+            size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
+            rhd_status st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np);
+            if (st) return st;
+        }
+    }
+    for (auto& gs : ctx->grids) {
+        if (v != RHD_VARIANT_TWOPASS) dfree(gs.uhalf);
+        gs.variant = v;
+        gs.z_chunk = zc;  // one chunk length for all grids, as at creation
+    }
+    clear_graphs(ctx);
+    return RHD_OK;
+}
+
 rhd_status ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_grid, int reps,
                              rhd_launch_config* table, int capacity, int* n_entries, rhd_launch_config* chosen)
 {
     GridState& g0 = ctx->grids[0];
+    const bool split = g0.desc.precision == RHD_SPLIT;
     int max_nz = 1;
     for (auto& gs : ctx->grids) max_nz = std::max(max_nz, gs.desc.n[2]);
     std::vector<rhd_launch_config> cand;
-    for (int zc : {8, 16, 32, 64, 128}) {
-        if (zc > max_nz && !cand.empty()) break;
-        cand.push_back({RHD_VARIANT_FUSED, g0.tx, g0.ty, zc, RHD_STAGING_CPASYNC, -1.0});
-    }
-    const int zc_before = g0.z_chunk;
+    auto add = [&](int v, int zc) {
+        if (zc > max_nz && zc != 8) return;
+        if (v == RHD_VARIANT_TWOPASS) cand.push_back({v, 32, 8, zc, RHD_STAGING_CPASYNC, -1.0});
+        else cand.push_back({v, g0.tx, g0.ty, zc, RHD_STAGING_CPASYNC, -1.0});
+    };
+    if (split)
+        for (int zc : {16, 32, 64}) add(RHD_VARIANT_TWOPASS, zc);
+    for (int zc : {8, 16, 32, 64, 128}) add(RHD_VARIANT_FUSED, zc);
+    const int v_before = g0.variant, zc_before = g0.z_chunk;
     rhd_status st = enter(ctx);
     if (st) return st;
     TuneBackup b;
@@ -946,12 +1004,13 @@ rhd_status ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_gri
         tune_free(b);
         return st;
     }
-    auto set_zc = [&](int zc) {
-        for (auto& gs : ctx->grids) gs.z_chunk = zc;  // one chunk length for all grids, as at creation
-    };
     int best = -1;
     for (size_t i = 0; i < cand.size() && !st; ++i) {
-        set_zc(cand[i].z_chunk);
+        if ((st = ens_apply(ctx, cand[i].variant, cand[i].z_chunk))) {
+            if (st != RHD_ERR_OOM) break;
+            st = RHD_OK;  // no room for the U^{m+1/2} buffers: skipped
+            continue;
+        }
         double dt_sig = 0.0, ms = -1.0;
         st = ens_prepare(ctx, chat, dt_per_grid, &dt_sig);
         if (!st) st = time_launches(ctx, reps, [&] { return ens_launch(ctx, chat, ctx->cur); }, &ms);
@@ -959,9 +1018,9 @@ rhd_status ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_gri
         cand[i].ms_per_subcycle = ms;
         if (!st && ms >= 0.0 && (best < 0 || ms < cand[best].ms_per_subcycle)) best = (int)i;
     }
-    set_zc(best >= 0 ? cand[best].z_chunk : zc_before);
-    clear_graphs(ctx);
-    rhd_status st2 = st ? RHD_OK : tune_restore(ctx, b);
+    rhd_status st2 = RHD_OK;
+    if (!st) st2 = best >= 0 ? ens_apply(ctx, cand[best].variant, cand[best].z_chunk) : ens_apply(ctx, v_before, zc_before);
+    if (!st && !st2) st2 = tune_restore(ctx, b);
     cudaError_t ce = cudaStreamSynchronize(ctx->stream);
     tune_free(b);
     if (st) return st;
@@ -985,10 +1044,10 @@ rhd_status ensemble_tune_once(rhd_ctx* ctx, double chat, const double* dt_per_gr
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tune_cache.find(tune_key(ctx));
         if (it != g_tune_cache.end()) {
-            for (auto& gs : ctx->grids) gs.z_chunk = it->second.z_chunk;
+            rhd_status st = ens_apply(ctx, it->second.variant, it->second.z_chunk);
+            if (st) return st;
             g0.tuned = true;
             g0.tuned_ms = it->second.ms_per_subcycle;
-            clear_graphs(ctx);
             return RHD_OK;
         }
     }
@@ -1211,6 +1270,10 @@ rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* 
             gs.desc = descs[i];
             gs.ncell = (long long)descs[i].n[0] * descs[i].n[1] * descs[i].n[2];
             fill_params(gs);
+            // split ensembles run the two-pass kernels unless descs[0] asks for the fused kernel
+            gs.variant = (descs[0].precision == RHD_SPLIT && !(descs[0].flags & RHD_FLAG_SPLIT_FUSED))
+                             ? RHD_VARIANT_TWOPASS
+                             : RHD_VARIANT_FUSED;
             st = alloc_grid(ctx, gs);
         }
         // one z chunk for all grids (the largest grid's automatic choice)
@@ -1221,10 +1284,14 @@ rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* 
         ctx->n_items = items;
         if (!st) st = dalloc(ctx, (void**)&ctx->d_egrids[0], sizeof(EnsembleGrid) * (size_t)n_grids);
         if (!st) st = dalloc(ctx, (void**)&ctx->d_egrids[1], sizeof(EnsembleGrid) * (size_t)n_grids);
-        if (!st) st = dalloc(ctx, (void**)&ctx->d_counter, sizeof(unsigned long long));
+        if (!st) st = dalloc(ctx, (void**)&ctx->d_counter, 2 * sizeof(unsigned long long));
         if (!st) {
             int per_sm = descs[0].precision == RHD_SPLIT ? ensemble_ctas_per_sm_split() : ensemble_ctas_per_sm_fp64();
             ctx->ens_ctas = per_sm * ctx->num_sms;
+            if (descs[0].precision == RHD_SPLIT) {
+                ctx->ens_pctas = ensemble_ctas_per_sm_predictor() * ctx->num_sms;
+                ctx->ens_cctas = ensemble_ctas_per_sm_corrector() * ctx->num_sms;
+            }
         }
     }
     if (st) {

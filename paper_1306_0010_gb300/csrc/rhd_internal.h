@@ -76,12 +76,18 @@ struct EnsembleGrid {
     double dt;
     int tiles_x, tiles_y, tiles_z;
     long long first_item;       // prefix sum of tiles over the grids before this one
+    // two-pass ensembles: U^{m+1/2} of this grid (padded by 2 ghost layers) and the predictor's
+    // tiles over the padded grid, with their prefix sum
+    float4* uhalf;
+    int ptiles_x, ptiles_y, ptiles_z;
+    long long first_pitem;
 };
 
 struct EnsembleParams {
     const EnsembleGrid* grids;  // device array
     int n_grids;
-    long long n_items;
+    long long n_items;          // corrector (or fused) work items
+    long long n_pitems;         // predictor work items (two-pass)
     double chat;
     int z_chunk;
     unsigned long long* counter;  // work-queue head, reset before each launch
@@ -99,6 +105,10 @@ cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 int ensemble_ctas_per_sm_fp64();
 int ensemble_ctas_per_sm_split();
+cudaError_t launch_ensemble_predictor(const EnsembleParams& p, int n_ctas, cudaStream_t s);
+cudaError_t launch_ensemble_corrector(const EnsembleParams& p, int n_ctas, cudaStream_t s);
+int ensemble_ctas_per_sm_predictor();
+int ensemble_ctas_per_sm_corrector();
 
 // Tile geometry: the default per precision and dimensionality, and the shapes compiled for 3D.
 void tile_shape(int precision, int nact, int* tx, int* ty);

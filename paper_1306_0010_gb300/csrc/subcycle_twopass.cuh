@@ -468,4 +468,84 @@ __global__ void __launch_bounds__(TX* TY, 3) corrector_kernel(const __grid_const
     max_counter(&P.stats->newton_iter_max, cnt.iter_max);
 }
 
+// ------------------------------------------------------------------------------------------------
+// persistent ensemble kernels: CTAs pull (grid, tile, z chunk) items from a global counter; the item
+// to grid map is a binary search over the grids' item prefix sums (predictor items cover each grid
+// padded by two ghost layers, corrector items its interior)
+// ------------------------------------------------------------------------------------------------
+
+// Claim the next item; returns false when the queue is empty.  On true, eg holds the item's grid
+// (copied to shared memory) and *local the item's index within that grid.
+template <bool PRED>
+__device__ __forceinline__ bool ens_next(const EnsembleParams& P, EnsembleGrid& eg, long long* item_s,
+                                         long long* local)
+{
+    if (threadIdx.x == 0) *item_s = (long long)atomicAdd(P.counter, 1ull);
+    __syncthreads();
+    const long long item = *item_s;
+    __syncthreads();
+    if (item >= (PRED ? P.n_pitems : P.n_items)) return false;
+    int lo = 0, hi = P.n_grids - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((PRED ? P.grids[mid].first_pitem : P.grids[mid].first_item) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    {
+        const int* src = reinterpret_cast<const int*>(P.grids + lo);
+        int* dst = reinterpret_cast<int*>(&eg);
+        for (int w = threadIdx.x; w < (int)(sizeof(EnsembleGrid) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    *local = item - (PRED ? eg.first_pitem : eg.first_item);
+    return true;
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, 4) predictor_ens_kernel(const __grid_constant__ EnsembleParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long item_s;
+    __shared__ __align__(16) EnsembleGrid eg;
+    Counters cnt = {0, 0, 0, 0, 0, 0};
+    long long local;
+#pragma unroll 1
+    while (ens_next<true>(P, eg, &item_s, &local)) {
+        const long long nxy = (long long)eg.ptiles_x * eg.ptiles_y;
+        const int txy = (int)(local % nxy), tz = (int)(local / nxy);
+        const int x0 = (txy % eg.ptiles_x) * TX - 2, y0 = (txy / eg.ptiles_x) * TY - 2;
+        const int z0 = tz * P.z_chunk - 2, z1 = min(z0 + P.z_chunk, eg.g.n[2] + 2);
+        predictor_tile<TX, TY>(eg.g, eg.a, eg.uhalf, P.chat, eg.dt, x0, y0, z0, z1,
+                               reinterpret_cast<float4*>(smem_raw), cnt);
+        __syncthreads();
+    }
+    add_counter(&P.stats->n_fix, cnt.fix);
+}
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, 3) corrector_ens_kernel(const __grid_constant__ EnsembleParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long item_s;
+    __shared__ __align__(16) EnsembleGrid eg;
+    Counters cnt = {0, 0, 0, 0, 0, 0};
+    long long local;
+#pragma unroll 1
+    while (ens_next<false>(P, eg, &item_s, &local)) {
+        const long long nxy = (long long)eg.tiles_x * eg.tiles_y;
+        const int txy = (int)(local % nxy), tz = (int)(local / nxy);
+        const int x0 = (txy % eg.tiles_x) * TX, y0 = (txy / eg.tiles_x) * TY;
+        const int z0 = tz * P.z_chunk, z1 = min(z0 + P.z_chunk, eg.g.n[2]);
+        corrector_tile<TX, TY>(eg.g, eg.a, eg.uhalf, P.chat, eg.dt, x0, y0, z0, z1,
+                               reinterpret_cast<float4*>(smem_raw), cnt);
+        __syncthreads();
+    }
+    add_counter(&P.stats->n_fix, cnt.fix);
+    add_counter(&P.stats->n_face, cnt.face);
+    add_counter(&P.stats->n_theta, cnt.theta);
+    add_counter(&P.stats->n_newton_fb, cnt.newton_fb);
+    add_counter(&P.stats->n_nonfinite, cnt.nonfinite);
+    max_counter(&P.stats->newton_iter_max, cnt.iter_max);
+}
+
 }  // namespace rhd

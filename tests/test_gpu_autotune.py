@@ -157,6 +157,32 @@ def test_ensemble_autotune(rhd):
     ens.close()
 
 
+def test_ensemble_split_autotune_variants(rhd):
+    cases = [wl.config5(n_grids=1, sizes=(n,), n_sub=2, precision="split", seed_offset=80 + i)[0]
+             for i, n in enumerate((32, 48))]
+    ens = rhd.Ensemble([c["desc"] for c in cases])
+    for i, c in enumerate(cases):
+        ens.load_case(i, c)
+    before = [(ens.get_moments(i), ens.get_gas_state(i)) for i in range(2)]
+    chosen, table = ens.autotune(1.0, [c["dt"] for c in cases], reps=2)
+    assert {c["variant"] for c in table} == {"fused", "twopass"}
+    best = min(table, key=lambda c: c["ms_per_subcycle"])
+    assert (chosen["variant"], chosen["z_chunk"]) == (best["variant"], best["z_chunk"])
+    assert ens.launch_config()["variant"] == best["variant"]
+    for i in range(2):
+        m, T = ens.get_moments(i), ens.get_gas_state(i)
+        assert np.array_equal(T, before[i][1])
+        for k in m:
+            assert np.array_equal(m[k], before[i][0][k]), (i, k)
+    ens.subcycle(2, 1.0, [c["dt"] for c in cases])
+    for i, c in enumerate(cases):
+        out = ens.get_moments(i)
+        out["T"] = ens.get_gas_state(i)
+        ref, _ = orc.subcycles(c, n_sub=2)
+        assert max(errors(out, ref, c["desc"]).values()) <= SPLIT_TOL, i
+    ens.close()
+
+
 def test_unsupported_launch_config_rejected(rhd):
     case = wl.parity_case("tune_bad", (16, 16, 16), n_sub=1, seed=34)  # FP64
     g = rhd.Grid(case["desc"])

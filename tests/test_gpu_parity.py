@@ -261,6 +261,31 @@ def test_ensemble_matches_per_grid_oracle(rhd):
     ens.close()
 
 
+@pytest.mark.parametrize("variant,flags", SPLIT_VARIANTS, ids=[v for v, _ in SPLIT_VARIANTS])
+def test_ensemble_split_matches_oracle(rhd, variant, flags):
+    """Split ensembles: persistent predictor + corrector launches (two-pass, default) or one persistent
+    fused launch per subcycle; uneven grid sizes and a z chunk that leaves ragged chunks."""
+    cases = []
+    for i, n in enumerate((16, 24, 40)):
+        c = wl.config5(n_grids=1, sizes=(n,), n_sub=3, precision="split", seed_offset=60 + i)[0]
+        c["desc"] = dict(c["desc"], flags=flags, z_chunk=7)
+        cases.append(c)
+    ens = rhd.Ensemble([c["desc"] for c in cases])
+    for i, c in enumerate(cases):
+        ens.load_case(i, c)
+    assert ens.launch_config()["variant"] == variant
+    ens.subcycle(3, 1.0, [c["dt"] for c in cases])
+    st = ens.get_stats()
+    assert st["n_nonfinite"] == 0
+    for i, c in enumerate(cases):
+        out = ens.get_moments(i)
+        out["T"] = ens.get_gas_state(i)
+        ref, _ = orc.subcycles(c, n_sub=3)
+        e = errors(out, ref, c["desc"])
+        assert max(e.values()) <= SPLIT_TOL, (i, e)
+    ens.close()
+
+
 # ----------------------------------------------------------------------------- interface behaviour
 
 def test_device_pointers_and_errors(rhd):
