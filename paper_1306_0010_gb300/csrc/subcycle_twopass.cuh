@@ -22,19 +22,54 @@ __device__ __forceinline__ long long pad_index(const GridParams& g, int x, int y
     return (long long)(x + 2) + px * ((long long)(y + 2) + py * (long long)(z + 2));
 }
 
+// Work layout shared by both kernels: every thread owns one cell (tlx, tly) of the tile; the loops
+// over cells, face-state records and faces are ordered so that the first passes are exactly one
+// item per thread (its own cell), and the few items beyond the tile (halo cells, the faces of the
+// tile's right column and top row) form one short last pass over the first threads.  No per-plane
+// index arithmetic is needed and the passes over the own cells do not diverge.
+
+// Gas of an interior cell at linear index li (split arrays; interior cells need no boundary rule).
+__device__ __forceinline__ GasCell<float> gas_at(const GridParams& g, const GridArrays& a, long long li)
+{
+    GasCell<float> c;
+    c.T = 0.0;
+    c.rho = 0.0;
+    const float r = __ldg(a.rho32 + li);
+    c.rho32 = r;
+    c.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, r);
+    c.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, r);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c.v[d] = a.v32[d] ? __ldg(a.v32[d] + li) : 0.0f;
+    c.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
+    return c;
+}
+
 template <int TX, int TY>
 struct GeoPred {
     static constexpr int NT = TX * TY;
     static constexpr int W1 = TX + 2, H1 = TY + 2;
     static constexpr int N1 = W1 * H1;
-    static constexpr int NR1 = (N1 + NT - 1) / NT;
+    static constexpr int NH = N1 - NT;  // halo cells of the tile + 1 region: rows -1 and TY, columns -1 and TX
+    static_assert(NH <= NT && TX + TY <= NT, "one extra item per thread at most");
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
     // float4 units
     static constexpr int UM = 0, CXo = UM + N1, CYo = CXo + N1, L3o = CYo + N1;
     static constexpr int FXo = L3o + (N1 + 1) / 2, FYo = FXo + NFX, END4 = FYo + NFY;
-    static constexpr int ST = 4 * N1;  // staged FP64 U^m, 4 per cell
+    static constexpr int ST = 4 * N1;  // staged FP64 U^m: own cells at 4 t, halo cells at 4 (NT + h)
     __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4 + 8 * (size_t)ST; }
     __device__ static __forceinline__ int i1(int lx, int ly) { return (lx + 1) + W1 * (ly + 1); }
+    // the h-th halo cell: rows ly = -1 and ly = TY with lx from -1 to TX, then columns lx = -1, TX
+    __device__ static __forceinline__ void halo(int h, int& lx, int& ly)
+    {
+        if (h < 2 * W1) {
+            ly = h < W1 ? -1 : TY;
+            lx = (h < W1 ? h : h - W1) - 1;
+        } else {
+            const int hh = h - 2 * W1;
+            ly = hh >> 1;
+            lx = (hh & 1) ? TX : -1;
+        }
+    }
 };
 
 // Predictor over the padded column tile (x0, y0) (coordinates in [-2, n+2)) for planes [z0, z1).
@@ -60,41 +95,61 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     const int gx = x0 + tlx, gy = y0 + tly;
     const bool own_in_pad = gx < g.n[0] + 2 && gy < g.n[1] + 2;
     const bool own_interior = gx >= 0 && gx < g.n[0] && gy >= 0 && gy < g.n[1];
-
-    int c_i1[G::NR1], c_off[G::NR1];
+    const bool has_h = t < G::NH;
+    int hlx = 0, hly = 0;
+    if (has_h) G::halo(t, hlx, hly);
+    const int i_own = G::i1(tlx, tly), i_h = G::i1(hlx, hly);
+    const int hx = x0 + hlx, hy = y0 + hly;
+    // every cell of the tile + 1 region inside the grid in x and y: all loads of in-range planes are plain copies
     const bool xy_inside = x0 - 1 >= 0 && x0 + TX + 1 <= g.n[0] && y0 - 1 >= 0 && y0 + TY + 1 <= g.n[1];
-#pragma unroll
-    for (int r = 0; r < G::NR1; ++r) {
-        const int c = t + r * G::NT;
-        const int lx = c % G::W1 - 1, ly = c / G::W1 - 1;
-        c_i1[r] = G::i1(lx, ly);
-        c_off[r] = (x0 + lx) + g.n[0] * (y0 + ly);
-    }
+    const int off_own = gx + g.n[0] * gy, off_h = hx + g.n[0] * hy;  // used only when xy_inside
+
+    auto stage = [&](double* d, int x, int y, int off, int q, bool fast, long long zoff) {
+        if (fast || inside(g, x, y, q)) {
+            const long long i = fast ? zoff + off : lin(g, x, y, q);
+            cp_async8(d + 0, a.E + i);
+            cp_async8(d + 1, a.G[0] + i);
+            cp_async8(d + 2, a.G[1] + i);
+            cp_async8(d + 3, a.G[2] + i);
+        } else {  // ghost cell: boundary rule (sign flips, Dirichlet values)
+            double U[4];
+            load_U(g, a, x, y, q, U);
+            d[0] = U[0];
+            d[1] = U[1];
+            d[2] = U[2];
+            d[3] = U[3];
+        }
+    };
     auto issue_plane = [&](int q) {
         const bool fast = xy_inside && (unsigned)q < (unsigned)g.n[2];
         const long long zoff = (long long)q * nxy;
-#pragma unroll
-        for (int r = 0; r < G::NR1; ++r) {
-            const int c = t + r * G::NT;
-            if (c < G::N1) {
-                double* d = stU + 4 * c;
-                const int x = x0 + c % G::W1 - 1, y = y0 + c / G::W1 - 1;
-                if (fast || inside(g, x, y, q)) {
-                    const long long i = fast ? zoff + c_off[r] : lin(g, x, y, q);
-                    cp_async8(d + 0, a.E + i);
-                    cp_async8(d + 1, a.G[0] + i);
-                    cp_async8(d + 2, a.G[1] + i);
-                    cp_async8(d + 3, a.G[2] + i);
-                } else {  // ghost cell: boundary rule (sign flips, Dirichlet values)
-                    double U[4];
-                    load_U(g, a, x, y, q, U);
-                    d[0] = U[0];
-                    d[1] = U[1];
-                    d[2] = U[2];
-                    d[3] = U[3];
-                }
-            }
-        }
+        stage(stU + 4 * t, gx, gy, off_own, q, fast, zoff);
+        if (has_h) stage(stU + 4 * (G::NT + t), hx, hy, off_h, q, fast, zoff);
+    };
+    auto to4 = [](const double* d) {
+        return make_float4(d2f_trunc(d[0]), d2f_trunc(d[1]), d2f_trunc(d[2]), d2f_trunc(d[3]));
+    };
+    auto closure_xy = [&](int i, const float4& U, const ClosureScalars<float>& k) {
+        float l1x, l3x, l1y, l3y;
+        wave_speeds(k, U.y, chat, fixed, l1x, l3x);
+        wave_speeds(k, U.z, chat, fixed, l1y, l3y);
+        const float bx = k.b * U.y;
+        const float Pxy = bx * U.z, Pxz = bx * U.w, Pyz = k.b * U.z * U.w;
+        CX[i] = make_float4(k.a + bx * U.y, Pxy, Pxz, l1x);
+        CY[i] = make_float4(Pxy, k.a + k.b * U.z * U.z, Pyz, l1y);
+        L3[i] = make_float2(l3x, l3y);
+    };
+    auto xface = [&](int iL, int iR) {
+        const float4 UL = Um[iL], UR = Um[iR], CL = CX[iL], CR = CX[iR];
+        const float4 FL = make_float4(chat * UL.y, chat * CL.x, chat * CL.y, chat * CL.z);
+        const float4 FR = make_float4(chat * UR.y, chat * CR.x, chat * CR.y, chat * CR.z);
+        return hll_pair(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x);
+    };
+    auto yface = [&](int iL, int iR) {
+        const float4 UL = Um[iL], UR = Um[iR], CL = CY[iL], CR = CY[iR];
+        const float4 FL = make_float4(chat * UL.z, chat * CL.x, chat * CL.y, chat * CL.z);
+        const float4 FR = make_float4(chat * UR.z, chat * CR.x, chat * CR.y, chat * CR.z);
+        return hll_pair(UL, UR, FL, FR, CL.w, L3[iL].y, CR.w, L3[iR].y);
     };
 
     float4 zU = make_float4(0.f, 0.f, 0.f, 0.f), zP = zU, dxy = zU, zfl = zU;
@@ -109,69 +164,43 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
         GasCell<float> gc;
         if (emit) gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
         cp_async_wait_all();
-#pragma unroll
-        for (int r = 0; r < G::NR1; ++r) {
-            const int c = t + r * G::NT;
-            if (c < G::N1) {
-                const double* d = stU + 4 * c;
-                Um[c_i1[r]] = make_float4(d2f_trunc(d[0]), d2f_trunc(d[1]), d2f_trunc(d[2]), d2f_trunc(d[3]));
-            }
-        }
+        Um[i_own] = to4(stU + 4 * t);
+        if (has_h) Um[i_h] = to4(stU + 4 * (G::NT + t));
         __syncthreads();
         if (q + 1 < qend) issue_plane(q + 1);
         cp_async_commit();
-        // closure of the R1 cells; z data of the own cell
-        float4 nU = zU, nP = zP;
-        float nl3 = zl3;
-#pragma unroll
-        for (int r = 0; r < G::NR1; ++r) {
-            const int c = t + r * G::NT;
-            if (c < G::N1) {
-                const int i = c_i1[r];
-                const float4 U = Um[i];
-                ClosureScalars<float> k = closure_scalars(U.x, U.y, U.z, U.w, chat, p1);
-                const float bx = k.b * U.y;
-                float l1x, l3x, l1y, l3y;
-                wave_speeds(k, U.y, chat, fixed, l1x, l3x);
-                wave_speeds(k, U.z, chat, fixed, l1y, l3y);
-                const float Pxy = bx * U.z, Pxz = bx * U.w, Pyz = k.b * U.z * U.w;
-                CX[i] = make_float4(k.a + bx * U.y, Pxy, Pxz, l1x);
-                CY[i] = make_float4(Pxy, k.a + k.b * U.z * U.z, Pyz, l1y);
-                L3[i] = make_float2(l3x, l3y);
-            }
-        }
+        // closure of the own cell (x, y and its z-direction data) and of the halo cell
+        float4 nU, nP;
+        float nl3;
         {
-            // z data of the own cell (tlx, tly)
-            const float4 U = Um[G::i1(tlx, tly)];
-            ClosureScalars<float> k = closure_scalars(U.x, U.y, U.z, U.w, chat, p1);
+            const float4 U = Um[i_own];
+            const ClosureScalars<float> k = closure_scalars(U.x, U.y, U.z, U.w, chat, p1);
+            closure_xy(i_own, U, k);
             float l1z, l3z;
             wave_speeds(k, U.w, chat, fixed, l1z, l3z);
             nU = U;
             nP = make_float4(k.b * U.y * U.w, k.b * U.z * U.w, k.a + k.b * U.w * U.w, l1z);
             nl3 = l3z;
         }
-        __syncthreads();
-        // x and y faces of the tile rows / columns
-        for (int f = t; f < G::NFX + G::NFY; f += G::NT) {
-            if (f < G::NFX) {
-                const int ly = f / (TX + 1), lx = f % (TX + 1);
-                const int iL = G::i1(lx - 1, ly), iR = iL + 1;
-                const float4 UL = Um[iL], UR = Um[iR], CL = CX[iL], CR = CX[iR];
-                const float4 FL = make_float4(chat * UL.y, chat * CL.x, chat * CL.y, chat * CL.z);
-                const float4 FR = make_float4(chat * UR.y, chat * CR.x, chat * CR.y, chat * CR.z);
-                Fx[f] = hll_pair(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x);
-            } else {
-                const int fc = f - G::NFX;
-                const int ly = fc / TX, lx = fc % TX;
-                const int iL = G::i1(lx, ly - 1), iR = iL + G::W1;
-                const float4 UL = Um[iL], UR = Um[iR], CL = CY[iL], CR = CY[iR];
-                const float4 FL = make_float4(chat * UL.z, chat * CL.x, chat * CL.y, chat * CL.z);
-                const float4 FR = make_float4(chat * UR.z, chat * CR.x, chat * CR.y, chat * CR.z);
-                Fy[fc] = hll_pair(UL, UR, FL, FR, CL.w, L3[iL].y, CR.w, L3[iR].y);
-            }
+        if (has_h) {
+            const float4 U = Um[i_h];
+            closure_xy(i_h, U, closure_scalars(U.x, U.y, U.z, U.w, chat, p1));
         }
         __syncthreads();
-        // own cell: x/y divergence of plane q, z face (q-1 | q), U^{m+1/2} of plane q - 1
+        // x face left of the own cell, y face below it, then the tile's top row and right column
+        Fx[tly * (TX + 1) + tlx] = xface(i_own - 1, i_own);
+        Fy[tly * TX + tlx] = yface(i_own - G::W1, i_own);
+        if (t < TX) {
+            const int iL = G::i1(t, TY - 1);
+            Fy[TY * TX + t] = yface(iL, iL + G::W1);
+        } else if (t < TX + TY) {
+            const int ly = t - TX, iL = G::i1(TX - 1, ly);
+            Fx[ly * (TX + 1) + TX] = xface(iL, iL + 1);
+        }
+        __syncthreads();
+        // own cell: x/y divergence of plane q, z face (q-1 | q), U^{m+1/2} of plane q - 1.  No barrier
+        // follows: every shared array written in the next plane is written after that plane's first
+        // barrier, which no thread passes before all threads have finished this block.
         {
             const int fl = tly * (TX + 1) + tlx, fb = tly * TX + tlx;
             const float4 ax = Fx[fl], bxf = Fx[fl + 1], ay = Fy[fb], by = Fy[fb + TX];
@@ -206,7 +235,6 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
             zl3 = nl3;
             dxy = nd;
         }
-        __syncthreads();
     }
     cp_async_wait_all();
 }
@@ -218,11 +246,16 @@ struct GeoCorr {
     static constexpr int NR2 = (N2 + NT - 1) / NT;
     static constexpr int NSX = (TX + 2) * TY, NSY = TX * (TY + 2);
     static constexpr int NCX = (TX + 1) * TY, NCY = TX * (TY + 1);
+    static constexpr int NHR = 2 * TX + 2 * TY;  // halo records: y records of rows -1, TY; x records of columns -1, TX
+    static_assert(NHR <= NT && TX + TY <= NT, "one extra item per thread at most");
     // float4 units: two U^{m+1/2} plane buffers, face-state records, fluxes
     static constexpr int UK = 0, SXo = UK + 2 * N2, SYo = SXo + 5 * NSX, CXo = SYo + 5 * NSY, CYo = CXo + NCX;
     static constexpr int END4 = CYo + NCY;
     __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4; }
     __device__ static __forceinline__ int i2(int lx, int ly) { return (lx + 2) + W2 * (ly + 2); }
+    // record slots: x record of (lx, ly), lx in [-1, TX]; y record of (lx, ly), ly in [-1, TY]
+    __device__ static __forceinline__ int sx(int lx, int ly) { return (lx + 1) + (TX + 2) * ly; }
+    __device__ static __forceinline__ int sy(int lx, int ly) { return lx + TX * (ly + 1); }
 };
 
 // Corrector over the interior column tile (x0, y0) for planes [z0, z1).
@@ -246,6 +279,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     const int gx = x0 + tlx, gy = y0 + tly;
     const bool own_col = gx < g.n[0] && gy < g.n[1];
     const long long pz = (long long)(g.n[0] + 4) * (g.n[1] + 4);
+    const long long nxy = (long long)g.n[0] * g.n[1];
 
     // the R2 plane of U^{m+1/2}: rows of W2 float4 starting at (x0 - 2, y0 + ly); all inside the padded array
     // except beyond the high edges of ragged tiles, which are clamped (those values are never used)
@@ -270,7 +304,36 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         }
     };
     const int ihc = G::i2(tlx, tly);
-    auto col = [&](int k) { return uh[(long long)(k + 2) * pz + (min(gx, g.n[0] + 1) + 2) + (long long)(g.n[0] + 4) * (min(gy, g.n[1] + 1) + 2)]; };
+    const int sx_own = G::sx(tlx, tly), sy_own = G::sy(tlx, tly);
+    // this thread's halo record, if any
+    const bool has_hr = t < G::NHR, hr_is_y = t < 2 * TX;
+    int hr_i = 0, hr_slot = 0;
+    if (has_hr) {
+        if (hr_is_y) {
+            const int ly = t < TX ? -1 : TY, lx = t % TX;
+            hr_i = G::i2(lx, ly);
+            hr_slot = G::sy(lx, ly);
+        } else {
+            const int hh = t - 2 * TX, ly = hh >> 1, lx = (hh & 1) ? TX : -1;
+            hr_i = G::i2(lx, ly);
+            hr_slot = G::sx(lx, ly);
+        }
+    }
+    // the own column of U^{m+1/2} (clamped for columns beyond ragged tile edges, whose values are unused)
+    const float4* colp = uh + (min(gx, g.n[0] + 1) + 2) + (long long)(g.n[0] + 4) * (min(gy, g.n[1] + 1) + 2);
+    auto col = [&](int k) { return colp[(long long)(k + 2) * pz]; };
+    auto store_rec = [](float4* S, int n, int slot, const float4 (&rec)[5]) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) S[v * n + slot] = rec[v];
+    };
+    auto hll_x = [&](int iL, int iR) {
+        const float4 LL = Sx[4 * G::NSX + iL], LR = Sx[4 * G::NSX + iR];
+        return hll_pair(Sx[2 * G::NSX + iL], Sx[iR], Sx[3 * G::NSX + iL], Sx[G::NSX + iR], LL.z, LL.w, LR.x, LR.y);
+    };
+    auto hll_y = [&](int iL, int iR) {
+        const float4 LL = Sy[4 * G::NSY + iL], LR = Sy[4 * G::NSY + iR];
+        return hll_pair(Sy[2 * G::NSY + iL], Sy[iR], Sy[3 * G::NSY + iL], Sy[G::NSY + iR], LL.z, LL.w, LR.x, LR.y);
+    };
 
     // lower z face of the first plane: face states of cells z0-1 and z0 from U^{m+1/2} at z0-2 .. z0+1
     float4 zpS, zpF, cfl;
@@ -289,50 +352,53 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         zpl3 = rb[4].w;
         ukp1 = u_1;
     }
+    long long li = own_col ? (long long)gx + (long long)g.n[0] * gy + (long long)z0 * nxy : 0;
     issue_plane(z0, 0);
     cp_async_commit();
 #pragma unroll 1
-    for (int k = z0; k < z1; ++k) {
+    for (int k = z0; k < z1; ++k, li += nxy) {
         const int buf = (k - z0) & 1;
         ukp2 = col(k + 2);
         // the own cell's FP64 state, temperature and gas, loaded here and used after the face phases
         double U0[4] = {0.0, 0.0, 0.0, 0.0}, Tn = 0.0;
         GasCell<float> gc;
-        long long li = 0;
         if (own_col) {
-            li = lin(g, gx, gy, k);
             U0[0] = __ldg(a.E + li);
             U0[1] = __ldg(a.G[0] + li);
             U0[2] = __ldg(a.G[1] + li);
             U0[3] = __ldg(a.G[2] + li);
             if (needT) Tn = a.T[li];
-            gc = load_gas<float, true>(g, a, gx, gy, k, false, false);
+            gc = gas_at(g, a, li);
         }
         cp_async_wait_all();
         __syncthreads();
         if (k + 1 < z1) issue_plane(k + 1, buf ^ 1);
         cp_async_commit();
         const float4* Uk = Ubuf + buf * G::N2;
-        // face-state records along x and y, and the z face (k | k+1) of the own column
-        for (int c = t; c < G::NSX + G::NSY; c += G::NT) {
+        // face-state records: the own cell along x and along y, then this thread's halo record
+        {
             float4 rec[5];
-            if (c < G::NSX) {
-                const int ly = c / (TX + 2), lx = c % (TX + 2) - 1;
-                const int i = G::i2(lx, ly);
-                const int fb = face_record<0>(Uk[i - 1], Uk[i], Uk[i + 1], chat, lim, p1, fixed, rec);
-                if (fb && lx >= 0 && lx < TX && x0 + lx < g.n[0] && y0 + ly < g.n[1]) cnt.face += 1;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) Sx[v * G::NSX + c] = rec[v];
+            const int fb = face_record<0>(Uk[ihc - 1], Uk[ihc], Uk[ihc + 1], chat, lim, p1, fixed, rec);
+            if (fb && own_col) cnt.face += 1;
+            store_rec(Sx, G::NSX, sx_own, rec);
+        }
+        {
+            float4 rec[5];
+            const int fb = face_record<1>(Uk[ihc - G::W2], Uk[ihc], Uk[ihc + G::W2], chat, lim, p1, fixed, rec);
+            if (fb && own_col) cnt.face += 1;
+            store_rec(Sy, G::NSY, sy_own, rec);
+        }
+        if (has_hr) {
+            float4 rec[5];
+            if (hr_is_y) {
+                face_record<1>(Uk[hr_i - G::W2], Uk[hr_i], Uk[hr_i + G::W2], chat, lim, p1, fixed, rec);
+                store_rec(Sy, G::NSY, hr_slot, rec);
             } else {
-                const int cy = c - G::NSX;
-                const int ly = cy / TX - 1, lx = cy % TX;
-                const int i = G::i2(lx, ly);
-                const int fb = face_record<1>(Uk[i - G::W2], Uk[i], Uk[i + G::W2], chat, lim, p1, fixed, rec);
-                if (fb && ly >= 0 && ly < TY && x0 + lx < g.n[0] && y0 + ly < g.n[1]) cnt.face += 1;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) Sy[v * G::NSY + cy] = rec[v];
+                face_record<0>(Uk[hr_i - 1], Uk[hr_i], Uk[hr_i + 1], chat, lim, p1, fixed, rec);
+                store_rec(Sx, G::NSX, hr_slot, rec);
             }
         }
+        // the z face (k | k+1) of the own column
         float4 cfh;
         {
             float4 rec[5];
@@ -345,23 +411,18 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             zpl3 = rec[4].w;
         }
         __syncthreads();
-        for (int f = t; f < G::NCX + G::NCY; f += G::NT) {
-            if (f < G::NCX) {
-                const int ly = f / (TX + 1), lx = f % (TX + 1);
-                const int iL = lx + (TX + 2) * ly, iR = iL + 1;
-                const float4 LL = Sx[4 * G::NSX + iL], LR = Sx[4 * G::NSX + iR];
-                Cx[f] = hll_pair(Sx[2 * G::NSX + iL], Sx[iR], Sx[3 * G::NSX + iL], Sx[G::NSX + iR], LL.z, LL.w,
-                                 LR.x, LR.y);
-            } else {
-                const int fc = f - G::NCX;
-                const int ly = fc / TX, lx = fc % TX;
-                const int iL = lx + TX * ly, iR = iL + TX;
-                const float4 LL = Sy[4 * G::NSY + iL], LR = Sy[4 * G::NSY + iR];
-                Cy[fc] = hll_pair(Sy[2 * G::NSY + iL], Sy[iR], Sy[3 * G::NSY + iL], Sy[G::NSY + iR], LL.z, LL.w,
-                                  LR.x, LR.y);
-            }
+        // fluxes: the x face left of the own cell, the y face below it, then the tile's top row and right column
+        Cx[tly * (TX + 1) + tlx] = hll_x(sx_own - 1, sx_own);
+        Cy[tly * TX + tlx] = hll_y(sy_own - TX, sy_own);
+        if (t < TX) {
+            Cy[TY * TX + t] = hll_y(G::sy(t, TY - 1), G::sy(t, TY));
+        } else if (t < TX + TY) {
+            const int ly = t - TX;
+            Cx[ly * (TX + 1) + TX] = hll_x(G::sx(TX - 1, ly), G::sx(TX, ly));
         }
         __syncthreads();
+        // own cell.  No barrier follows: every shared array written in the next plane is written after
+        // that plane's first barrier, which no thread passes before all threads have finished this block.
         if (own_col) {
             const int fl = tly * (TX + 1) + tlx, fb = tly * TX + tlx;
             const float4 ax = Cx[fl], bxf = Cx[fl + 1], ay = Cy[fb], by = Cy[fb + TX];
@@ -432,7 +493,6 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         }
         cfl = cfh;
         ukp1 = ukp2;
-        __syncthreads();
     }
     cp_async_wait_all();
 }
