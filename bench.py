@@ -52,6 +52,9 @@ def parse():
                     help="throughput: one 512^3 grid (the headline); ensemble: 64 independent grids of "
                          "32^3..128^3, one persistent launch per subcycle, against per-grid plain launches")
     ap.add_argument("--n-grids", type=int, default=64)
+    ap.add_argument("--traffic-from", default=None,
+                    help="write profiles/traffic.json from this ncu raw CSV (measured at --N, scaled to 512^3; "
+                         "--launch names the configuration) and exit")
     ap.add_argument("--ens-n-sub", type=int, default=50, help="subcycles per step of the ensemble workload")
     return ap.parse_args()
 
@@ -162,6 +165,49 @@ def run_reference(args):
             "data": "synthetic", "config": workload_config(args, "fp64"),
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def kernel_source_hash():
+    """SHA-256 over the CUDA sources of the library: ncu traffic recorded for other sources is stale."""
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_1306_0010_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()
+
+
+def record_traffic(csv_path, measured_N, target_N, launch_spec):
+    """Write profiles/traffic.json from an `ncu --page raw --csv` export: DRAM bytes per launch of each
+    split kernel, scaled from measured_N^3 to target_N^3 cells (traffic grows with the cell count)."""
+    import csv
+
+    names = {"predictor_kernel": "twopass_predictor_split", "corrector_kernel": "twopass_corrector_split"}
+    rows = list(csv.reader(open(csv_path)))
+    hdr, units = rows[0], rows[1]
+    scale = (target_N / measured_N) ** 3
+    out = {"note": f"dram__bytes_read.sum + dram__bytes_write.sum per launch, ncu at {measured_N}^3, scaled to "
+                   f"{target_N}^3 by the cell count", "source_sha256": kernel_source_hash()}
+    unit_mult = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    for r in rows[2:]:
+        kname = r[hdr.index("Kernel Name")]
+        key = next((v for k, v in names.items() if k in kname), None)
+        if key is None:
+            continue
+        b = 0.0
+        for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            j = hdr.index(m)
+            b += float(r[j].replace(",", "")) * unit_mult[units[j]]
+        out[key] = {"N": target_N, "launch": launch_spec, "bytes_per_launch": b * scale, "measured_N": measured_N,
+                    "measured_bytes_per_cell": b / measured_N ** 3}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out, indent=1))
 
 
 def launch_key(launch):
@@ -422,6 +468,8 @@ def run_ensemble(args):
 
 def main():
     args = parse()
+    if args.traffic_from:
+        return record_traffic(args.traffic_from, args.N, 512, args.launch)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
@@ -463,8 +511,10 @@ def main():
     roofline = kernel_roofline(kt, hbm_peak, peak_kind)
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_path):
-        tr = json.load(open(traffic_path)).get(roofline["kernel"])
-        if tr and tr.get("N") == args.N and tr.get("launch") == launch_key(launch):
+        trj = json.load(open(traffic_path))
+        tr = trj.get(roofline["kernel"])
+        if (tr and tr.get("N") == args.N and tr.get("launch") == launch_key(launch)
+                and trj.get("source_sha256") == kernel_source_hash()):
             roofline["traffic"] = tr["bytes_per_launch"]
     # the whole subcycle against the method's own bytes per cell-update (U^m, gas, T in; U^{m+1}, T out)
     sub_achieved = B_ALG["split"] * cells / (sub_ms * 1e-3) / 1e9
