@@ -13,6 +13,14 @@
 // half-step state written once and read once).
 #pragma once
 
+// resident CTAs per SM the two kernels are compiled for (register budget 65536 / (256 x this))
+#ifndef RHD_PRED_MIN_BLOCKS
+#define RHD_PRED_MIN_BLOCKS 4
+#endif
+#ifndef RHD_CORR_MIN_BLOCKS
+#define RHD_CORR_MIN_BLOCKS 3
+#endif
+
 namespace rhd {
 
 // index of (x, y, z), each in [-2, n+2), in the padded U^{m+1/2} array
@@ -120,9 +128,9 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
             d[3] = U[3];
         }
     };
-    auto issue_plane = [&](int q) {
+    // zoff = q * nxy, carried by the caller
+    auto issue_plane = [&](int q, long long zoff) {
         const bool fast = xy_inside && (unsigned)q < (unsigned)g.n[2];
-        const long long zoff = (long long)q * nxy;
         stage(stU + 4 * t, gx, gy, off_own, q, fast, zoff);
         if (has_h) stage(stU + 4 * (G::NT + t), hx, hy, off_h, q, fast, zoff);
     };
@@ -155,19 +163,30 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     float4 zU = make_float4(0.f, 0.f, 0.f, 0.f), zP = zU, dxy = zU, zfl = zU;
     float zl3 = 0.f;
     const int qbeg = z0 - 1, qend = z1 + 1;
-    issue_plane(qbeg);
+    // running 64-bit offsets: the staged plane's, and the own cell's U^{m+1/2} at plane q - 1 in the
+    // padded array
+    long long zoff = (long long)qbeg * nxy;
+    const long long pzs = (long long)(g.n[0] + 4) * (g.n[1] + 4);
+    long long uoff = pad_index(g, gx, gy, qbeg - 1);  // negative before the first written plane
+    issue_plane(qbeg, zoff);
+    zoff += nxy;
     cp_async_commit();
 #pragma unroll 1
-    for (int q = qbeg; q < qend; ++q) {
+    for (int q = qbeg; q < qend; ++q, zoff += nxy, uoff += pzs) {
         // gas of the own cell of plane q - 1, loaded here and used after the face phase
         const bool emit = q > qbeg + 1 && own_in_pad;
         GasCell<float> gc;
-        if (emit) gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
+        if (emit) {
+            // zoff is (q + 1) nxy here: the own cell of plane q - 1 is at off_own + zoff - 2 nxy
+            if (own_interior && (unsigned)(q - 1) < (unsigned)g.n[2] && !needT)
+                gc = gas_at(g, a, (long long)off_own + zoff - 2 * nxy);
+            else gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
+        }
         cp_async_wait_all();
         Um[i_own] = to4(stU + 4 * t);
         if (has_h) Um[i_h] = to4(stU + 4 * (G::NT + t));
         __syncthreads();
-        if (q + 1 < qend) issue_plane(q + 1);
+        if (q + 1 < qend) issue_plane(q + 1, zoff);
         cp_async_commit();
         // closure of the own cell (x, y and its z-direction data) and of the halo cell
         float4 nU, nP;
@@ -227,7 +246,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
                 theta_updates(g, gc, chat, hdt, U);
                 const int fx_ = realize(U, g.f_E_floor);
                 if (own_interior && p >= 0 && p < g.n[2]) cnt.fix += fx_;
-                uh[pad_index(g, gx, gy, p)] = f4(U);
+                uh[uoff] = f4(U);
             }
             zfl = zfh;
             zU = nU;
@@ -291,13 +310,18 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         const int xx = min(x0 + lx, g.n[0] + 1), yy = min(y0 + ly, g.n[1] + 1);
         c_gpos[r] = (xx + 2) + (g.n[0] + 4) * (yy + 2);
     }
-    auto issue_plane = [&](int k, int buf) {
-        const float4* base = uh + (long long)(k + 2) * pz;
+    // shared-memory destinations of this thread's copies, for both buffers
+    unsigned c_dsm[G::NR2];
+#pragma unroll
+    for (int r = 0; r < G::NR2; ++r) c_dsm[r] = (unsigned)__cvta_generic_to_shared(Ubuf + t + r * G::NT);
+    const unsigned buf_bytes = 16u * G::N2;
+    // base: the plane's first element in the padded array
+    auto issue_plane = [&](const float4* base, int buf) {
 #pragma unroll
         for (int r = 0; r < G::NR2; ++r) {
             const int c = t + r * G::NT;
             if (c < G::N2) {
-                unsigned dsm = (unsigned)__cvta_generic_to_shared(Ubuf + buf * G::N2 + c);
+                const unsigned dsm = c_dsm[r] + (buf ? buf_bytes : 0u);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dsm), "l"(base + c_gpos[r])
                              : "memory");
             }
@@ -353,12 +377,17 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         ukp1 = u_1;
     }
     long long li = own_col ? (long long)gx + (long long)g.n[0] * gy + (long long)z0 * nxy : 0;
-    issue_plane(z0, 0);
+    // running pointers (64-bit offsets advanced once per plane): the next plane to stage, and the
+    // own column of U^{m+1/2} two planes ahead
+    const float4* next_plane = uh + (long long)(z0 + 2) * pz;
+    const float4* colk2 = colp + (long long)(z0 + 4) * pz;
+    issue_plane(next_plane, 0);
+    next_plane += pz;
     cp_async_commit();
 #pragma unroll 1
-    for (int k = z0; k < z1; ++k, li += nxy) {
+    for (int k = z0; k < z1; ++k, li += nxy, next_plane += pz, colk2 += pz) {
         const int buf = (k - z0) & 1;
-        ukp2 = col(k + 2);
+        ukp2 = *colk2;
         // the own cell's FP64 state, temperature and gas, loaded here and used after the face phases
         double U0[4] = {0.0, 0.0, 0.0, 0.0}, Tn = 0.0;
         GasCell<float> gc;
@@ -372,7 +401,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         }
         cp_async_wait_all();
         __syncthreads();
-        if (k + 1 < z1) issue_plane(k + 1, buf ^ 1);
+        if (k + 1 < z1) issue_plane(next_plane, buf ^ 1);
         cp_async_commit();
         const float4* Uk = Ubuf + buf * G::N2;
         // face-state records: the own cell along x and along y, then this thread's halo record
@@ -498,7 +527,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 4) predictor_kernel(const __grid_constant__ StepParams P)
+__global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
@@ -511,7 +540,7 @@ __global__ void __launch_bounds__(TX* TY, 4) predictor_kernel(const __grid_const
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 3) corrector_kernel(const __grid_constant__ StepParams P)
+__global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
@@ -562,7 +591,7 @@ __device__ __forceinline__ bool ens_next(const EnsembleParams& P, EnsembleGrid& 
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 4) predictor_ens_kernel(const __grid_constant__ EnsembleParams P)
+__global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_ens_kernel(const __grid_constant__ EnsembleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long item_s;
@@ -583,7 +612,7 @@ __global__ void __launch_bounds__(TX* TY, 4) predictor_ens_kernel(const __grid_c
 }
 
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, 3) corrector_ens_kernel(const __grid_constant__ EnsembleParams P)
+__global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_ens_kernel(const __grid_constant__ EnsembleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ long long item_s;
