@@ -119,7 +119,8 @@ typedef struct {
     int64_t n_newton_fallback;   /* energy-exchange solves finished by bisection */
     int64_t n_nonfinite;         /* interior cells that produced a non-finite value */
     int32_t newton_iter_max;     /* largest Newton iteration count of one solve */
-    int32_t reserved;
+    int32_t wait_timeouts;       /* bounded device-side waits that ran out; nonzero makes rhd_get_stats
+                                    return RHD_ERR_TIMEOUT (the affected tiles were not updated) */
     double sum_E;                /* sum of E over the interior (current state), FP64, fixed order */
     double sum_F[3];             /* sums of Fx, Fy, Fz */
     double max_f;                /* max |F|/(cE) */

@@ -79,8 +79,8 @@ cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s)
     StepParams pc = p;
     pc.tiles_x = (p.g.n[0] + TX - 1) / TX;
     pc.tiles_y = (p.g.n[1] + TY - 1) / TY;
-    auto k = corrector_kernel<TX, TY>;
-    const size_t smem = GeoCorr<TX, TY>::bytes();
+    auto k = p.staging == 1 ? corrector_kernel<TX, TY, true> : corrector_kernel<TX, TY, false>;
+    const size_t smem = GeoCorr<TX, TY>::bytes() + 128;  // + alignment slack for TMA destinations
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(pc.tiles_x * pc.tiles_y), (unsigned)((p.g.n[2] + zc - 1) / zc));
@@ -94,7 +94,39 @@ cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s)
     return e != cudaSuccess ? e : launch_twopass_corrector(p, s);
 }
 
-bool tma_available() { return false; }
+// cuTensorMapEncodeTiled from the driver, found at run time (the library does not link libcuda)
+static decltype(&cuTensorMapEncodeTiled) tensor_map_encoder()
+{
+    static decltype(&cuTensorMapEncodeTiled) fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<decltype(&cuTensorMapEncodeTiled)>(p);
+    }();
+    return fn;
+}
+
+bool tma_available() { return tensor_map_encoder() != nullptr; }
+
+bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const int n[3])
+{
+    auto enc = tensor_map_encoder();
+    if (!enc || !uhalf) return false;
+    constexpr int TX = 32, TY = 8;
+    using G = GeoCorr<TX, TY>;
+    // uhalf as floats: x = 4 (n0 + 4) floats per row, n1 + 4 rows, n2 + 4 planes; strides in bytes
+    const cuuint64_t dims[3] = {4ull * (n[0] + 4), (cuuint64_t)(n[1] + 4), (cuuint64_t)(n[2] + 4)};
+    const cuuint64_t strides[2] = {16ull * (n[0] + 4), 16ull * (n[0] + 4) * (n[1] + 4)};
+    const cuuint32_t box[3] = {4u * G::W2, (cuuint32_t)G::H2, 1u};  // the tile + 2-cell halo of one plane
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, uhalf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 template <typename K>
 static int occupancy_of(K k, size_t smem, int threads)

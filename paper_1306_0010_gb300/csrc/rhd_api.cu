@@ -54,6 +54,8 @@ struct GridState {
     int variant = 0;              // RHD_VARIANT_FUSED / RHD_VARIANT_TWOPASS
     int staging = 0;              // RHD_STAGING_*
     float4* uhalf = nullptr;      // two-pass: padded U^{m+1/2}
+    CUtensorMap uh_map;           // its tensor map (staging RHD_STAGING_TMA), valid when uh_map_ok
+    bool uh_map_ok = false;
     bool tuned = false;           // RHD_FLAG_AUTOTUNE handled
     double tuned_ms = -1.0;       // time per subcycle measured by the last tuning
 };
@@ -489,6 +491,8 @@ StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double
     p.chat = chat;
     p.dt = dt;
     p.uhalf = gs.uhalf;
+    p.staging = gs.staging;
+    if (gs.staging == RHD_STAGING_TMA) p.uh_map = gs.uh_map;
     p.z_chunk = gs.z_chunk;
     p.tx = gs.tx;
     p.ty = gs.ty;
@@ -759,6 +763,12 @@ rhd_status apply_config(rhd_ctx* ctx, GridState& gs, const rhd_launch_config& c)
         if (st) return st;
     }
     if (c.variant != RHD_VARIANT_TWOPASS) dfree(gs.uhalf);
+    if (c.staging == RHD_STAGING_TMA) {
+        gs.uh_map_ok = encode_uhalf_map(&gs.uh_map, gs.uhalf, gs.desc.n);
+        if (!gs.uh_map_ok) return fail(ctx, RHD_ERR_CUDA, "tensor map of U^{m+1/2} could not be encoded");
+    } else {
+        gs.uh_map_ok = false;
+    }
     gs.variant = c.variant;
     gs.staging = c.staging;
     gs.tx = c.tile_x;
@@ -1219,9 +1229,11 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
     out->n_newton_fallback = (int64_t)hs.n_newton_fb;
     out->n_nonfinite = (int64_t)hs.n_nonfinite;
     out->newton_iter_max = (int32_t)hs.newton_iter_max;
+    out->wait_timeouts = (int32_t)hs.n_timeout;
     out->sum_E = sums[0];
     for (int d = 0; d < 3; ++d) out->sum_F[d] = sums[1 + d];
     out->max_f = sums[4];
+    if (out->wait_timeouts) return fail(ctx, RHD_ERR_TIMEOUT, "a device-side wait ran out; some tiles were not updated");
     return out->n_nonfinite ? RHD_ERR_NONFINITE : RHD_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (types only; the library does not link libcuda)
 #include <cuda_runtime.h>
 
 namespace rhd {
@@ -18,7 +19,7 @@ struct DevStats {
     unsigned long long n_newton_fb;
     unsigned long long n_nonfinite;
     unsigned int newton_iter_max;
-    unsigned int pad;
+    unsigned int n_timeout;     // bounded waits that ran out (the tile's work was abandoned)
 };
 
 // Per-grid constants of one subcycle launch.
@@ -66,7 +67,9 @@ struct StepParams {
     int z_chunk;                // planes per CTA
     int tx, ty;                 // tile shape (selects the kernel instantiation)
     int tiles_x, tiles_y;       // tile grid in x, y
+    int staging;                // two-pass corrector: 0 per-thread cp.async, 1 one TMA tile copy per plane
     DevStats* stats;
+    CUtensorMap uh_map;         // staging 1: tensor map of uhalf as floats {4 (n0+4), n1+4, n2+4}, box {4 (32+4), 8+4, 1}
 };
 
 // Ensemble work items: (grid, tile) pairs handed out by a global counter.
@@ -101,6 +104,9 @@ cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s);
 cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s);
 cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s);
 bool tma_available();  // tensor-map staging of the two-pass corrector can be used on this device
+// Encode the corrector's tensor map over a padded U^{m+1/2} array; false if the driver entry point is
+// missing or the encoding is refused.
+bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const int n[3]);
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 int ensemble_ctas_per_sm_fp64();

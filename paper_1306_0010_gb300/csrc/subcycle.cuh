@@ -661,7 +661,7 @@ __device__ __forceinline__ void max_counter(unsigned* dst, unsigned v)
 }
 
 struct Counters {
-    unsigned fix, face, theta, newton_fb, nonfinite, iter_max;
+    unsigned fix, face, theta, newton_fb, nonfinite, iter_max, timeout;
 };
 
 template <typename R>

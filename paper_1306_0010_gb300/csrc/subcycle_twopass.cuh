@@ -23,6 +23,50 @@
 
 namespace rhd {
 
+// ------------------------------------------------------------------------------------------------
+// TMA staging (tensor copies completed on an mbarrier), inline PTX
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make the initialised barriers visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// order this thread's earlier shared-memory accesses before later asynchronous-proxy accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// 3D tiled tensor copy global -> shared; (x, y, z) is the box origin in elements (x: floats, x*4 bytes
+// a multiple of 16, every coordinate >= 0)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+// Wait until the barrier's phase with parity ph has completed; gives up after max_polls polls
+// (each poll may suspend the thread for a bounded, implementation-defined time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned ph, unsigned max_polls)
+{
+    const unsigned a = smem_addr(bar);
+    for (unsigned it = 0; it < max_polls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(ph)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr unsigned kMaxPolls = 1u << 22;
+
 // index of (x, y, z), each in [-2, n+2), in the padded U^{m+1/2} array
 __device__ __forceinline__ long long pad_index(const GridParams& g, int x, int y, int z)
 {
@@ -277,11 +321,14 @@ struct GeoCorr {
     __device__ static __forceinline__ int sy(int lx, int ly) { return lx + TX * (ly + 1); }
 };
 
-// Corrector over the interior column tile (x0, y0) for planes [z0, z1).
-template <int TX, int TY>
+// Corrector over the interior column tile (x0, y0) for planes [z0, z1).  TMA: the tile + 2-cell halo
+// of each U^{m+1/2} plane arrives by one tensor copy (issued by thread 0, completed on mbar[buf]; map
+// and mbar are then required, and sm must be 128-byte aligned); otherwise by per-thread cp.async.
+template <int TX, int TY, bool TMA = false>
 __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridArrays& a, const float4* uh,
                                                double chat_d, double dt_d, int x0, int y0, int z0, int z1, float4* sm,
-                                               Counters& cnt)
+                                               Counters& cnt, const CUtensorMap* map = nullptr,
+                                               uint64_t* mbar = nullptr)
 {
     using G = GeoCorr<TX, TY>;
     const int t = threadIdx.x;
@@ -315,15 +362,23 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
 #pragma unroll
     for (int r = 0; r < G::NR2; ++r) c_dsm[r] = (unsigned)__cvta_generic_to_shared(Ubuf + t + r * G::NT);
     const unsigned buf_bytes = 16u * G::N2;
-    // base: the plane's first element in the padded array
-    auto issue_plane = [&](const float4* base, int buf) {
+    // base: the plane's first element in the padded array; k: the plane (TMA)
+    auto issue_plane = [&](const float4* base, int buf, int k) {
+        if constexpr (TMA) {
+            if (t == 0) {
+                fence_proxy_async();  // the buffer's earlier generic reads complete before the copy
+                mbar_arrive_expect_tx(mbar + buf, 16u * G::N2);
+                tma_load_3d(Ubuf + buf * G::N2, map, 4 * x0, y0, k + 2, mbar + buf);
+            }
+        } else {
 #pragma unroll
-        for (int r = 0; r < G::NR2; ++r) {
-            const int c = t + r * G::NT;
-            if (c < G::N2) {
-                const unsigned dsm = c_dsm[r] + (buf ? buf_bytes : 0u);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dsm), "l"(base + c_gpos[r])
-                             : "memory");
+            for (int r = 0; r < G::NR2; ++r) {
+                const int c = t + r * G::NT;
+                if (c < G::N2) {
+                    const unsigned dsm = c_dsm[r] + (buf ? buf_bytes : 0u);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dsm), "l"(base + c_gpos[r])
+                                 : "memory");
+                }
             }
         }
     };
@@ -381,9 +436,20 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     // own column of U^{m+1/2} two planes ahead
     const float4* next_plane = uh + (long long)(z0 + 2) * pz;
     const float4* colk2 = colp + (long long)(z0 + 4) * pz;
-    issue_plane(next_plane, 0);
+    if constexpr (TMA) {
+        if (t == 0) {
+            mbar_init(mbar + 0, 1);
+            mbar_init(mbar + 1, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+    issue_plane(next_plane, 0, z0);
     next_plane += pz;
     cp_async_commit();
+    bool timed_out = false;
+    int fail_buf = 0;
+    unsigned fail_ph = 0;
 #pragma unroll 1
     for (int k = z0; k < z1; ++k, li += nxy, next_plane += pz, colk2 += pz) {
         const int buf = (k - z0) & 1;
@@ -399,9 +465,21 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             if (needT) Tn = a.T[li];
             gc = gas_at(g, a, li);
         }
-        cp_async_wait_all();
-        __syncthreads();
-        if (k + 1 < z1) issue_plane(next_plane, buf ^ 1);
+        if constexpr (TMA) {
+            // completion of this plane's copy: buffer buf's ((k - z0) >> 1)-th use, phase parity = that & 1
+            const unsigned ph = ((k - z0) >> 1) & 1;
+            const bool ok = mbar_wait(mbar + buf, ph, kMaxPolls);
+            if (__syncthreads_or(!ok)) {
+                timed_out = true;
+                fail_buf = buf;
+                fail_ph = ph;
+                break;
+            }
+        } else {
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        if (k + 1 < z1) issue_plane(next_plane, buf ^ 1, k + 1);
         cp_async_commit();
         const float4* Uk = Ubuf + buf * G::N2;
         // face-state records: the own cell along x and along y, then this thread's halo record
@@ -524,6 +602,18 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         ukp1 = ukp2;
     }
     cp_async_wait_all();
+    if constexpr (TMA) {
+        if (timed_out) {
+            // a copy did not complete in time: count it, give the one copy in flight (the awaited one; the
+            // next plane's copy is issued only after a successful wait) another bounded wait, and leave the
+            // tile; the host reports RHD_ERR_TIMEOUT
+            if (t == 0) {
+                cnt.timeout += 1;
+                mbar_wait(mbar + fail_buf, fail_ph, kMaxPolls);
+            }
+            __syncthreads();
+        }
+    }
 }
 
 template <int TX, int TY>
@@ -539,22 +629,27 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_kernel(
     add_counter(&P.stats->n_fix, cnt.fix);
 }
 
-template <int TX, int TY>
+template <int TX, int TY, bool TMA>
 __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
     const int tile = blockIdx.x;
     const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
     const int z0 = (int)blockIdx.y * P.z_chunk;
     const int z1 = min(z0 + P.z_chunk, P.g.n[2]);
     Counters cnt = {0, 0, 0, 0, 0, 0};
-    corrector_tile<TX, TY>(P.g, P.a, P.uhalf, P.chat, P.dt, x0, y0, z0, z1, reinterpret_cast<float4*>(smem_raw), cnt);
+    // TMA destinations need 128-byte alignment: the launch adds 128 bytes of slack
+    float4* sm = reinterpret_cast<float4*>(smem_raw);
+    if constexpr (TMA) sm = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    corrector_tile<TX, TY, TMA>(P.g, P.a, P.uhalf, P.chat, P.dt, x0, y0, z0, z1, sm, cnt, &P.uh_map, mbar);
     add_counter(&P.stats->n_fix, cnt.fix);
     add_counter(&P.stats->n_face, cnt.face);
     add_counter(&P.stats->n_theta, cnt.theta);
     add_counter(&P.stats->n_newton_fb, cnt.newton_fb);
     add_counter(&P.stats->n_nonfinite, cnt.nonfinite);
     max_counter(&P.stats->newton_iter_max, cnt.iter_max);
+    if (cnt.timeout) atomicAdd(&P.stats->n_timeout, cnt.timeout);
 }
 
 // ------------------------------------------------------------------------------------------------

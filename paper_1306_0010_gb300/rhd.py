@@ -77,14 +77,14 @@ class Stats(ctypes.Structure):
         ("n_newton_fallback", ctypes.c_int64),
         ("n_nonfinite", ctypes.c_int64),
         ("newton_iter_max", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("wait_timeouts", ctypes.c_int32),
         ("sum_E", ctypes.c_double),
         ("sum_F", ctypes.c_double * 3),
         ("max_f", ctypes.c_double),
     ]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "sum_F")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "sum_F"}
         d["sum_F"] = tuple(self.sum_F)
         return d
 

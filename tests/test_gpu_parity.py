@@ -197,6 +197,31 @@ def test_config4_reduced_split(rhd, variant, flags):
     assert max(e.values()) <= SPLIT_TOL, e
 
 
+def test_split_twopass_tma_staging(rhd):
+    """The corrector's tile + 2-cell halo of U^{m+1/2} staged by one tensor (TMA) copy per plane:
+    ragged tiles at the high x / y edges (the box reads past the array and is zero-filled there),
+    several z chunks, every boundary kind."""
+    case = wl.parity_case("tma", (37, 11, 23), bc=(["periodic", "outflow", "reflect"], ["periodic", "outflow", "outflow"]),
+                          exchange="full", beta_tau=True, with_j=True, n_sub=3, seed=19, precision="split")
+    ref, _ = orc.subcycles(case)
+    for zc in (1, 5, 23):
+        g = rhd.Grid(case["desc"])
+        try:
+            g.set_launch_config(dict(variant="twopass", tile=(32, 8), z_chunk=zc, staging="tma"))
+        except rhd.RhdError:
+            g.close()
+            pytest.skip("TMA staging unavailable (no tensor-map encoder in the driver)")
+        g.load_case(case)
+        g.radiation_subcycle(case["n_sub"], case["chat"], case["dt"])
+        out = g.get_moments()
+        out["T"] = g.get_gas_state()
+        st = g.get_stats()
+        g.close()
+        assert st["wait_timeouts"] == 0 and st["n_nonfinite"] == 0
+        e = errors(out, ref, case["desc"])
+        assert max(e.values()) <= SPLIT_TOL, (zc, e)
+
+
 def test_split_twopass_z_chunks(rhd):
     """Predictor chunks cover the padded z range [-2, n+2) and corrector chunks the interior; ragged
     chunks of either kernel must not change the result beyond the split bound."""
