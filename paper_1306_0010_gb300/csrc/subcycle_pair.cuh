@@ -65,6 +65,26 @@ __device__ __forceinline__ void closure_pair(float2 E, float2 gx, float2 gy, flo
     l3 = p_mul(p_add(fd, sr), cs);
 }
 
+// Limited slope from the left and right differences (minmod, MC or none), as `limited` in
+// subcycle.cuh but with selects instead of branches: the same values, and straight-line code the
+// compiler can interleave with the other direction's record.
+__device__ __forceinline__ float limited_f(float dl, float dr, int lim)
+{
+    const float avg = 0.5f * (dl + dr);
+    const float m = fminf(fabsf(dl), fabsf(dr));
+    const float mag = lim == LIM_MC ? fminf(2.0f * m, fabsf(avg)) : m;
+    const bool same = (fminf(dl, dr) > 0.0f) | (fmaxf(dl, dr) < 0.0f);
+    const float r = same ? copysignf(mag, dl) : 0.0f;
+    return lim == LIM_NONE ? avg : r;
+}
+
+// E <= 0 or |G|^2 > (1 + tol) E^2, without short-circuit branches (same test as face_unrealizable)
+__device__ __forceinline__ int unrealizable_f(float4 U)
+{
+    const float g2 = U.y * U.y + U.z * U.z + U.w * U.w;
+    return (int)(!(U.x > 0.0f)) | (int)(g2 > (1.0f + Tol<float>::face) * (U.x * U.x));
+}
+
 // Face-state record of one cell in direction D (see face_states): minus state, its flux, plus state,
 // its flux, and (l1m, l3m, l1p, l3p).  Returns 1 if the slope was zeroed.
 template <int D>
@@ -72,14 +92,15 @@ __device__ __forceinline__ int face_record(float4 um, float4 u0, float4 up, floa
                                            float4 rec[5])
 {
     float4 sl;
-    sl.x = limited(u0.x - um.x, up.x - u0.x, lim);
-    sl.y = limited(u0.y - um.y, up.y - u0.y, lim);
-    sl.z = limited(u0.z - um.z, up.z - u0.z, lim);
-    sl.w = limited(u0.w - um.w, up.w - u0.w, lim);
+    sl.x = limited_f(u0.x - um.x, up.x - u0.x, lim);
+    sl.y = limited_f(u0.y - um.y, up.y - u0.y, lim);
+    sl.z = limited_f(u0.z - um.z, up.z - u0.z, lim);
+    sl.w = limited_f(u0.w - um.w, up.w - u0.w, lim);
     float4 Sm = make_float4(u0.x - 0.5f * sl.x, u0.y - 0.5f * sl.y, u0.z - 0.5f * sl.z, u0.w - 0.5f * sl.w);
     float4 Sp = make_float4(u0.x + 0.5f * sl.x, u0.y + 0.5f * sl.y, u0.z + 0.5f * sl.z, u0.w + 0.5f * sl.w);
-    const int fb = face_unrealizable(Sm.x, Sm.y, Sm.z, Sm.w) || face_unrealizable(Sp.x, Sp.y, Sp.z, Sp.w);
-    if (fb) Sm = Sp = u0;
+    const int fb = unrealizable_f(Sm) | unrealizable_f(Sp);
+    Sm = fb ? u0 : Sm;
+    Sp = fb ? u0 : Sp;
     float2 F[4], l1, l3;
     closure_pair<D>(make_float2(Sm.x, Sp.x), make_float2(Sm.y, Sp.y), make_float2(Sm.z, Sp.z),
                     make_float2(Sm.w, Sp.w), chat, p1, fixed, F, l1, l3);
@@ -108,6 +129,23 @@ __device__ __forceinline__ float4 hll_pair(float4 UL, float4 UR, float4 FL, floa
     const float2 lo = p_mul(p_add(p_lo(FL), p_lo(FR)), p_s(0.5f));
     const float2 hi = p_mul(p_add(p_hi(FL), p_hi(FR)), p_s(0.5f));
     return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// The same HLL flux with scalar FP32 operations (same operation order and fused multiply-adds as
+// hll_pair, so the same bits): cheaper where the operands are not already register pairs.
+__device__ __forceinline__ float4 hll4(float4 UL, float4 UR, float4 FL, float4 FR, float l1L, float l3L, float l1R,
+                                       float l3R)
+{
+    const float SRp = fmaxf(fmaxf(l3L, l3R), 0.f), SLm = fminf(fminf(l1L, l1R), 0.f);
+    const float den = SRp - SLm;
+    if (den > 0.f) {
+        const float a = SRp, b = -SLm, c = SRp * SLm, iv = rcp(den);
+        return make_float4(fmaf(c, UR.x - UL.x, fmaf(b, FR.x, a * FL.x)) * iv,
+                           fmaf(c, UR.y - UL.y, fmaf(b, FR.y, a * FL.y)) * iv,
+                           fmaf(c, UR.z - UL.z, fmaf(b, FR.z, a * FL.z)) * iv,
+                           fmaf(c, UR.w - UL.w, fmaf(b, FR.w, a * FL.w)) * iv);
+    }
+    return make_float4((FL.x + FR.x) * 0.5f, (FL.y + FR.y) * 0.5f, (FL.z + FR.z) * 0.5f, (FL.w + FR.w) * 0.5f);
 }
 
 __device__ __forceinline__ float4 f4(const float U[4]) { return make_float4(U[0], U[1], U[2], U[3]); }

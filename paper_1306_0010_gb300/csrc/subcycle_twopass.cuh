@@ -195,13 +195,13 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
         const float4 UL = Um[iL], UR = Um[iR], CL = CX[iL], CR = CX[iR];
         const float4 FL = make_float4(chat * UL.y, chat * CL.x, chat * CL.y, chat * CL.z);
         const float4 FR = make_float4(chat * UR.y, chat * CR.x, chat * CR.y, chat * CR.z);
-        return hll_pair(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x);
+        return hll4(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x);
     };
     auto yface = [&](int iL, int iR) {
         const float4 UL = Um[iL], UR = Um[iR], CL = CY[iL], CR = CY[iR];
         const float4 FL = make_float4(chat * UL.z, chat * CL.x, chat * CL.y, chat * CL.z);
         const float4 FR = make_float4(chat * UR.z, chat * CR.x, chat * CR.y, chat * CR.z);
-        return hll_pair(UL, UR, FL, FR, CL.w, L3[iL].y, CR.w, L3[iR].y);
+        return hll4(UL, UR, FL, FR, CL.w, L3[iL].y, CR.w, L3[iR].y);
     };
 
     float4 zU = make_float4(0.f, 0.f, 0.f, 0.f), zP = zU, dxy = zU, zfl = zU;
@@ -217,15 +217,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     cp_async_commit();
 #pragma unroll 1
     for (int q = qbeg; q < qend; ++q, zoff += nxy, uoff += pzs) {
-        // gas of the own cell of plane q - 1, loaded here and used after the face phase
         const bool emit = q > qbeg + 1 && own_in_pad;
-        GasCell<float> gc;
-        if (emit) {
-            // zoff is (q + 1) nxy here: the own cell of plane q - 1 is at off_own + zoff - 2 nxy
-            if (own_interior && (unsigned)(q - 1) < (unsigned)g.n[2] && !needT)
-                gc = gas_at(g, a, (long long)off_own + zoff - 2 * nxy);
-            else gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
-        }
         cp_async_wait_all();
         Um[i_own] = to4(stU + 4 * t);
         if (has_h) Um[i_h] = to4(stU + 4 * (G::NT + t));
@@ -275,10 +267,16 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
             if (q > qbeg) {
                 const float4 FL = make_float4(chat * zU.w, chat * zP.x, chat * zP.y, chat * zP.z);
                 const float4 FR = make_float4(chat * nU.w, chat * nP.x, chat * nP.y, chat * nP.z);
-                zfh = hll_pair(zU, nU, FL, FR, zP.w, zl3, nP.w, nl3);
+                zfh = hll4(zU, nU, FL, FR, zP.w, zl3, nP.w, nl3);
             }
             const int p = q - 1;
             if (emit) {
+                // gas of the own cell of plane q - 1; zoff is (q + 1) nxy here, so that cell is at
+                // off_own + zoff - 2 nxy in the interior arrays
+                GasCell<float> gc;
+                if (own_interior && (unsigned)(q - 1) < (unsigned)g.n[2] && !needT)
+                    gc = gas_at(g, a, (long long)off_own + zoff - 2 * nxy);
+                else gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
                 const float U0a[4] = {zU.x, zU.y, zU.z, zU.w};
                 const float div[4] = {dxy.x + (zfh.x - zfl.x) * idz, dxy.y + (zfh.y - zfl.y) * idz,
                                       dxy.z + (zfh.z - zfl.z) * idz, dxy.w + (zfh.w - zfl.w) * idz};
@@ -423,7 +421,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         float4 ra[5], rb[5];
         face_record<2>(u_m2, u_m1, u_0, chat, lim, p1, fixed, ra);
         const int fb = face_record<2>(u_m1, u_0, u_1, chat, lim, p1, fixed, rb);
-        if (fb && own_col) cnt.face += 1;
+        cnt.face += (unsigned)(fb & (int)own_col);
         cfl = hll_pair(ra[2], rb[0], ra[3], rb[1], ra[4].z, ra[4].w, rb[4].x, rb[4].y);
         zpS = rb[2];
         zpF = rb[3];
@@ -454,17 +452,6 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     for (int k = z0; k < z1; ++k, li += nxy, next_plane += pz, colk2 += pz) {
         const int buf = (k - z0) & 1;
         ukp2 = *colk2;
-        // the own cell's FP64 state, temperature and gas, loaded here and used after the face phases
-        double U0[4] = {0.0, 0.0, 0.0, 0.0}, Tn = 0.0;
-        GasCell<float> gc;
-        if (own_col) {
-            U0[0] = __ldg(a.E + li);
-            U0[1] = __ldg(a.G[0] + li);
-            U0[2] = __ldg(a.G[1] + li);
-            U0[3] = __ldg(a.G[2] + li);
-            if (needT) Tn = a.T[li];
-            gc = gas_at(g, a, li);
-        }
         if constexpr (TMA) {
             // completion of this plane's copy: buffer buf's ((k - z0) >> 1)-th use, phase parity = that & 1
             const unsigned ph = ((k - z0) >> 1) & 1;
@@ -486,13 +473,13 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         {
             float4 rec[5];
             const int fb = face_record<0>(Uk[ihc - 1], Uk[ihc], Uk[ihc + 1], chat, lim, p1, fixed, rec);
-            if (fb && own_col) cnt.face += 1;
+            cnt.face += (unsigned)(fb & (int)own_col);
             store_rec(Sx, G::NSX, sx_own, rec);
         }
         {
             float4 rec[5];
             const int fb = face_record<1>(Uk[ihc - G::W2], Uk[ihc], Uk[ihc + G::W2], chat, lim, p1, fixed, rec);
-            if (fb && own_col) cnt.face += 1;
+            cnt.face += (unsigned)(fb & (int)own_col);
             store_rec(Sy, G::NSY, sy_own, rec);
         }
         if (has_hr) {
@@ -510,7 +497,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         {
             float4 rec[5];
             const int fb = face_record<2>(Uk[ihc], ukp1, ukp2, chat, lim, p1, fixed, rec);
-            if (fb && k + 1 < z1 && own_col) cnt.face += 1;
+            cnt.face += (unsigned)(fb & (int)(k + 1 < z1) & (int)own_col);
             cfh = hll_pair(zpS, rec[0], zpF, rec[1], zpl1, zpl3, rec[4].x, rec[4].y);
             zpS = rec[2];
             zpF = rec[3];
@@ -531,6 +518,13 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         // own cell.  No barrier follows: every shared array written in the next plane is written after
         // that plane's first barrier, which no thread passes before all threads have finished this block.
         if (own_col) {
+            double U0[4], Tn = 0.0;
+            U0[0] = __ldg(a.E + li);
+            U0[1] = __ldg(a.G[0] + li);
+            U0[2] = __ldg(a.G[1] + li);
+            U0[3] = __ldg(a.G[2] + li);
+            if (needT) Tn = a.T[li];
+            const GasCell<float> gc = gas_at(g, a, li);
             const int fl = tly * (TX + 1) + tlx, fb = tly * TX + tlx;
             const float4 ax = Cx[fl], bxf = Cx[fl + 1], ay = Cy[fb], by = Cy[fb + TX];
             const float div[4] = {(bxf.x - ax.x) * idx + (by.x - ay.x) * idy + (cfh.x - cfl.x) * idz,
