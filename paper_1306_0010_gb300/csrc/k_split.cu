@@ -1,4 +1,6 @@
 // k_fp64.cu -- Split-precision (FP32 fluxes, FP64 state) instantiations of the fused subcycle kernel and of the ensemble kernel.
+#include <type_traits>
+
 #include "subcycle.cuh"
 
 namespace rhd {
@@ -79,7 +81,14 @@ cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s)
     StepParams pc = p;
     pc.tiles_x = (p.g.n[0] + TX - 1) / TX;
     pc.tiles_y = (p.g.n[1] + TY - 1) / TY;
-    auto k = p.staging == 1 ? corrector_kernel<TX, TY, true> : corrector_kernel<TX, TY, false>;
+    // one instantiation per staging and limiter (the limiter is a compile-time constant in the kernel)
+    auto pick = [&](auto tma) {
+        constexpr bool T = decltype(tma)::value;
+        return p.g.limiter == LIM_MC ? corrector_kernel<TX, TY, T, LIM_MC>
+               : p.g.limiter == LIM_NONE ? corrector_kernel<TX, TY, T, LIM_NONE>
+                                         : corrector_kernel<TX, TY, T, LIM_MINMOD>;
+    };
+    auto k = p.staging == 1 ? pick(std::true_type{}) : pick(std::false_type{});
     const size_t smem = GeoCorr<TX, TY>::bytes() + 128;  // + alignment slack for TMA destinations
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -65,17 +65,21 @@ __device__ __forceinline__ void closure_pair(float2 E, float2 gx, float2 gy, flo
     l3 = p_mul(p_add(fd, sr), cs);
 }
 
-// Limited slope from the left and right differences (minmod, MC or none), as `limited` in
-// subcycle.cuh but with selects instead of branches: the same values, and straight-line code the
-// compiler can interleave with the other direction's record.
+// minmod(a, b): the one of a, b nearer zero if they have the same sign, else 0.  One of the two terms
+// is always a signed zero, so the sum is exactly a, b or 0.
+__device__ __forceinline__ float minmod_f(float a, float b) { return fmaxf(0.0f, fminf(a, b)) + fminf(0.0f, fmaxf(a, b)); }
+
+// Limited slope from the left and right differences (minmod, MC or none): the same values as
+// `limited` in subcycle.cuh (MC = minmod(2 minmod(dl, dr), (dl + dr)/2)), as straight-line min / max
+// code the compiler can interleave with the other direction's record; with lim a compile-time
+// constant only the chosen limiter remains.
 __device__ __forceinline__ float limited_f(float dl, float dr, int lim)
 {
     const float avg = 0.5f * (dl + dr);
-    const float m = fminf(fabsf(dl), fabsf(dr));
-    const float mag = lim == LIM_MC ? fminf(2.0f * m, fabsf(avg)) : m;
-    const bool same = (fminf(dl, dr) > 0.0f) | (fmaxf(dl, dr) < 0.0f);
-    const float r = same ? copysignf(mag, dl) : 0.0f;
-    return lim == LIM_NONE ? avg : r;
+    const float mm = minmod_f(dl, dr);
+    if (lim == LIM_NONE) return avg;
+    if (lim == LIM_MC) return minmod_f(2.0f * mm, avg);
+    return mm;
 }
 
 // E <= 0 or |G|^2 > (1 + tol) E^2, without short-circuit branches (same test as face_unrealizable)

@@ -322,7 +322,7 @@ struct GeoCorr {
 // Corrector over the interior column tile (x0, y0) for planes [z0, z1).  TMA: the tile + 2-cell halo
 // of each U^{m+1/2} plane arrives by one tensor copy (issued by thread 0, completed on mbar[buf]; map
 // and mbar are then required, and sm must be 128-byte aligned); otherwise by per-thread cp.async.
-template <int TX, int TY, bool TMA = false>
+template <int TX, int TY, bool TMA = false, int LIMK = -1>
 __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridArrays& a, const float4* uh,
                                                double chat_d, double dt_d, int x0, int y0, int z0, int z1, float4* sm,
                                                Counters& cnt, const CUtensorMap* map = nullptr,
@@ -337,7 +337,8 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     float4* Cy = sm + G::CYo;
     const float chat = (float)chat_d, dt = (float)dt_d;
     const float idx = (float)g.inv_dx[0], idy = (float)g.inv_dx[1], idz = (float)g.inv_dx[2];
-    const int p1 = g.closure == 1, fixed = g.speeds == 1, lim = g.limiter;
+    // LIMK >= 0: the limiter is a compile-time constant (only its code is generated); -1: g.limiter
+    const int p1 = g.closure == 1, fixed = g.speeds == 1, lim = LIMK >= 0 ? LIMK : g.limiter;
     const bool needT = g.exchange == EX_FULL || g.exchange == EX_FROZEN_T;
     const int tlx = t % TX, tly = t / TX;
     const int gx = x0 + tlx, gy = y0 + tly;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_kernel(
     add_counter(&P.stats->n_fix, cnt.fix);
 }
 
-template <int TX, int TY, bool TMA>
+template <int TX, int TY, bool TMA, int LIMK>
 __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -636,7 +637,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(
     // TMA destinations need 128-byte alignment: the launch adds 128 bytes of slack
     float4* sm = reinterpret_cast<float4*>(smem_raw);
     if constexpr (TMA) sm = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    corrector_tile<TX, TY, TMA>(P.g, P.a, P.uhalf, P.chat, P.dt, x0, y0, z0, z1, sm, cnt, &P.uh_map, mbar);
+    corrector_tile<TX, TY, TMA, LIMK>(P.g, P.a, P.uhalf, P.chat, P.dt, x0, y0, z0, z1, sm, cnt, &P.uh_map, mbar);
     add_counter(&P.stats->n_fix, cnt.fix);
     add_counter(&P.stats->n_face, cnt.face);
     add_counter(&P.stats->n_theta, cnt.theta);
