@@ -65,6 +65,56 @@ __device__ __forceinline__ void closure_pair(float2 E, float2 gx, float2 gy, flo
     l3 = p_mul(p_add(fd, sr), cs);
 }
 
+// Closure coefficients of two states (lanes .x, .y): P = a I + b G G^T (a, b of closure_scalars) and
+// the wave speeds lambda_1, lambda_3 in direction D; the flux follows from (U, a, b) by flux_ab.
+template <int D>
+__device__ __forceinline__ void closure_ab_pair(float2 E, float2 gx, float2 gy, float2 gz, float chat, int p1,
+                                                int fixed, float2& a, float2& b, float2& l1, float2& l3)
+{
+    const float2 ch = p_s(chat);
+    const float2 invE = p_rcp(E);
+    const float2 g2 = p_fma(gz, gz, p_fma(gy, gy, p_mul(gx, gx)));
+    float2 f2 = p_mul(g2, p_mul(invE, invE));
+    f2.x = fminf(f2.x, 1.f);
+    f2.y = fminf(f2.y, 1.f);
+    const float2 s = p_sqrt(p_fma(p_s(-3.f), f2, p_s(4.f)));
+    const float2 inv2ps = p_rcp(p_add(s, p_s(2.f)));
+    const float2 sm1 = p_add(s, p_s(-1.f));
+    if (p1) {
+        a = p_mul(E, p_s(1.f / 3.f));
+        b = p_s(0.f);
+    } else {
+        a = p_mul(p_mul(sm1, E), p_s(1.f / 3.f));
+        b = p_mul(p_mul(inv2ps, invE), p_s(3.f));
+    }
+    if (fixed) {
+        l3 = p_s(chat * 0.57735026918962576451f);
+        l1 = p_s(-chat * 0.57735026918962576451f);
+        return;
+    }
+    const float2 gd = D == 0 ? gx : (D == 1 ? gy : gz);
+    const float2 fd = p_mul(gd, invE);
+    const float2 u = p_fma(p_s(-3.f), p_mul(p_mul(fd, fd), inv2ps), s);
+    float2 rad = p_mul(p_mul(sm1, p_s(2.f / 3.f)), u);
+    rad.x = fmaxf(rad.x, 0.f);
+    rad.y = fmaxf(rad.y, 0.f);
+    const float2 sr = p_sqrt(rad);
+    const float2 cs = p_mul(ch, p_rcp(s));
+    l1 = p_mul(p_sub(fd, sr), cs);
+    l3 = p_mul(p_add(fd, sr), cs);
+}
+
+// Flux chat (G_D, P_D.) of state U in direction D from its closure coefficients (same operations as
+// the flux of closure_pair).
+template <int D>
+__device__ __forceinline__ float4 flux_ab(float4 U, float a, float b, float chat)
+{
+    const float gd = D == 0 ? U.y : (D == 1 ? U.z : U.w);
+    const float bg = b * gd;
+    return make_float4(chat * gd, chat * (D == 0 ? fmaf(bg, U.y, a) : bg * U.y),
+                       chat * (D == 1 ? fmaf(bg, U.z, a) : bg * U.z), chat * (D == 2 ? fmaf(bg, U.w, a) : bg * U.w));
+}
+
 // minmod(a, b): the one of a, b nearer zero if they have the same sign, else 0.  One of the two terms
 // is always a signed zero, so the sum is exactly a, b or 0.
 __device__ __forceinline__ float minmod_f(float a, float b) { return fmaxf(0.0f, fminf(a, b)) + fminf(0.0f, fmaxf(a, b)); }
@@ -113,6 +163,32 @@ __device__ __forceinline__ int face_record(float4 um, float4 u0, float4 up, floa
     rec[2] = Sp;
     rec[3] = make_float4(F[0].y, F[1].y, F[2].y, F[3].y);
     rec[4] = make_float4(l1.x, l3.x, l1.y, l3.y);
+    return fb;
+}
+
+// Compact face-state record of one cell in direction D: minus state, plus state, their closure
+// coefficients (a-, b-, a+, b+) and (l1-, l3-, l1+, l3+).  Returns 1 if the slope was zeroed.
+template <int D>
+__device__ __forceinline__ int face_record_ab(float4 um, float4 u0, float4 up, float chat, int lim, int p1, int fixed,
+                                              float4 rec[4])
+{
+    float4 sl;
+    sl.x = limited_f(u0.x - um.x, up.x - u0.x, lim);
+    sl.y = limited_f(u0.y - um.y, up.y - u0.y, lim);
+    sl.z = limited_f(u0.z - um.z, up.z - u0.z, lim);
+    sl.w = limited_f(u0.w - um.w, up.w - u0.w, lim);
+    float4 Sm = make_float4(u0.x - 0.5f * sl.x, u0.y - 0.5f * sl.y, u0.z - 0.5f * sl.z, u0.w - 0.5f * sl.w);
+    float4 Sp = make_float4(u0.x + 0.5f * sl.x, u0.y + 0.5f * sl.y, u0.z + 0.5f * sl.z, u0.w + 0.5f * sl.w);
+    const int fb = unrealizable_f(Sm) | unrealizable_f(Sp);
+    Sm = fb ? u0 : Sm;
+    Sp = fb ? u0 : Sp;
+    float2 a, b, l1, l3;
+    closure_ab_pair<D>(make_float2(Sm.x, Sp.x), make_float2(Sm.y, Sp.y), make_float2(Sm.z, Sp.z),
+                       make_float2(Sm.w, Sp.w), chat, p1, fixed, a, b, l1, l3);
+    rec[0] = Sm;
+    rec[1] = Sp;
+    rec[2] = make_float4(a.x, b.x, a.y, b.y);
+    rec[3] = make_float4(l1.x, l3.x, l1.y, l3.y);
     return fb;
 }
 

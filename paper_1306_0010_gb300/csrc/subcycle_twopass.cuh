@@ -310,9 +310,12 @@ struct GeoCorr {
     static constexpr int NHR = 2 * TX + 2 * TY;  // halo records: y records of rows -1, TY; x records of columns -1, TX
     static_assert(NHR <= NT && TX + TY <= NT, "one extra item per thread at most");
     // float4 units: two U^{m+1/2} plane buffers, face-state records, fluxes
-    static constexpr int UK = 0, SXo = UK + 2 * N2, SYo = SXo + 5 * NSX, CXo = SYo + 5 * NSY, CYo = CXo + NCX;
+    // records: 4 float4 each (minus state, plus state, closure coefficients, wave speeds; face_record_ab)
+    static constexpr int UK = 0, SXo = UK + 2 * N2, SYo = SXo + 4 * NSX, CXo = SYo + 4 * NSY, CYo = CXo + NCX;
     static constexpr int END4 = CYo + NCY;
-    __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4; }
+    // the own cell's FP64 state and T (5 doubles) and rho, v (4 floats), staged per thread (SoA by field)
+    static constexpr int OD = 5, OG = 4;
+    __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4 + 8 * (size_t)OD * NT + 4 * (size_t)OG * NT; }
     __device__ static __forceinline__ int i2(int lx, int ly) { return (lx + 2) + W2 * (ly + 2); }
     // record slots: x record of (lx, ly), lx in [-1, TX]; y record of (lx, ly), ly in [-1, TY]
     __device__ static __forceinline__ int sx(int lx, int ly) { return (lx + 1) + (TX + 2) * ly; }
@@ -335,6 +338,8 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     float4* Sy = sm + G::SYo;
     float4* Cx = sm + G::CXo;
     float4* Cy = sm + G::CYo;
+    double* oD = reinterpret_cast<double*>(sm + G::END4) + t;                       // oD[q NT]: E, Gx, Gy, Gz, T
+    float* oG = reinterpret_cast<float*>(reinterpret_cast<double*>(sm + G::END4) + G::OD * G::NT) + t;  // rho, v
     const float chat = (float)chat_d, dt = (float)dt_d;
     const float idx = (float)g.inv_dx[0], idy = (float)g.inv_dx[1], idz = (float)g.inv_dx[2];
     // LIMK >= 0: the limiter is a compile-time constant (only its code is generated); -1: g.limiter
@@ -400,34 +405,43 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     // the own column of U^{m+1/2} (clamped for columns beyond ragged tile edges, whose values are unused)
     const float4* colp = uh + (min(gx, g.n[0] + 1) + 2) + (long long)(g.n[0] + 4) * (min(gy, g.n[1] + 1) + 2);
     auto col = [&](int k) { return colp[(long long)(k + 2) * pz]; };
-    auto store_rec = [](float4* S, int n, int slot, const float4 (&rec)[5]) {
+    auto store_rec = [](float4* S, int n, int slot, const float4 (&rec)[4]) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) S[v * n + slot] = rec[v];
+        for (int v = 0; v < 4; ++v) S[v * n + slot] = rec[v];
     };
+    // HLL at the face between record slots iL (its plus state) and iR (its minus state)
     auto hll_x = [&](int iL, int iR) {
-        const float4 LL = Sx[4 * G::NSX + iL], LR = Sx[4 * G::NSX + iR];
-        return hll_pair(Sx[2 * G::NSX + iL], Sx[iR], Sx[3 * G::NSX + iL], Sx[G::NSX + iR], LL.z, LL.w, LR.x, LR.y);
+        const float4 UL = Sx[G::NSX + iL], UR = Sx[iR];
+        const float4 cL = Sx[2 * G::NSX + iL], cR = Sx[2 * G::NSX + iR];
+        const float4 LL = Sx[3 * G::NSX + iL], LR = Sx[3 * G::NSX + iR];
+        return hll_pair(UL, UR, flux_ab<0>(UL, cL.z, cL.w, chat), flux_ab<0>(UR, cR.x, cR.y, chat), LL.z, LL.w, LR.x,
+                        LR.y);
     };
     auto hll_y = [&](int iL, int iR) {
-        const float4 LL = Sy[4 * G::NSY + iL], LR = Sy[4 * G::NSY + iR];
-        return hll_pair(Sy[2 * G::NSY + iL], Sy[iR], Sy[3 * G::NSY + iL], Sy[G::NSY + iR], LL.z, LL.w, LR.x, LR.y);
+        const float4 UL = Sy[G::NSY + iL], UR = Sy[iR];
+        const float4 cL = Sy[2 * G::NSY + iL], cR = Sy[2 * G::NSY + iR];
+        const float4 LL = Sy[3 * G::NSY + iL], LR = Sy[3 * G::NSY + iR];
+        return hll_pair(UL, UR, flux_ab<1>(UL, cL.z, cL.w, chat), flux_ab<1>(UR, cR.x, cR.y, chat), LL.z, LL.w, LR.x,
+                        LR.y);
     };
 
     // lower z face of the first plane: face states of cells z0-1 and z0 from U^{m+1/2} at z0-2 .. z0+1
-    float4 zpS, zpF, cfl;
-    float zpl1, zpl3;
+    float4 zpS, cfl;  // plus state of the previous cell in z, with its closure coefficients and speeds
+    float zpa, zpb, zpl1, zpl3;
     float4 ukp1, ukp2;  // U^{m+1/2} of the own column at k+1, k+2
     {
         const float4 u_m2 = col(z0 - 2), u_m1 = col(z0 - 1), u_0 = col(z0), u_1 = col(z0 + 1);
-        float4 ra[5], rb[5];
-        face_record<2>(u_m2, u_m1, u_0, chat, lim, p1, fixed, ra);
-        const int fb = face_record<2>(u_m1, u_0, u_1, chat, lim, p1, fixed, rb);
+        float4 ra[4], rb[4];
+        face_record_ab<2>(u_m2, u_m1, u_0, chat, lim, p1, fixed, ra);
+        const int fb = face_record_ab<2>(u_m1, u_0, u_1, chat, lim, p1, fixed, rb);
         cnt.face += (unsigned)(fb & (int)own_col);
-        cfl = hll_pair(ra[2], rb[0], ra[3], rb[1], ra[4].z, ra[4].w, rb[4].x, rb[4].y);
-        zpS = rb[2];
-        zpF = rb[3];
-        zpl1 = rb[4].z;
-        zpl3 = rb[4].w;
+        cfl = hll_pair(ra[1], rb[0], flux_ab<2>(ra[1], ra[2].z, ra[2].w, chat), flux_ab<2>(rb[0], rb[2].x, rb[2].y, chat),
+                       ra[3].z, ra[3].w, rb[3].x, rb[3].y);
+        zpS = rb[1];
+        zpa = rb[2].z;
+        zpb = rb[2].w;
+        zpl1 = rb[3].z;
+        zpl3 = rb[3].w;
         ukp1 = u_1;
     }
     long long li = own_col ? (long long)gx + (long long)g.n[0] * gy + (long long)z0 * nxy : 0;
@@ -467,43 +481,58 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             cp_async_wait_all();
             __syncthreads();
         }
+        // the own cell's data of this plane, one commit group, awaited before the own-cell block
+        if (own_col) {
+            cp_async8(oD + 0 * G::NT, a.E + li);
+            cp_async8(oD + 1 * G::NT, a.G[0] + li);
+            cp_async8(oD + 2 * G::NT, a.G[1] + li);
+            cp_async8(oD + 3 * G::NT, a.G[2] + li);
+            if (needT) cp_async8(oD + 4 * G::NT, a.T + li);
+            cp_async4(oG + 0 * G::NT, a.rho32 + li);
+            if (a.v32[0]) cp_async4(oG + 1 * G::NT, a.v32[0] + li);
+            if (a.v32[1]) cp_async4(oG + 2 * G::NT, a.v32[1] + li);
+            if (a.v32[2]) cp_async4(oG + 3 * G::NT, a.v32[2] + li);
+        }
+        cp_async_commit();
         if (k + 1 < z1) issue_plane(next_plane, buf ^ 1, k + 1);
         cp_async_commit();
         const float4* Uk = Ubuf + buf * G::N2;
         // face-state records: the own cell along x and along y, then this thread's halo record
         {
-            float4 rec[5];
-            const int fb = face_record<0>(Uk[ihc - 1], Uk[ihc], Uk[ihc + 1], chat, lim, p1, fixed, rec);
+            float4 rec[4];
+            const int fb = face_record_ab<0>(Uk[ihc - 1], Uk[ihc], Uk[ihc + 1], chat, lim, p1, fixed, rec);
             cnt.face += (unsigned)(fb & (int)own_col);
             store_rec(Sx, G::NSX, sx_own, rec);
         }
         {
-            float4 rec[5];
-            const int fb = face_record<1>(Uk[ihc - G::W2], Uk[ihc], Uk[ihc + G::W2], chat, lim, p1, fixed, rec);
+            float4 rec[4];
+            const int fb = face_record_ab<1>(Uk[ihc - G::W2], Uk[ihc], Uk[ihc + G::W2], chat, lim, p1, fixed, rec);
             cnt.face += (unsigned)(fb & (int)own_col);
             store_rec(Sy, G::NSY, sy_own, rec);
         }
         if (has_hr) {
-            float4 rec[5];
+            float4 rec[4];
             if (hr_is_y) {
-                face_record<1>(Uk[hr_i - G::W2], Uk[hr_i], Uk[hr_i + G::W2], chat, lim, p1, fixed, rec);
+                face_record_ab<1>(Uk[hr_i - G::W2], Uk[hr_i], Uk[hr_i + G::W2], chat, lim, p1, fixed, rec);
                 store_rec(Sy, G::NSY, hr_slot, rec);
             } else {
-                face_record<0>(Uk[hr_i - 1], Uk[hr_i], Uk[hr_i + 1], chat, lim, p1, fixed, rec);
+                face_record_ab<0>(Uk[hr_i - 1], Uk[hr_i], Uk[hr_i + 1], chat, lim, p1, fixed, rec);
                 store_rec(Sx, G::NSX, hr_slot, rec);
             }
         }
         // the z face (k | k+1) of the own column
         float4 cfh;
         {
-            float4 rec[5];
-            const int fb = face_record<2>(Uk[ihc], ukp1, ukp2, chat, lim, p1, fixed, rec);
+            float4 rec[4];
+            const int fb = face_record_ab<2>(Uk[ihc], ukp1, ukp2, chat, lim, p1, fixed, rec);
             cnt.face += (unsigned)(fb & (int)(k + 1 < z1) & (int)own_col);
-            cfh = hll_pair(zpS, rec[0], zpF, rec[1], zpl1, zpl3, rec[4].x, rec[4].y);
-            zpS = rec[2];
-            zpF = rec[3];
-            zpl1 = rec[4].z;
-            zpl3 = rec[4].w;
+            cfh = hll_pair(zpS, rec[0], flux_ab<2>(zpS, zpa, zpb, chat), flux_ab<2>(rec[0], rec[2].x, rec[2].y, chat), zpl1,
+                           zpl3, rec[3].x, rec[3].y);
+            zpS = rec[1];
+            zpa = rec[2].z;
+            zpb = rec[2].w;
+            zpl1 = rec[3].z;
+            zpl3 = rec[3].w;
         }
         __syncthreads();
         // fluxes: the x face left of the own cell, the y face below it, then the tile's top row and right column
@@ -518,14 +547,26 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         __syncthreads();
         // own cell.  No barrier follows: every shared array written in the next plane is written after
         // that plane's first barrier, which no thread passes before all threads have finished this block.
+        if constexpr (TMA) cp_async_wait_all();  // only the own-cell group is pending
+        else cp_async_wait_1();                   // the own-cell group; the next plane's may still be pending
         if (own_col) {
             double U0[4], Tn = 0.0;
-            U0[0] = __ldg(a.E + li);
-            U0[1] = __ldg(a.G[0] + li);
-            U0[2] = __ldg(a.G[1] + li);
-            U0[3] = __ldg(a.G[2] + li);
-            if (needT) Tn = a.T[li];
-            const GasCell<float> gc = gas_at(g, a, li);
+            U0[0] = oD[0 * G::NT];
+            U0[1] = oD[1 * G::NT];
+            U0[2] = oD[2 * G::NT];
+            U0[3] = oD[3 * G::NT];
+            if (needT) Tn = oD[4 * G::NT];
+            GasCell<float> gc;
+            gc.T = 0.0;
+            gc.rho = 0.0;
+            const float rr = oG[0];
+            gc.rho32 = rr;
+            gc.v[0] = a.v32[0] ? oG[1 * G::NT] : 0.0f;
+            gc.v[1] = a.v32[1] ? oG[2 * G::NT] : 0.0f;
+            gc.v[2] = a.v32[2] ? oG[3 * G::NT] : 0.0f;
+            gc.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, rr);
+            gc.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, rr);
+            gc.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
             const int fl = tly * (TX + 1) + tlx, fb = tly * TX + tlx;
             const float4 ax = Cx[fl], bxf = Cx[fl + 1], ay = Cy[fb], by = Cy[fb + TX];
             const float div[4] = {(bxf.x - ax.x) * idx + (by.x - ay.x) * idy + (cfh.x - cfl.x) * idz,
