@@ -121,6 +121,40 @@ static decltype(&cuTensorMapEncodeTiled) tensor_map_encoder()
 
 bool tma_available() { return tensor_map_encoder() != nullptr; }
 
+__global__ void to_um32_kernel(float4* dst, const double* E, const double* G0, const double* G1, const double* G2,
+                               long long n)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = make_float4(d2f_trunc(E[i]), d2f_trunc(G0[i]), d2f_trunc(G1[i]), d2f_trunc(G2[i]));
+}
+
+cudaError_t launch_to_um32(float4* dst, const double* E, const double* G0, const double* G1, const double* G2,
+                           long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long b = (n + 255) / 256;
+    to_um32_kernel<<<(unsigned)(b < 152 * 16 ? b : 152 * 16), 256, 0, s>>>(dst, E, G0, G1, G2, n);
+    return cudaGetLastError();
+}
+
+__global__ void to_gas4_kernel(float4* dst, const float* rho, const float* vx, const float* vy, const float* vz,
+                               long long n)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] = make_float4(rho[i], vx ? vx[i] : 0.0f, vy ? vy[i] : 0.0f, vz ? vz[i] : 0.0f);
+}
+
+cudaError_t launch_to_gas4(float4* dst, const float* rho32, const float* vx, const float* vy, const float* vz,
+                           long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long b = (n + 255) / 256;
+    to_gas4_kernel<<<(unsigned)(b < 152 * 16 ? b : 152 * 16), 256, 0, s>>>(dst, rho32, vx, vy, vz, n);
+    return cudaGetLastError();
+}
+
 bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const int n[3])
 {
     auto enc = tensor_map_encoder();

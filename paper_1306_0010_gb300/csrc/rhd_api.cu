@@ -54,6 +54,9 @@ struct GridState {
     int variant = 0;              // RHD_VARIANT_FUSED / RHD_VARIANT_TWOPASS
     int staging = 0;              // RHD_STAGING_*
     float4* uhalf = nullptr;      // two-pass: padded U^{m+1/2}
+    float4* um32 = nullptr;       // two-pass: FP32 mirror of the current state (valid when um32_ok)
+    float4* gas4 = nullptr;       // two-pass: interleaved FP32 (rho, v) (valid when gas4_ok)
+    bool um32_ok = false, gas4_ok = false;
     CUtensorMap uh_map;           // its tensor map (staging RHD_STAGING_TMA), valid when uh_map_ok
     bool uh_map_ok = false;
     bool tuned = false;           // RHD_FLAG_AUTOTUNE handled
@@ -277,12 +280,42 @@ void free_grid(GridState& gs)
     dfree(gs.kF32);
     dfree(gs.j32);
     dfree(gs.uhalf);
+    dfree(gs.um32);
+    dfree(gs.gas4);
 }
 
 void clear_graphs(rhd_ctx* ctx)
 {
     for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
+}
+
+// Buffers of the two-pass split path: U^{m+1/2} on the padded grid, the FP32 state mirror and the
+// interleaved FP32 gas (allocated once, kept until the variant changes).
+rhd_status alloc_twopass(rhd_ctx* ctx, GridState& gs)
+{
+    rhd_status st;
+    if (!gs.uhalf) {
+        size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
+        if ((st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np))) return st;
+    }
+    if (!gs.um32) {
+        if ((st = dalloc(ctx, (void**)&gs.um32, sizeof(float4) * (size_t)gs.ncell))) return st;
+        gs.um32_ok = false;
+    }
+    if (!gs.gas4) {
+        if ((st = dalloc(ctx, (void**)&gs.gas4, sizeof(float4) * (size_t)gs.ncell))) return st;
+        gs.gas4_ok = false;
+    }
+    return RHD_OK;
+}
+
+void free_twopass(GridState& gs)
+{
+    dfree(gs.uhalf);
+    dfree(gs.um32);
+    dfree(gs.gas4);
+    gs.um32_ok = gs.gas4_ok = false;
 }
 
 rhd_status alloc_grid(rhd_ctx* ctx, GridState& gs)
@@ -301,11 +334,7 @@ rhd_status alloc_grid(rhd_ctx* ctx, GridState& gs)
         st = dalloc(ctx, (void**)&gs.rho32, sizeof(float) * (size_t)gs.ncell);
         if (st) return st;
     }
-    if (gs.variant == 1) {
-        size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
-        st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np);
-        if (st) return st;
-    }
+    if (gs.variant == RHD_VARIANT_TWOPASS) return alloc_twopass(ctx, gs);
     return RHD_OK;
 }
 
@@ -404,6 +433,7 @@ rhd_status set_gas(rhd_ctx* ctx, GridState& gs, const double* rho, const double*
     if ((st = set_optional(ctx, gs, gs.kF, gs.kF32, gs.has_kF, kF, on_device))) return st;
     if ((st = set_optional(ctx, gs, gs.j, gs.j32, gs.has_j, j, on_device))) return st;
     gs.has_gas = true;
+    gs.gas4_ok = false;
     clear_graphs(ctx);  // array pointers may have changed
     return leave(ctx);
 }
@@ -426,6 +456,7 @@ rhd_status set_moments(rhd_ctx* ctx, GridState& gs, const double* E, const doubl
         }
     }
     gs.has_moments = true;
+    gs.um32_ok = false;
     return leave(ctx);
 }
 
@@ -488,6 +519,9 @@ StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double
     a.kP32 = gs.has_kP ? gs.kP32 : nullptr;
     a.kF32 = gs.has_kF ? gs.kF32 : nullptr;
     a.j32 = gs.has_j ? gs.j32 : nullptr;
+    const bool twopass = gs.variant == RHD_VARIANT_TWOPASS;
+    a.um32 = twopass ? gs.um32 : nullptr;
+    a.gas4 = twopass ? gs.gas4 : nullptr;
     p.chat = chat;
     p.dt = dt;
     p.uhalf = gs.uhalf;
@@ -569,6 +603,23 @@ rhd_status timed_launch(rhd_ctx* ctx, int kernel, double alg_bytes, Fn&& fn)
     return RHD_OK;
 }
 
+// Before two-pass subcycles: rebuild the FP32 state mirror (from buffer cur) and the interleaved FP32
+// gas if they may be stale.  Each two-pass subcycle's corrector rewrites the mirror with U^{m+1}.
+rhd_status prepare_twopass(rhd_ctx* ctx, GridState& gs)
+{
+    if (gs.variant != RHD_VARIANT_TWOPASS) return RHD_OK;
+    if (!gs.gas4_ok && gs.has_gas) {
+        RHD_CUDA(ctx, launch_to_gas4(gs.gas4, gs.rho32, gs.v32[0], gs.v32[1], gs.v32[2], gs.ncell, ctx->stream));
+        gs.gas4_ok = true;
+    }
+    if (!gs.um32_ok && gs.has_moments) {
+        double** U = gs.U[ctx->cur];
+        RHD_CUDA(ctx, launch_to_um32(gs.um32, U[0], U[1], U[2], U[3], gs.ncell, ctx->stream));
+        gs.um32_ok = true;
+    }
+    return RHD_OK;
+}
+
 rhd_status launch_one(rhd_ctx* ctx, GridState& gs, int src, double chat, double dt)
 {
     StepParams p = step_params(ctx, gs, src, chat, dt);
@@ -577,9 +628,11 @@ rhd_status launch_one(rhd_ctx* ctx, GridState& gs, int src, double chat, double 
     if (gs.desc.precision != RHD_SPLIT)
         return timed_launch(ctx, K_FUSED_FP64, nc * alg_bytes_per_cell(gs, K_FUSED_FP64),
                             [&] { return launch_subcycle_fp64(p, s); });
-    if (gs.variant != RHD_VARIANT_TWOPASS)
+    if (gs.variant != RHD_VARIANT_TWOPASS) {
+        gs.um32_ok = false;
         return timed_launch(ctx, K_FUSED_SPLIT, nc * alg_bytes_per_cell(gs, K_FUSED_SPLIT),
                             [&] { return launch_subcycle_split(p, s); });
+    }
     rhd_status st = timed_launch(ctx, K_PREDICTOR, nc * alg_bytes_per_cell(gs, K_PREDICTOR),
                                  [&] { return launch_twopass_predictor(p, s); });
     if (st) return st;
@@ -704,7 +757,10 @@ rhd_status ens_launch(rhd_ctx* ctx, double chat, int src)
     ep.stats = ctx->dstats;
     if (!twopass) {
         double bytes = 0.0;
-        for (auto& gs : ctx->grids) bytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_FUSED_FP64);
+        for (auto& gs : ctx->grids) {
+            bytes += (double)gs.ncell * alg_bytes_per_cell(gs, K_FUSED_FP64);
+            gs.um32_ok = false;
+        }
         ep.counter = ctx->d_counter;
         RHD_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(unsigned long long), ctx->stream));
         return timed_launch(ctx, split ? K_ENS_SPLIT : K_ENS_FP64, bytes, [&] {
@@ -757,12 +813,13 @@ bool config_supported(const GridState& gs, const rhd_launch_config& c)
 // Make c the configuration of gs (c must be supported); allocates or frees the U^{m+1/2} buffer.
 rhd_status apply_config(rhd_ctx* ctx, GridState& gs, const rhd_launch_config& c)
 {
-    if (c.variant == RHD_VARIANT_TWOPASS && !gs.uhalf) {
-        size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
-        rhd_status st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np);
+    if (c.variant == RHD_VARIANT_TWOPASS) {
+        rhd_status st = alloc_twopass(ctx, gs);
         if (st) return st;
+    } else {
+        free_twopass(gs);
     }
-    if (c.variant != RHD_VARIANT_TWOPASS) dfree(gs.uhalf);
+    gs.um32_ok = false;
     if (c.staging == RHD_STAGING_TMA) {
         gs.uh_map_ok = encode_uhalf_map(&gs.uh_map, gs.uhalf, gs.desc.n);
         if (!gs.uh_map_ok) return fail(ctx, RHD_ERR_CUDA, "tensor map of U^{m+1/2} could not be encoded");
@@ -925,7 +982,9 @@ rhd_status grid_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_lau
             continue;
         }
         double ms = -1.0;
-        st = time_launches(ctx, reps, [&] { return launch_one(ctx, gs, ctx->cur, chat, dt); }, &ms);
+        st = prepare_twopass(ctx, gs);
+        if (!st) st = time_launches(ctx, reps, [&] { return launch_one(ctx, gs, ctx->cur, chat, dt); }, &ms);
+        gs.um32_ok = false;  // the timed correctors rewrote the mirror with the next state
         if (!st) st = tune_restore(ctx, b);
         cand[i].ms_per_subcycle = ms;
         if (!st && ms >= 0.0 && (best < 0 || ms < cand[best].ms_per_subcycle)) best = (int)i;
@@ -975,14 +1034,14 @@ rhd_status grid_tune_once(rhd_ctx* ctx, double chat, double dt)
 rhd_status ens_apply(rhd_ctx* ctx, int v, int zc)
 {
     for (auto& gs : ctx->grids) {
-        if (v == RHD_VARIANT_TWOPASS && !gs.uhalf) {
-            size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
-            rhd_status st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np);
+        if (v == RHD_VARIANT_TWOPASS) {
+            rhd_status st = alloc_twopass(ctx, gs);
             if (st) return st;
         }
     }
     for (auto& gs : ctx->grids) {
-        if (v != RHD_VARIANT_TWOPASS) dfree(gs.uhalf);
+        if (v != RHD_VARIANT_TWOPASS) free_twopass(gs);
+        gs.um32_ok = false;
         gs.variant = v;
         gs.z_chunk = zc;  // one chunk length for all grids, as at creation
     }
@@ -1022,8 +1081,11 @@ rhd_status ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_gri
             continue;
         }
         double dt_sig = 0.0, ms = -1.0;
-        st = ens_prepare(ctx, chat, dt_per_grid, &dt_sig);
+        for (auto& gs : ctx->grids)
+            if (!st) st = prepare_twopass(ctx, gs);
+        if (!st) st = ens_prepare(ctx, chat, dt_per_grid, &dt_sig);
         if (!st) st = time_launches(ctx, reps, [&] { return ens_launch(ctx, chat, ctx->cur); }, &ms);
+        for (auto& gs : ctx->grids) gs.um32_ok = false;
         if (!st) st = tune_restore(ctx, b);
         cand[i].ms_per_subcycle = ms;
         if (!st && ms >= 0.0 && (best < 0 || ms < cand[best].ms_per_subcycle)) best = (int)i;
@@ -1159,6 +1221,7 @@ rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double d
     if (n_sub == 0) return RHD_OK;
     if ((gs.desc.flags & RHD_FLAG_AUTOTUNE) && !gs.tuned && (st = grid_tune_once(ctx, chat, dt))) return st;
     if ((st = enter(ctx))) return st;
+    if ((st = prepare_twopass(ctx, gs))) return st;
     bool use_graph = !(gs.desc.flags & RHD_FLAG_NO_GRAPH) && !ctx->ktiming;
     st = run_steps(ctx, n_sub, chat, dt, use_graph, [&](int src) { return launch_one(ctx, gs, src, chat, dt); });
     if (st) return st;
@@ -1378,6 +1441,8 @@ rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const dou
         (st = ensemble_tune_once(ctx, chat, dt_per_grid)))
         return st;
     if ((st = enter(ctx))) return st;
+    for (auto& gs : ctx->grids)
+        if ((st = prepare_twopass(ctx, gs))) return st;
     double dt_sig = 0.0;
     if ((st = ens_prepare(ctx, chat, dt_per_grid, &dt_sig))) return st;
     bool use_graph = !(ctx->grids[0].desc.flags & RHD_FLAG_NO_GRAPH) && !ctx->ktiming;

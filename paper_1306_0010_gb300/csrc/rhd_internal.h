@@ -57,6 +57,10 @@ struct GridArrays {
     const float* kP32;
     const float* kF32;
     const float* j32;
+    // two-pass split path only (else NULL):
+    float4* um32;               // U^m as FP32 (each component truncated toward zero): read by the predictor,
+                                // rewritten with U^{m+1} by the corrector
+    const float4* gas4;         // (rho, vx, vy, vz) as FP32 per cell (the FP32 gas copies interleaved)
 };
 
 struct StepParams {
@@ -104,6 +108,12 @@ cudaError_t launch_twopass_split(const StepParams& p, cudaStream_t s);
 cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s);
 cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s);
 bool tma_available();  // tensor-map staging of the two-pass corrector can be used on this device
+// FP32 mirror of the FP64 state (E, G): dst[i] = truncation toward zero of each component
+cudaError_t launch_to_um32(float4* dst, const double* E, const double* G0, const double* G1, const double* G2,
+                           long long n, cudaStream_t s);
+// interleaved FP32 gas: dst[i] = (rho32[i], vx[i], vy[i], vz[i]), absent velocity components zero
+cudaError_t launch_to_gas4(float4* dst, const float* rho32, const float* vx, const float* vy, const float* vz,
+                           long long n, cudaStream_t s);
 // Encode the corrector's tensor map over a padded U^{m+1/2} array; false if the driver entry point is
 // missing or the encoding is refused.
 bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const int n[3]);

@@ -104,11 +104,12 @@ struct GeoPred {
     static constexpr int NH = N1 - NT;  // halo cells of the tile + 1 region: rows -1 and TY, columns -1 and TX
     static_assert(NH <= NT && TX + TY <= NT, "one extra item per thread at most");
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-    // float4 units
-    static constexpr int UM = 0, CXo = UM + N1, CYo = CXo + N1, L3o = CYo + N1;
-    static constexpr int FXo = L3o + (N1 + 1) / 2, FYo = FXo + NFX, END4 = FYo + NFY;
-    static constexpr int ST = 4 * N1;  // staged FP64 U^m: own cells at 4 t, halo cells at 4 (NT + h)
-    __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4 + 8 * (size_t)ST; }
+    // float4 units: U^m of the tile + 1 region (two plane buffers), closure data, fluxes, and three
+    // per-thread slots for the own cell's gas (rho, vx, vy, vz): plane p's gas is copied when plane p
+    // is staged and read at the end of plane p + 1, after plane p + 2 has been issued
+    static constexpr int UM = 0, CXo = UM + 2 * N1, CYo = CXo + N1, L3o = CYo + N1;
+    static constexpr int FXo = L3o + (N1 + 1) / 2, FYo = FXo + NFX, GSo = FYo + NFY, END4 = GSo + 3 * NT;
+    __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4; }
     __device__ static __forceinline__ int i1(int lx, int ly) { return (lx + 1) + W1 * (ly + 1); }
     // the h-th halo cell: rows ly = -1 and ly = TY with lx from -1 to TX, then columns lx = -1, TX
     __device__ static __forceinline__ void halo(int h, int& lx, int& ly)
@@ -131,13 +132,13 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
 {
     using G = GeoPred<TX, TY>;
     const int t = threadIdx.x;
-    float4* Um = sm + G::UM;
+    float4* Um0 = sm + G::UM;  // plane buffers Um0[buf * N1 + i]
     float4* CX = sm + G::CXo;
     float4* CY = sm + G::CYo;
     float2* L3 = reinterpret_cast<float2*>(sm + G::L3o);
     float4* Fx = sm + G::FXo;
     float4* Fy = sm + G::FYo;
-    double* stU = reinterpret_cast<double*>(sm + G::END4);
+    float4* gsl = sm + G::GSo + t;  // gsl[(p % 3) NT]: the own cell's (rho, vx, vy, vz) of plane p
     const float chat = (float)chat_d, hdt = 0.5f * (float)dt_d;
     const float idx = (float)g.inv_dx[0], idy = (float)g.inv_dx[1], idz = (float)g.inv_dx[2];
     const int p1 = g.closure == 1, fixed = g.speeds == 1;
@@ -156,30 +157,26 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     const bool xy_inside = x0 - 1 >= 0 && x0 + TX + 1 <= g.n[0] && y0 - 1 >= 0 && y0 + TY + 1 <= g.n[1];
     const int off_own = gx + g.n[0] * gy, off_h = hx + g.n[0] * hy;  // used only when xy_inside
 
-    auto stage = [&](double* d, int x, int y, int off, int q, bool fast, long long zoff) {
+    // U^m of one cell into the plane buffer: in-grid cells from the FP32 mirror (the FP64 state truncated
+    // toward zero), ghost cells by the boundary rule applied to the FP64 state, then truncated the same way
+    auto stage = [&](float4* d, int x, int y, int off, int q, bool fast, long long zoff) {
         if (fast || inside(g, x, y, q)) {
-            const long long i = fast ? zoff + off : lin(g, x, y, q);
-            cp_async8(d + 0, a.E + i);
-            cp_async8(d + 1, a.G[0] + i);
-            cp_async8(d + 2, a.G[1] + i);
-            cp_async8(d + 3, a.G[2] + i);
+            cp_async16(d, a.um32 + (fast ? zoff + off : lin(g, x, y, q)));
         } else {  // ghost cell: boundary rule (sign flips, Dirichlet values)
             double U[4];
             load_U(g, a, x, y, q, U);
-            d[0] = U[0];
-            d[1] = U[1];
-            d[2] = U[2];
-            d[3] = U[3];
+            *d = make_float4(d2f_trunc(U[0]), d2f_trunc(U[1]), d2f_trunc(U[2]), d2f_trunc(U[3]));
         }
     };
     // zoff = q * nxy, carried by the caller
-    auto issue_plane = [&](int q, long long zoff) {
+    auto issue_plane = [&](int q, long long zoff, int buf) {
         const bool fast = xy_inside && (unsigned)q < (unsigned)g.n[2];
-        stage(stU + 4 * t, gx, gy, off_own, q, fast, zoff);
-        if (has_h) stage(stU + 4 * (G::NT + t), hx, hy, off_h, q, fast, zoff);
-    };
-    auto to4 = [](const double* d) {
-        return make_float4(d2f_trunc(d[0]), d2f_trunc(d[1]), d2f_trunc(d[2]), d2f_trunc(d[3]));
+        float4* Ub = Um0 + buf * G::N1;
+        stage(Ub + i_own, gx, gy, off_own, q, fast, zoff);
+        if (has_h) stage(Ub + i_h, hx, hy, off_h, q, fast, zoff);
+        // the own cell's gas of plane q, for its half step one plane later
+        if (own_interior && (unsigned)q < (unsigned)g.n[2] && !needT)
+            cp_async16(gsl + (q % 3) * G::NT, a.gas4 + zoff + off_own);
     };
     auto closure_xy = [&](int i, const float4& U, const ClosureScalars<float>& k) {
         float l1x, l3x, l1y, l3y;
@@ -191,6 +188,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
         CY[i] = make_float4(Pxy, k.a + k.b * U.z * U.z, Pyz, l1y);
         L3[i] = make_float2(l3x, l3y);
     };
+    const float4* Um = Um0;  // the current plane's buffer
     auto xface = [&](int iL, int iR) {
         const float4 UL = Um[iL], UR = Um[iR], CL = CX[iL], CR = CX[iR];
         const float4 FL = make_float4(chat * UL.y, chat * CL.x, chat * CL.y, chat * CL.z);
@@ -212,17 +210,17 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     long long zoff = (long long)qbeg * nxy;
     const long long pzs = (long long)(g.n[0] + 4) * (g.n[1] + 4);
     long long uoff = pad_index(g, gx, gy, qbeg - 1);  // negative before the first written plane
-    issue_plane(qbeg, zoff);
+    issue_plane(qbeg, zoff, 0);
     zoff += nxy;
     cp_async_commit();
 #pragma unroll 1
     for (int q = qbeg; q < qend; ++q, zoff += nxy, uoff += pzs) {
         const bool emit = q > qbeg + 1 && own_in_pad;
+        const int buf = (q - qbeg) & 1;
+        Um = Um0 + buf * G::N1;
         cp_async_wait_all();
-        Um[i_own] = to4(stU + 4 * t);
-        if (has_h) Um[i_h] = to4(stU + 4 * (G::NT + t));
         __syncthreads();
-        if (q + 1 < qend) issue_plane(q + 1, zoff);
+        if (q + 1 < qend) issue_plane(q + 1, zoff, buf ^ 1);
         cp_async_commit();
         // closure of the own cell (x, y and its z-direction data) and of the halo cell
         float4 nU, nP;
@@ -274,9 +272,22 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
                 // gas of the own cell of plane q - 1; zoff is (q + 1) nxy here, so that cell is at
                 // off_own + zoff - 2 nxy in the interior arrays
                 GasCell<float> gc;
-                if (own_interior && (unsigned)(q - 1) < (unsigned)g.n[2] && !needT)
-                    gc = gas_at(g, a, (long long)off_own + zoff - 2 * nxy);
-                else gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
+                if (own_interior && (unsigned)(q - 1) < (unsigned)g.n[2] && !needT) {
+                    // staged when plane q - 1 was issued; the other optional arrays are read here
+                    const float4 gv = gsl[((q - 1) % 3) * G::NT];
+                    const long long li = (long long)off_own + zoff - 2 * nxy;
+                    gc.T = 0.0;
+                    gc.rho = 0.0;
+                    gc.rho32 = gv.x;
+                    gc.v[0] = gv.y;
+                    gc.v[1] = gv.z;
+                    gc.v[2] = gv.w;
+                    gc.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, gv.x);
+                    gc.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, gv.x);
+                    gc.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
+                } else {
+                    gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
+                }
                 const float U0a[4] = {zU.x, zU.y, zU.z, zU.w};
                 const float div[4] = {dxy.x + (zfh.x - zfl.x) * idz, dxy.y + (zfh.y - zfl.y) * idz,
                                       dxy.z + (zfh.z - zfl.z) * idz, dxy.w + (zfh.w - zfl.w) * idz};
@@ -313,7 +324,8 @@ struct GeoCorr {
     // records: 4 float4 each (minus state, plus state, closure coefficients, wave speeds; face_record_ab)
     static constexpr int UK = 0, SXo = UK + 2 * N2, SYo = SXo + 4 * NSX, CXo = SYo + 4 * NSY, CYo = CXo + NCX;
     static constexpr int END4 = CYo + NCY;
-    // the own cell's FP64 state and T (5 doubles) and rho, v (4 floats), staged per thread (SoA by field)
+    // the own cell's FP64 state and T (5 doubles, SoA by field) and (rho, vx, vy, vz) (one float4), staged
+    // per thread
     static constexpr int OD = 5, OG = 4;
     __host__ __device__ static constexpr size_t bytes() { return 16 * (size_t)END4 + 8 * (size_t)OD * NT + 4 * (size_t)OG * NT; }
     __device__ static __forceinline__ int i2(int lx, int ly) { return (lx + 2) + W2 * (ly + 2); }
@@ -339,7 +351,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     float4* Cx = sm + G::CXo;
     float4* Cy = sm + G::CYo;
     double* oD = reinterpret_cast<double*>(sm + G::END4) + t;                       // oD[q NT]: E, Gx, Gy, Gz, T
-    float* oG = reinterpret_cast<float*>(reinterpret_cast<double*>(sm + G::END4) + G::OD * G::NT) + t;  // rho, v
+    float4* oG = reinterpret_cast<float4*>(reinterpret_cast<double*>(sm + G::END4) + G::OD * G::NT) + t;  // gas
     const float chat = (float)chat_d, dt = (float)dt_d;
     const float idx = (float)g.inv_dx[0], idy = (float)g.inv_dx[1], idz = (float)g.inv_dx[2];
     // LIMK >= 0: the limiter is a compile-time constant (only its code is generated); -1: g.limiter
@@ -488,10 +500,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             cp_async8(oD + 2 * G::NT, a.G[1] + li);
             cp_async8(oD + 3 * G::NT, a.G[2] + li);
             if (needT) cp_async8(oD + 4 * G::NT, a.T + li);
-            cp_async4(oG + 0 * G::NT, a.rho32 + li);
-            if (a.v32[0]) cp_async4(oG + 1 * G::NT, a.v32[0] + li);
-            if (a.v32[1]) cp_async4(oG + 2 * G::NT, a.v32[1] + li);
-            if (a.v32[2]) cp_async4(oG + 3 * G::NT, a.v32[2] + li);
+            cp_async16(oG, a.gas4 + li);
         }
         cp_async_commit();
         if (k + 1 < z1) issue_plane(next_plane, buf ^ 1, k + 1);
@@ -559,11 +568,12 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             GasCell<float> gc;
             gc.T = 0.0;
             gc.rho = 0.0;
-            const float rr = oG[0];
+            const float4 gv = *oG;
+            const float rr = gv.x;
             gc.rho32 = rr;
-            gc.v[0] = a.v32[0] ? oG[1 * G::NT] : 0.0f;
-            gc.v[1] = a.v32[1] ? oG[2 * G::NT] : 0.0f;
-            gc.v[2] = a.v32[2] ? oG[3 * G::NT] : 0.0f;
+            gc.v[0] = gv.y;
+            gc.v[1] = gv.z;
+            gc.v[2] = gv.w;
             gc.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, rr);
             gc.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, rr);
             gc.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
@@ -632,6 +642,8 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             a.Go[0][li] = Un[1];
             a.Go[1][li] = Un[2];
             a.Go[2][li] = Un[3];
+            // the FP32 mirror of U^{m+1} for the next subcycle's predictor
+            a.um32[li] = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
             if (full) a.T[li] = Tn;
         }
         cfl = cfh;
