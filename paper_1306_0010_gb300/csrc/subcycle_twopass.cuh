@@ -96,6 +96,31 @@ __device__ __forceinline__ GasCell<float> gas_at(const GridParams& g, const Grid
     return c;
 }
 
+// One coordinate p of a cell in direction d mapped into [0, n) by the face's boundary rule, as one step
+// of remap_cell: periodic wraps, reflect mirrors and flips the normal component (bit d of flip),
+// outflow clamps; Dirichlet clamps too, or, when dir_ok and no earlier direction was Dirichlet,
+// records the face (2 d + high) in dface.  The ghost layers whose values the predictor uses are at
+// most three cells deep and active directions have n >= 3, so one step lands inside, as remap_cell's
+// loop does; cells farther out (beyond the padded grid in ragged tiles, values unused) are clamped
+// into the grid so that every access stays in bounds.
+__device__ __forceinline__ int ghost1(const GridParams& g, int d, int p, bool dir_ok, int& flip, int& dface)
+{
+    const int n = g.n[d];
+    if ((unsigned)p < (unsigned)n) return p;
+    const bool low = p < 0;
+    const int bc = low ? g.bc_lo[d] : g.bc_hi[d];
+    int r = low ? 0 : n - 1;
+    if (bc == BC_DIRICHLET && dir_ok) {
+        if (dface < 0) dface = 2 * d + (low ? 0 : 1);
+    } else if (bc == BC_PERIODIC) {
+        r = low ? p + n : p - n;
+    } else if (bc == BC_REFLECT) {
+        flip ^= 1 << d;
+        r = low ? -p - 1 : 2 * n - 1 - p;
+    }
+    return min(max(r, 0), n - 1);
+}
+
 template <int TX, int TY>
 struct GeoPred {
     static constexpr int NT = TX * TY;
@@ -157,26 +182,59 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     const bool xy_inside = x0 - 1 >= 0 && x0 + TX + 1 <= g.n[0] && y0 - 1 >= 0 && y0 + TY + 1 <= g.n[1];
     const int off_own = gx + g.n[0] * gy, off_h = hx + g.n[0] * hy;  // used only when xy_inside
 
-    // U^m of one cell into the plane buffer: in-grid cells from the FP32 mirror (the FP64 state truncated
-    // toward zero), ghost cells by the boundary rule applied to the FP64 state, then truncated the same way
-    auto stage = [&](float4* d, int x, int y, int off, int q, bool fast, long long zoff) {
-        if (fast || inside(g, x, y, q)) {
-            cp_async16(d, a.um32 + (fast ? zoff + off : lin(g, x, y, q)));
-        } else {  // ghost cell: boundary rule (sign flips, Dirichlet values)
-            double U[4];
-            load_U(g, a, x, y, q, U);
-            *d = make_float4(d2f_trunc(U[0]), d2f_trunc(U[1]), d2f_trunc(U[2]), d2f_trunc(U[3]));
+    // Boundary rule of the x / y coordinates of the own and halo cells (fixed along the z march): the
+    // source cell, the sign flips of the normal G components, and a Dirichlet face (state: dir_ok) or
+    // clamping (gas: no Dirichlet values).
+    int ox_fl = 0, ox_df = -1, hx_fl = 0, hx_df = -1, gx_fl = 0, gx_df = -1;
+    int oxr = ghost1(g, 0, gx, true, ox_fl, ox_df);
+    int oyr = ghost1(g, 1, gy, true, ox_fl, ox_df);
+    const int hxr = ghost1(g, 0, hx, true, hx_fl, hx_df);
+    const int hyr = ghost1(g, 1, hy, true, hx_fl, hx_df);
+    const int gxr = ghost1(g, 0, gx, false, gx_fl, gx_df);
+    const int gyr = ghost1(g, 1, gy, false, gx_fl, gx_df);
+    (void)oxr;
+    (void)oyr;
+    // U^m of one cell into the plane buffer from the FP32 mirror (the FP64 state truncated toward zero):
+    // in-grid cells directly, ghost cells from their source cell by the boundary rule (sign flips applied
+    // once the copy has landed, by flip_ghosts) or, at a Dirichlet face, the face state truncated
+    auto stage = [&](float4* d, int xr, int yr, int fl, int df, int off, int q, bool fast, long long zoff) {
+        if (fast) {
+            cp_async16(d, a.um32 + zoff + off);
+            return;
+        }
+        const int qr = ghost1(g, 2, q, true, fl, df);
+        if (df >= 0) {
+            const double* sd = (df & 1) ? g.dir_hi[df >> 1] : g.dir_lo[df >> 1];
+            *d = make_float4(d2f_trunc(sd[0]), d2f_trunc(sd[1]), d2f_trunc(sd[2]), d2f_trunc(sd[3]));
+        } else {
+            cp_async16(d, a.um32 + lin(g, xr, yr, qr));
+        }
+    };
+    // negate the G components of a staged ghost cell that the boundary rule mirrors
+    auto flip_ghost = [&](float4* d, int fl, int df, int q) {
+        ghost1(g, 2, q, true, fl, df);
+        if (df < 0 && fl) {
+            float4 v = *d;
+            if (fl & 1) v.y = -v.y;
+            if (fl & 2) v.z = -v.z;
+            if (fl & 4) v.w = -v.w;
+            *d = v;
         }
     };
     // zoff = q * nxy, carried by the caller
     auto issue_plane = [&](int q, long long zoff, int buf) {
         const bool fast = xy_inside && (unsigned)q < (unsigned)g.n[2];
         float4* Ub = Um0 + buf * G::N1;
-        stage(Ub + i_own, gx, gy, off_own, q, fast, zoff);
-        if (has_h) stage(Ub + i_h, hx, hy, off_h, q, fast, zoff);
-        // the own cell's gas of plane q, for its half step one plane later
-        if (own_interior && (unsigned)q < (unsigned)g.n[2] && !needT)
-            cp_async16(gsl + (q % 3) * G::NT, a.gas4 + zoff + off_own);
+        stage(Ub + i_own, oxr, oyr, ox_fl, ox_df, off_own, q, fast, zoff);
+        if (has_h) stage(Ub + i_h, hxr, hyr, hx_fl, hx_df, off_h, q, fast, zoff);
+        // the own cell's gas of plane q (the boundary rule's source cell for ghost cells), for its half
+        // step one plane later
+        if (own_in_pad && !needT) {
+            int fl = gx_fl, df = -1;
+            const int qr = ghost1(g, 2, q, false, fl, df);
+            cp_async16(gsl + ((q + 3) % 3) * G::NT,
+                       a.gas4 + ((own_interior && (unsigned)q < (unsigned)g.n[2]) ? zoff + off_own : lin(g, gxr, gyr, qr)));
+        }
     };
     auto closure_xy = [&](int i, const float4& U, const ClosureScalars<float>& k) {
         float l1x, l3x, l1y, l3y;
@@ -219,6 +277,10 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
         const int buf = (q - qbeg) & 1;
         Um = Um0 + buf * G::N1;
         cp_async_wait_all();
+        if (!(xy_inside && (unsigned)q < (unsigned)g.n[2])) {
+            flip_ghost(Um0 + buf * G::N1 + i_own, ox_fl, ox_df, q);
+            if (has_h) flip_ghost(Um0 + buf * G::N1 + i_h, hx_fl, hx_df, q);
+        }
         __syncthreads();
         if (q + 1 < qend) issue_plane(q + 1, zoff, buf ^ 1);
         cp_async_commit();
@@ -272,16 +334,21 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
                 // gas of the own cell of plane q - 1; zoff is (q + 1) nxy here, so that cell is at
                 // off_own + zoff - 2 nxy in the interior arrays
                 GasCell<float> gc;
-                if (own_interior && (unsigned)(q - 1) < (unsigned)g.n[2] && !needT) {
-                    // staged when plane q - 1 was issued; the other optional arrays are read here
-                    const float4 gv = gsl[((q - 1) % 3) * G::NT];
-                    const long long li = (long long)off_own + zoff - 2 * nxy;
+                const bool opt = a.kP32 || a.kF32 || a.j32;  // optional per-cell opacity / emissivity arrays
+                const bool inner = own_interior && (unsigned)(q - 1) < (unsigned)g.n[2];
+                if (!needT && (!opt || inner)) {
+                    // staged when plane q - 1 was issued (the boundary rule's source cell for ghost cells,
+                    // whose mirrored velocity components are negated here)
+                    const float4 gv = gsl[((q - 1 + 3) % 3) * G::NT];
+                    int fl = gx_fl, df = -1;
+                    ghost1(g, 2, q - 1, false, fl, df);
                     gc.T = 0.0;
                     gc.rho = 0.0;
                     gc.rho32 = gv.x;
-                    gc.v[0] = gv.y;
-                    gc.v[1] = gv.z;
-                    gc.v[2] = gv.w;
+                    gc.v[0] = (fl & 1) ? -gv.y : gv.y;
+                    gc.v[1] = (fl & 2) ? -gv.z : gv.z;
+                    gc.v[2] = (fl & 4) ? -gv.w : gv.w;
+                    const long long li = (long long)off_own + zoff - 2 * nxy;  // interior cells only (opt)
                     gc.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, gv.x);
                     gc.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, gv.x);
                     gc.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
