@@ -513,7 +513,11 @@ def main():
     if os.path.exists(traffic_path):
         trj = json.load(open(traffic_path))
         tr = trj.get(roofline["kernel"])
-        if (tr and tr.get("N") == args.N and tr.get("launch") == launch_key(launch)
+        # the corrector's DRAM traffic does not depend on the z chunk (its only per-chunk extra is four
+        # planes of one column): match variant, tile and staging
+        def same_kernel(a, b):
+            return a.split(":")[:2] + a.split(":")[3:] == b.split(":")[:2] + b.split(":")[3:]
+        if (tr and tr.get("N") == args.N and same_kernel(tr.get("launch", ""), launch_key(launch))
                 and trj.get("source_sha256") == kernel_source_hash()):
             roofline["traffic"] = tr["bytes_per_launch"]
     # the whole subcycle against the method's own bytes per cell-update (U^m, gas, T in; U^{m+1}, T out)

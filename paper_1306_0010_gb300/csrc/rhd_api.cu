@@ -558,18 +558,22 @@ const char* const kKernelNames[K_COUNT] = {"subcycle_fused_fp64", "subcycle_fuse
                                            "twopass_corrector_split", "ensemble_fp64", "ensemble_split",
                                            "ensemble_predictor_split", "ensemble_corrector_split"};
 
-// Algorithmic bytes per interior cell of one launch of kernel k: every input read once, every output
-// written once (U = 4 FP64 moments, U^{m+1/2} = 4 FP32, gas arrays in the kernel's precision).
+// Algorithmic bytes per interior cell of one launch of kernel k: every array the kernel reads, read
+// once, and every array it writes, written once.  Fused kernels: U^m and U^{m+1} (4 FP64 each), the
+// gas arrays in the kernel's precision, T.  Two-pass kernels: the predictor reads the FP32 state
+// mirror (16 B) and the interleaved FP32 gas (16 B) and writes U^{m+1/2} (16 B); the corrector reads
+// U^{m+1/2}, U^m (FP64), the gas and T, and writes U^{m+1} (FP64), T and the new mirror.
 double alg_bytes_per_cell(const GridState& gs, int k)
 {
     const bool split = gs.desc.precision == RHD_SPLIT;
     const double w = split ? 4.0 : 8.0;
-    const double gas = w * (1 + (gs.has_v ? 3 : 0) + (gs.has_kP ? 1 : 0) + (gs.has_kF ? 1 : 0) + (gs.has_j ? 1 : 0));
+    const double opt = w * ((gs.has_kP ? 1 : 0) + (gs.has_kF ? 1 : 0) + (gs.has_j ? 1 : 0));
+    const double gas = w * (1 + (gs.has_v ? 3 : 0)) + opt;
     const int ex = gs.desc.exchange;
     const double Tr = (ex == RHD_EX_FULL || ex == RHD_EX_FROZEN_T) ? 8.0 : 0.0, Tw = ex == RHD_EX_FULL ? 8.0 : 0.0;
     switch (k) {
-    case K_PREDICTOR: return 32.0 + gas + (ex == RHD_EX_FROZEN_T ? 8.0 : 0.0) + 16.0;
-    case K_CORRECTOR: return 16.0 + 32.0 + gas + Tr + 32.0 + Tw;
+    case K_PREDICTOR: return 16.0 + 16.0 + opt + (ex == RHD_EX_FROZEN_T ? 8.0 : 0.0) + 16.0;
+    case K_CORRECTOR: return 16.0 + 32.0 + 16.0 + opt + Tr + 32.0 + Tw + 16.0;
     default: return 32.0 + gas + Tr + 32.0 + Tw;
     }
 }

@@ -216,9 +216,10 @@ def test_kernel_timer_counts_and_bytes(rhd):
         assert np.array_equal(out[k], ref[k]), k
     ncell = 40 * 24 * 36
     assert set(kt) == {"twopass_predictor_split", "twopass_corrector_split"}
-    # split gas arrays: rho32 + v32 (beta tau) = 16 B/cell; FULL reads and writes T
-    assert kt["twopass_predictor_split"]["alg_bytes_per_launch"] == ncell * (32 + 16 + 16)
-    assert kt["twopass_corrector_split"]["alg_bytes_per_launch"] == ncell * (16 + 32 + 16 + 8 + 32 + 8)
+    # predictor: FP32 state mirror 16 + interleaved FP32 gas 16 in, U^{m+1/2} 16 out; corrector:
+    # U^{m+1/2} 16 + U^m 32 + gas 16 + T 8 in, U^{m+1} 32 + T 8 + mirror 16 out (FULL exchange)
+    assert kt["twopass_predictor_split"]["alg_bytes_per_launch"] == ncell * (16 + 16 + 16)
+    assert kt["twopass_corrector_split"]["alg_bytes_per_launch"] == ncell * (16 + 32 + 16 + 8 + 32 + 8 + 16)
     for v in kt.values():
         assert v["launches"] == 3 and v["total_ms"] > 0
     g.radiation_subcycle(2, case["chat"], case["dt"])
