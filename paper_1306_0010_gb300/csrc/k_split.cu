@@ -192,7 +192,11 @@ cudaError_t launch_ensemble_predictor(const EnsembleParams& p, int n_ctas, cudaS
 
 cudaError_t launch_ensemble_corrector(const EnsembleParams& p, int n_ctas, cudaStream_t s)
 {
-    auto k = corrector_ens_kernel<32, 8>;
+    // all grids of an ensemble share the limiter: one instantiation per limiter
+    const int lim = p.n_grids > 0 ? p.limiter : LIM_MINMOD;
+    auto k = lim == LIM_MC     ? corrector_ens_kernel<32, 8, LIM_MC>
+             : lim == LIM_NONE ? corrector_ens_kernel<32, 8, LIM_NONE>
+                               : corrector_ens_kernel<32, 8, LIM_MINMOD>;
     const size_t smem = GeoCorr<32, 8>::bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -201,7 +205,10 @@ cudaError_t launch_ensemble_corrector(const EnsembleParams& p, int n_ctas, cudaS
 }
 
 int ensemble_ctas_per_sm_predictor() { return occupancy_of(predictor_ens_kernel<32, 8>, GeoPred<32, 8>::bytes(), 256); }
-int ensemble_ctas_per_sm_corrector() { return occupancy_of(corrector_ens_kernel<32, 8>, GeoCorr<32, 8>::bytes(), 256); }
+int ensemble_ctas_per_sm_corrector()
+{
+    return occupancy_of(corrector_ens_kernel<32, 8, LIM_MINMOD>, GeoCorr<32, 8>::bytes(), 256);
+}
 
 int ensemble_ctas_per_sm_split() { return ens_occupancy<float, 32, 8, true>(); }
 

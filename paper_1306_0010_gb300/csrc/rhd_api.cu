@@ -758,6 +758,7 @@ rhd_status ens_launch(rhd_ctx* ctx, double chat, int src)
     ep.n_pitems = ctx->n_pitems;
     ep.chat = chat;
     ep.z_chunk = ctx->grids[0].z_chunk;
+    ep.limiter = ctx->grids[0].desc.limiter;
     ep.stats = ctx->dstats;
     if (!twopass) {
         double bytes = 0.0;

@@ -97,6 +97,7 @@ struct EnsembleParams {
     long long n_pitems;         // predictor work items (two-pass)
     double chat;
     int z_chunk;
+    int limiter;                // shared by all grids (the two-pass corrector is instantiated per limiter)
     unsigned long long* counter;  // work-queue head, reset before each launch
     DevStats* stats;
 };

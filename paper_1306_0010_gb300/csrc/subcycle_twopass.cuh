@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_ens_ker
     add_counter(&P.stats->n_fix, cnt.fix);
 }
 
-template <int TX, int TY>
+template <int TX, int TY, int LIMK>
 __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_ens_kernel(const __grid_constant__ EnsembleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_ens_ker
         const int txy = (int)(local % nxy), tz = (int)(local / nxy);
         const int x0 = (txy % eg.tiles_x) * TX, y0 = (txy / eg.tiles_x) * TY;
         const int z0 = tz * P.z_chunk, z1 = min(z0 + P.z_chunk, eg.g.n[2]);
-        corrector_tile<TX, TY>(eg.g, eg.a, eg.uhalf, P.chat, eg.dt, x0, y0, z0, z1,
+        corrector_tile<TX, TY, false, LIMK>(eg.g, eg.a, eg.uhalf, P.chat, eg.dt, x0, y0, z0, z1,
                                reinterpret_cast<float4*>(smem_raw), cnt);
         __syncthreads();
     }
