@@ -57,6 +57,13 @@ typedef enum {
     RHD_ERR_UNSUPPORTED = 8 /* the operation is not part of this library */
 } rhd_status;
 
+/* Environment (read by the library, none required):
+ *   RHD_LOG=1                   print every error status and its message to stderr; 2: also the launch
+ *                               configurations the autotuner chooses
+ *   RHD_DEVICE_MEMORY_LIMIT=B   cap (bytes) on the cumulative device allocations of each context created
+ *                               afterwards; allocations beyond it return RHD_ERR_OOM (a test hook for the
+ *                               out-of-memory paths)
+ * Every API call is also marked as an NVTX range of the same name for Nsight tools. */
 typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_OUTFLOW = 1, RHD_BC_REFLECT = 2, RHD_BC_DIRICHLET = 3 } rhd_bc;
 
 /* Energy-exchange treatment (Section 3.4):
@@ -157,6 +164,16 @@ rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas);
 
 /* Copy the current moments out (synchronises the stream).  Errors: RHD_ERR_ARG, RHD_ERR_STATE, RHD_ERR_CUDA. */
 rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, double* Fz, int on_device);
+
+/* The radiation state in the variables the solver advances, E and G = F / c (the radiation rows of
+ * Eq. algorithm:variables with the momentum rows divided by c), copied without arithmetic: a state
+ * saved with rhd_get_conserved and given back with rhd_set_conserved continues bit for bit (the
+ * F = c G conversion of rhd_get/set_moments rounds).  Same layout, ownership and synchronisation as
+ * rhd_set_moments / rhd_get_moments.  Errors: RHD_ERR_ARG, RHD_ERR_STATE (get before any set, or an
+ * ensemble context), RHD_ERR_CUDA. */
+rhd_status rhd_set_conserved(rhd_ctx* ctx, const double* E, const double* Gx, const double* Gy,
+                             const double* Gz, int on_device);
+rhd_status rhd_get_conserved(rhd_ctx* ctx, double* E, double* Gx, double* Gy, double* Gz, int on_device);
 
 /* Copy the current gas temperature out (changes only in FULL mode).  Synchronises the stream. */
 rhd_status rhd_get_gas_state(rhd_ctx* ctx, double* T, int on_device);

@@ -14,6 +14,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>  // header-only: ranges are recorded only when a profiler is attached
+
 #include "rhd.h"
 #include "rhd_internal.h"
 
@@ -22,6 +24,22 @@ using namespace rhd;
 namespace {
 
 thread_local std::string g_init_error;
+
+// RHD_LOG: 0 (default) silent; 1 error messages to stderr; 2 also the launch configurations chosen
+int log_level()
+{
+    static const int lv = [] {
+        const char* v = std::getenv("RHD_LOG");
+        return v ? std::atoi(v) : 0;
+    }();
+    return lv;
+}
+
+// NVTX range around one API call (visible in Nsight tools; a no-op otherwise)
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+};
 
 struct GraphEntry {
     int n_sub;
@@ -83,6 +101,9 @@ struct rhd_ctx {
     std::vector<GraphEntry> graphs;
     unsigned long long stamp = 0;
     std::string err;
+    // RHD_DEVICE_MEMORY_LIMIT (bytes, read at creation): cap on the context's cumulative device
+    // allocations, a test hook that forces RHD_ERR_OOM without exhausting the device
+    size_t mem_limit = 0, mem_used = 0;
     // kernel timing: events recorded around each kernel launch (plain launches while enabled)
     bool ktiming = false;
     std::vector<cudaEvent_t> kev;          // event pool, reused after each read
@@ -102,6 +123,7 @@ rhd_status fail(rhd_ctx* ctx, rhd_status st, const std::string& msg)
 {
     if (ctx) ctx->err = msg;
     else g_init_error = msg;
+    if (log_level() >= 1) std::fprintf(stderr, "rhd: status %d: %s\n", (int)st, msg.c_str());
     return st;
 }
 
@@ -245,6 +267,11 @@ void fill_params(GridState& gs)
 
 rhd_status dalloc(rhd_ctx* ctx, void** p, size_t bytes)
 {
+    if (ctx && ctx->mem_limit && ctx->mem_used + bytes > ctx->mem_limit) {
+        *p = nullptr;
+        return fail(ctx, RHD_ERR_OOM, "RHD_DEVICE_MEMORY_LIMIT reached (" + std::to_string(ctx->mem_used + bytes) +
+                                          " bytes requested in total)");
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -252,6 +279,7 @@ rhd_status dalloc(rhd_ctx* ctx, void** p, size_t bytes)
         return fail(ctx, e == cudaErrorMemoryAllocation ? RHD_ERR_OOM : RHD_ERR_CUDA,
                     std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
+    if (ctx) ctx->mem_used += bytes;
     return RHD_OK;
 }
 
@@ -340,6 +368,7 @@ rhd_status alloc_grid(rhd_ctx* ctx, GridState& gs)
 
 rhd_status common_init(rhd_ctx* ctx)
 {
+    if (const char* lim = std::getenv("RHD_DEVICE_MEMORY_LIMIT")) ctx->mem_limit = (size_t)std::strtoull(lim, nullptr, 10);
     RHD_CUDA(ctx, cudaGetDevice(&ctx->device));
     RHD_CUDA(ctx, cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
     if (ctx->user_stream == nullptr || ctx->user_stream == cudaStreamLegacy || ctx->user_stream == cudaStreamPerThread) {
@@ -438,17 +467,20 @@ rhd_status set_gas(rhd_ctx* ctx, GridState& gs, const double* rho, const double*
     return leave(ctx);
 }
 
+// conserved = false: (E, F) with G = F / c formed on the device; true: (E, G) copied as they are
 rhd_status set_moments(rhd_ctx* ctx, GridState& gs, const double* E, const double* Fx, const double* Fy,
-                       const double* Fz, int on_device)
+                       const double* Fz, int on_device, bool conserved = false)
 {
-    if (!E || !Fx || !Fy || !Fz) return fail(ctx, RHD_ERR_ARG, "E, Fx, Fy, Fz are required");
+    if (!E || !Fx || !Fy || !Fz) return fail(ctx, RHD_ERR_ARG, "E and the three flux components are required");
     rhd_status st = enter(ctx);
     if (st) return st;
     double** U = gs.U[ctx->cur];
     if ((st = put(ctx, U[0], E, gs.ncell, on_device))) return st;
     const double* F[3] = {Fx, Fy, Fz};
     for (int d = 0; d < 3; ++d) {
-        if (on_device) {
+        if (conserved) {
+            if ((st = put(ctx, U[1 + d], F[d], gs.ncell, on_device))) return st;
+        } else if (on_device) {
             RHD_CUDA(ctx, launch_scale_copy(U[1 + d], F[d], gs.desc.c, gs.ncell, ctx->stream));
         } else {
             if ((st = put(ctx, U[1 + d], F[d], gs.ncell, 0))) return st;
@@ -460,9 +492,11 @@ rhd_status set_moments(rhd_ctx* ctx, GridState& gs, const double* E, const doubl
     return leave(ctx);
 }
 
-rhd_status get_moments(rhd_ctx* ctx, GridState& gs, double* E, double* Fx, double* Fy, double* Fz, int on_device)
+// conserved = false: (E, F = c G); true: (E, G) as the solver holds them
+rhd_status get_moments(rhd_ctx* ctx, GridState& gs, double* E, double* Fx, double* Fy, double* Fz, int on_device,
+                       bool conserved = false)
 {
-    if (!E || !Fx || !Fy || !Fz) return fail(ctx, RHD_ERR_ARG, "E, Fx, Fy, Fz are required");
+    if (!E || !Fx || !Fy || !Fz) return fail(ctx, RHD_ERR_ARG, "E and the three flux components are required");
     if (!gs.has_moments) return fail(ctx, RHD_ERR_STATE, "moments were never set");
     rhd_status st = enter(ctx);
     if (st) return st;
@@ -470,7 +504,11 @@ rhd_status get_moments(rhd_ctx* ctx, GridState& gs, double* E, double* Fx, doubl
     double** W = gs.U[1 - ctx->cur];  // scratch: the other half of the ping-pong pair
     size_t bytes = sizeof(double) * (size_t)gs.ncell;
     double* F[3] = {Fx, Fy, Fz};
-    if (on_device) {
+    if (conserved) {
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        for (int q = 0; q < 4; ++q)
+            RHD_CUDA(ctx, cudaMemcpyAsync(q ? F[q - 1] : E, U[q], bytes, kind, ctx->stream));
+    } else if (on_device) {
         RHD_CUDA(ctx, cudaMemcpyAsync(E, U[0], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         for (int d = 0; d < 3; ++d) RHD_CUDA(ctx, launch_scale_copy(F[d], U[1 + d], -gs.desc.c, gs.ncell, ctx->stream));
     } else {
@@ -1005,6 +1043,12 @@ rhd_status grid_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_lau
     gs.tuned = true;
     gs.tuned_ms = best >= 0 ? cand[best].ms_per_subcycle : -1.0;
     report(cand, current_config(gs), table, capacity, n_entries, chosen);
+    if (log_level() >= 2) {
+        const rhd_launch_config c = current_config(gs);
+        std::fprintf(stderr, "rhd: tuned %dx%dx%d: variant %d tile %dx%d z %d staging %d, %.3f ms per subcycle\n",
+                     gs.desc.n[0], gs.desc.n[1], gs.desc.n[2], c.variant, c.tile_x, c.tile_y, c.z_chunk, c.staging,
+                     c.ms_per_subcycle);
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         g_tune_cache[tune_key(ctx)] = current_config(gs);
@@ -1145,6 +1189,7 @@ const char* rhd_last_error(const rhd_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 rhd_status rhd_init_grid(rhd_ctx** out, const rhd_grid_desc* d)
 {
+    ApiRange range_("rhd_init_grid");
     if (!out) return fail(nullptr, RHD_ERR_ARG, "out is NULL");
     rhd_status st = validate_desc(nullptr, d);
     if (st) return st;
@@ -1186,6 +1231,7 @@ rhd_status rhd_destroy(rhd_ctx* ctx)
 rhd_status rhd_set_gas_state(rhd_ctx* ctx, const double* rho, const double* T, const double* vx, const double* vy,
                              const double* vz, const double* kP, const double* kF, const double* j, int on_device)
 {
+    ApiRange range_("rhd_set_gas_state");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_set_gas_state on an ensemble");
     return set_gas(ctx, ctx->grids[0], rho, T, vx, vy, vz, kP, kF, j, on_device);
@@ -1194,9 +1240,27 @@ rhd_status rhd_set_gas_state(rhd_ctx* ctx, const double* rho, const double* T, c
 rhd_status rhd_set_moments(rhd_ctx* ctx, const double* E, const double* Fx, const double* Fy, const double* Fz,
                            int on_device)
 {
+    ApiRange range_("rhd_set_moments");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_set_moments on an ensemble");
     return set_moments(ctx, ctx->grids[0], E, Fx, Fy, Fz, on_device);
+}
+
+rhd_status rhd_set_conserved(rhd_ctx* ctx, const double* E, const double* Gx, const double* Gy, const double* Gz,
+                             int on_device)
+{
+    ApiRange range_("rhd_set_conserved");
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not available on an ensemble context");
+    return set_moments(ctx, ctx->grids[0], E, Gx, Gy, Gz, on_device, true);
+}
+
+rhd_status rhd_get_conserved(rhd_ctx* ctx, double* E, double* Gx, double* Gy, double* Gz, int on_device)
+{
+    ApiRange range_("rhd_get_conserved");
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not available on an ensemble context");
+    return get_moments(ctx, ctx->grids[0], E, Gx, Gy, Gz, on_device, true);
 }
 
 rhd_status rhd_set_dirichlet(rhd_ctx* ctx, int face, const double state[4])
@@ -1216,6 +1280,7 @@ rhd_status rhd_set_dirichlet(rhd_ctx* ctx, int face, const double state[4])
 
 rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double dt)
 {
+    ApiRange range_("rhd_radiation_subcycle");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_subcycle on an ensemble");
     if (n_sub < 0) return fail(ctx, RHD_ERR_ARG, "n_sub must be >= 0");
@@ -1243,6 +1308,7 @@ rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas)
 
 rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, double* Fz, int on_device)
 {
+    ApiRange range_("rhd_get_moments");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_get_moments on an ensemble");
     return get_moments(ctx, ctx->grids[0], E, Fx, Fy, Fz, on_device);
@@ -1250,6 +1316,7 @@ rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, doub
 
 rhd_status rhd_get_gas_state(rhd_ctx* ctx, double* T, int on_device)
 {
+    ApiRange range_("rhd_get_gas_state");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_get_gas_state on an ensemble");
     return get_T(ctx, ctx->grids[0], T, on_device);
@@ -1267,6 +1334,7 @@ rhd_status rhd_reset_stats(rhd_ctx* ctx)
 
 rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
 {
+    ApiRange range_("rhd_get_stats");
     if (!ctx || !out) return fail(ctx, RHD_ERR_ARG, "ctx and out are required");
     std::memset(out, 0, sizeof(*out));
     rhd_status st = enter(ctx);
@@ -1302,7 +1370,10 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
     for (int d = 0; d < 3; ++d) out->sum_F[d] = sums[1 + d];
     out->max_f = sums[4];
     if (out->wait_timeouts) return fail(ctx, RHD_ERR_TIMEOUT, "a device-side wait ran out; some tiles were not updated");
-    return out->n_nonfinite ? RHD_ERR_NONFINITE : RHD_OK;
+    if (out->n_nonfinite)
+        return fail(ctx, RHD_ERR_NONFINITE,
+                    std::to_string(out->n_nonfinite) + " non-finite values were produced since the last reset");
+    return RHD_OK;
 }
 
 rhd_status rhd_synchronize(rhd_ctx* ctx, int timeout_ms)
@@ -1326,6 +1397,7 @@ rhd_status rhd_synchronize(rhd_ctx* ctx, int timeout_ms)
 // ---------------------------------------------------------------------------------------------
 rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* descs)
 {
+    ApiRange range_("rhd_ensemble_create");
     if (!out || !descs || n_grids < 1) return fail(nullptr, RHD_ERR_ARG, "out, descs and n_grids >= 1 are required");
     for (int i = 0; i < n_grids; ++i) {
         rhd_status st = validate_desc(nullptr, descs + i);
@@ -1430,6 +1502,7 @@ rhd_status rhd_ensemble_get_gas_state(rhd_ctx* ctx, int grid, double* T, int on_
 
 rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const double* dt_per_grid)
 {
+    ApiRange range_("rhd_ensemble_subcycle");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (!ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not an ensemble context");
     if (n_sub < 0 || !dt_per_grid) return fail(ctx, RHD_ERR_ARG, "n_sub >= 0 and dt_per_grid are required");
@@ -1464,6 +1537,7 @@ rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const dou
 rhd_status rhd_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_launch_config* table, int capacity,
                         int* n_entries, rhd_launch_config* chosen)
 {
+    ApiRange range_("rhd_autotune");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_autotune on an ensemble");
     if (reps < 1 || capacity < 0) return fail(ctx, RHD_ERR_ARG, "reps >= 1 and capacity >= 0 are required");
@@ -1477,6 +1551,7 @@ rhd_status rhd_autotune(rhd_ctx* ctx, double chat, double dt, int reps, rhd_laun
 rhd_status rhd_ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_grid, int reps,
                                  rhd_launch_config* table, int capacity, int* n_entries, rhd_launch_config* chosen)
 {
+    ApiRange range_("rhd_ensemble_autotune");
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (!ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not an ensemble context");
     if (reps < 1 || capacity < 0 || !dt_per_grid)

@@ -135,10 +135,21 @@ template <typename R>
 __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R gz, R chat, int p1)
 {
     ClosureScalars<R> k;
-    k.invE = rcp(E);
+    R invE = rcp(E);
     R g2 = gx * gx + gy * gy + gz * gz;
-    R f2 = g2 * (k.invE * k.invE);
-    f2 = rmin(f2, R(1));
+    R f2 = g2 * (invE * invE);
+    R invEb = invE;
+    if (f2 > R(1)) {
+        // |G| > E (a state outside the realizable set, e.g. an input U^m): the closure is that of
+        // f = 1 along n = G/|G|, i.e. of the state (E, G/f), so mu f = gd/(E f) in the wave speeds and
+        // b G G^T = E n n^T with b = 1/(E f^2).  Face states of the corrector have passed the
+        // realizability test and never take this branch beyond its rounding allowance.
+        const R q = rcp(rsq(f2));
+        invE = invE * q;
+        invEb = invE * q;
+        f2 = R(1);
+    }
+    k.invE = invE;
     k.s = rsq(R(4) - R(3) * f2);
     k.inv2ps = rcp(R(2) + k.s);
     k.cs = chat * rcp(k.s);
@@ -147,7 +158,7 @@ __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R 
         k.b = R(0);
     } else {
         k.a = (k.s - R(1)) * E * R(1.0 / 3.0);
-        k.b = R(3) * k.inv2ps * k.invE;
+        k.b = R(3) * k.inv2ps * invEb;
     }
     return k;
 }

@@ -10,6 +10,7 @@ of a context raises.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -143,6 +144,8 @@ _SIGS = {
     "rhd_radiation_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "rhd_gas_step": (ctypes.c_int, [_P, ctypes.c_double]),
     "rhd_get_moments": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
+    "rhd_set_conserved": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
+    "rhd_get_conserved": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
     "rhd_get_gas_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "rhd_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),
     "rhd_reset_stats": (ctypes.c_int, [_P]),
@@ -280,7 +283,14 @@ class Grid:
         except Exception:
             pass
 
+    _GAS_KEYS = ("rho", "T", "vx", "vy", "vz", "kP", "kF", "j")
+
     def set_gas_state(self, rho, T, vx=None, vy=None, vz=None, kP=None, kF=None, j=None):
+        # references to the frozen gas inputs, for checkpoint() (T evolves and is read back from the device)
+        self._gas_in = dict(zip(self._GAS_KEYS, (rho, T, vx, vy, vz, kP, kF, j)))
+        self._set_gas_state(rho, T, vx, vy, vz, kP, kF, j)
+
+    def _set_gas_state(self, rho, T, vx=None, vy=None, vz=None, kP=None, kF=None, j=None):
         ps = [_ptr(a, self.ncell) for a in (rho, T, vx, vy, vz, kP, kF, j)]
         od = _same_residency(ps)
         _check(self._ctx, lib().rhd_set_gas_state(self._ctx, *[p for p, _ in ps], od))
@@ -307,6 +317,21 @@ class Grid:
         od = _same_residency(ps)
         _check(self._ctx, lib().rhd_get_moments(self._ctx, *[p for p, _ in ps], od))
         return {"E": E, "Fx": Fx, "Fy": Fy, "Fz": Fz}
+
+    def set_conserved(self, E, Gx, Gy, Gz):
+        """Set the solver's own variables E and G = F/c (no conversion; see get_conserved)."""
+        ps = [_ptr(a, self.ncell) for a in (E, Gx, Gy, Gz)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_set_conserved(self._ctx, *[p for p, _ in ps], od))
+
+    def get_conserved(self, E=None, Gx=None, Gy=None, Gz=None):
+        """The solver's own variables E and G = F/c, copied without arithmetic (bitwise restartable)."""
+        if E is None:
+            E, Gx, Gy, Gz = (np.empty(self.shape) for _ in range(4))
+        ps = [_ptr(a, self.ncell, writable=True) for a in (E, Gx, Gy, Gz)]
+        od = _same_residency(ps)
+        _check(self._ctx, lib().rhd_get_conserved(self._ctx, *[p for p, _ in ps], od))
+        return {"E": E, "Gx": Gx, "Gy": Gy, "Gz": Gz}
 
     def get_gas_state(self, T=None):
         if T is None:
@@ -352,17 +377,47 @@ class Grid:
         c = LaunchConfig.from_dict(cfg)
         _check(self._ctx, lib().rhd_set_launch_config(self._ctx, ctypes.byref(c)))
 
+    def checkpoint(self, path):
+        """Save the evolving state (E, G = F/c, T), the descriptor, the launch configuration and the frozen
+        gas inputs last given to set_gas_state (as they are at this call) to an .npz file;
+        Grid.restore(path) continues bit for bit."""
+        out = self.get_conserved()
+        out["T_state"] = self.get_gas_state()
+        for k, v in getattr(self, "_gas_in", {}).items():
+            if v is not None and k != "T":
+                out["gas_" + k] = v.detach().cpu().numpy() if _is_torch(v) else np.asarray(v)
+        cfg = self.launch_config()
+        np.savez(path, desc=np.array(json.dumps(self.desc, default=float)),
+                 launch=np.array(json.dumps(dict(cfg, tile=list(cfg["tile"])))), **out)
+
+    @classmethod
+    def restore(cls, path, stream=None):
+        """A new Grid in the state a checkpoint() saved (same launch configuration)."""
+        z = np.load(path)
+        desc = json.loads(str(z["desc"]))
+        g = cls(desc, stream=stream)
+        cfg = json.loads(str(z["launch"]))
+        g.set_launch_config(dict(cfg, tile=tuple(cfg["tile"])))
+        gas = {k: (np.ascontiguousarray(z["gas_" + k]) if "gas_" + k in z else None) for k in cls._GAS_KEYS}
+        gas["T"] = np.ascontiguousarray(z["T_state"])
+        g.set_gas_state(*(gas[k] for k in cls._GAS_KEYS))
+        g.set_conserved(*(np.ascontiguousarray(z[k]) for k in ("E", "Gx", "Gy", "Gz")))
+        g._set_dirichlet_from_desc(desc)
+        return g
+
+    def _set_dirichlet_from_desc(self, d):
+        for face in range(6):
+            dd, side = face // 2, face % 2
+            if (d["bc_hi"] if side else d["bc_lo"])[dd] == "dirichlet":
+                self.set_dirichlet(face, (d["dirichlet_hi"] if side else d["dirichlet_lo"])[dd])
+
     def load_case(self, case):
         """Set the gas state and moments of a case dict (see workloads.py)."""
         f = case["fields"]
         self.set_gas_state(*(None if f.get(k) is None else np.ascontiguousarray(f[k], dtype=np.float64)
                              for k in ("rho", "T", "vx", "vy", "vz", "kP", "kF", "j")))
         self.set_moments(*(np.ascontiguousarray(f[k], dtype=np.float64) for k in ("E", "Fx", "Fy", "Fz")))
-        d = case["desc"]
-        for face in range(6):
-            dd, side = face // 2, face % 2
-            if (d["bc_hi"] if side else d["bc_lo"])[dd] == "dirichlet":
-                self.set_dirichlet(face, (d["dirichlet_hi"] if side else d["dirichlet_lo"])[dd])
+        self._set_dirichlet_from_desc(case["desc"])
 
 
 class Ensemble:

@@ -1,0 +1,123 @@
+"""GPU: failures are reported as statuses and leave the context usable (no device fault, trap or hang
+is ever provoked; every failure here comes from the inputs or a host-side limit)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1306_0010_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_TOL = 2e-5
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rhd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1306_0010_gb300 import build, rhd as binding
+
+    build.build()
+    binding.lib()
+    return binding
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_nonfinite_input_reported_then_recovers(rhd, precision):
+    case = wl.parity_case("nan", (20, 12, 10), bc="periodic", exchange="full", n_sub=2, seed=41, precision=precision)
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    f = case["fields"]
+    E = f["E"].copy()
+    E[5, 6, 7] = np.nan
+    g.set_moments(E, f["Fx"], f["Fy"], f["Fz"])
+    g.radiation_subcycle(2, case["chat"], case["dt"])
+    with pytest.raises(rhd.RhdError) as ei:
+        g.get_stats()
+    assert ei.value.status == rhd.ERR_NONFINITE
+    assert g.get_stats(allow_nonfinite=True)["n_nonfinite"] > 0
+    # the context is still usable: a fresh finite state (moments and gas, whose T the exchange
+    # with the NaN cell may have spoiled) advances cleanly
+    g.reset_stats()
+    g.load_case(case)
+    g.radiation_subcycle(2, case["chat"], case["dt"])
+    st = g.get_stats()
+    assert st["n_nonfinite"] == 0 and np.isfinite(st["sum_E"])
+    g.close()
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_superluminal_input_is_rescaled(rhd, precision):
+    """|F| > cE on input is outside the realizable set: the closure clamps f and the update rescales
+    the flux (Section 2.2); the result follows the oracle, which does the same."""
+    case = wl.parity_case("flux", (16, 12, 10), bc="periodic", exchange="equilibrium", n_sub=1, seed=42,
+                          precision=precision)
+    f = case["fields"]
+    f["Fx"] = f["Fx"].copy()
+    f["Fx"][3, 4, 5] = 5.0 * case["desc"]["c"] * f["E"][3, 4, 5]  # |F| = 5 cE
+    ref, st_ref = orc.subcycles(case)
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    g.radiation_subcycle(1, case["chat"], case["dt"])
+    st = g.get_stats()
+    out = g.get_moments()
+    g.close()
+    assert st["n_realizability_fix"] > 0 and st_ref["n_realizability_fix"] > 0 and st["n_nonfinite"] == 0
+    tol = SPLIT_TOL if precision == "split" else FP64_TOL
+    sE = float(np.max(np.abs(ref["E"])))
+    assert float(np.max(np.abs(out["E"] - ref["E"]))) <= tol * sE
+    for k in ("Fx", "Fy", "Fz"):
+        assert float(np.max(np.abs(out[k] - ref[k]))) <= tol * case["desc"]["c"] * sE, k
+    if precision == "fp64":
+        assert st["n_realizability_fix"] == st_ref["n_realizability_fix"]
+    F = np.sqrt(out["Fx"] ** 2 + out["Fy"] ** 2 + out["Fz"] ** 2)
+    assert np.all(F <= case["desc"]["c"] * out["E"] * (1 + 1e-6))
+
+
+def test_step_arguments_rejected_context_usable(rhd):
+    case = wl.parity_case("args", (16, 8, 8), n_sub=1, seed=43, precision="split")
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    c, dt = case["chat"], case["dt"]
+    dx = min(case["desc"]["dx"])
+    for bad, status in (((c, 2 * case["desc"]["cfl"] * dx / c), rhd.ERR_CFL), ((0.0, dt), rhd.ERR_ARG),
+                        ((-1.0, dt), rhd.ERR_ARG), ((2.0 * case["desc"]["c"], dt), rhd.ERR_CFL),
+                        ((c, float("nan")), rhd.ERR_ARG)):
+        with pytest.raises(rhd.RhdError) as ei:
+            g.radiation_subcycle(1, *bad)
+        assert ei.value.status == status, bad
+    with pytest.raises(rhd.RhdError) as ei:
+        g.radiation_subcycle(-1, c, dt)
+    assert ei.value.status == rhd.ERR_ARG
+    g.radiation_subcycle(1, c, dt)
+    assert g.get_stats()["n_subcycles"] == 1
+    g.close()
+
+
+def test_forced_out_of_memory_then_recovers(rhd, monkeypatch):
+    case = wl.parity_case("oom", (48, 32, 32), n_sub=1, seed=44, precision="split")
+    monkeypatch.setenv("RHD_DEVICE_MEMORY_LIMIT", str(1 << 20))
+    with pytest.raises(rhd.RhdError) as ei:
+        rhd.Grid(case["desc"])
+    assert ei.value.status == rhd.ERR_OOM
+    # without the limit the same process creates and steps the grid
+    monkeypatch.delenv("RHD_DEVICE_MEMORY_LIMIT")
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    g.radiation_subcycle(1, case["chat"], case["dt"])
+    assert g.get_stats()["n_nonfinite"] == 0
+    g.close()
+
+
+def test_state_required_before_stepping(rhd):
+    case = wl.parity_case("state", (16, 8, 8), n_sub=1, seed=45, precision="split")
+    g = rhd.Grid(case["desc"])
+    with pytest.raises(rhd.RhdError) as ei:
+        g.radiation_subcycle(1, case["chat"], case["dt"])
+    assert ei.value.status == rhd.ERR_STATE
+    with pytest.raises(rhd.RhdError) as ei:
+        g.get_moments()
+    assert ei.value.status == rhd.ERR_STATE
+    g.close()
