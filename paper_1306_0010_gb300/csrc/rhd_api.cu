@@ -244,6 +244,7 @@ void fill_params(GridState& gs)
     g.f_E_floor = (float)d.E_floor;
     g.f_kappa_P = (float)d.kappa_P;
     g.f_kappa_F = (float)d.kappa_F;
+    for (int k = 0; k < 3; ++k) g.f_inv_dx[k] = (float)g.inv_dx[k];
     tile_shape(d.precision, g.nact, &gs.tx, &gs.ty);
     if (const char* ov = std::getenv("RHD_TILE")) {  // "TXxTY": measurement override of the tile shape
         int tx = 0, ty = 0;
@@ -562,6 +563,8 @@ StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double
     a.gas4 = twopass ? gs.gas4 : nullptr;
     p.chat = chat;
     p.dt = dt;
+    p.f_chat = (float)chat;
+    p.f_dt = (float)dt;
     p.uhalf = gs.uhalf;
     p.staging = gs.staging;
     if (gs.staging == RHD_STAGING_TMA) p.uh_map = gs.uh_map;
@@ -758,6 +761,7 @@ rhd_status ens_prepare(rhd_ctx* ctx, double chat, const double* dt_per_grid, dou
             eg[i].g = p.g;
             eg[i].a = p.a;
             eg[i].dt = dt_per_grid[i];
+            eg[i].f_dt = (float)dt_per_grid[i];
             // corrector (two-pass) or fused items: tiles of the interior; the two-pass kernels use 32 x 8
             eg[i].tiles_x = twopass ? (gs.desc.n[0] + 31) / 32 : gs.tiles_x;
             eg[i].tiles_y = twopass ? (gs.desc.n[1] + 7) / 8 : gs.tiles_y;
@@ -795,6 +799,7 @@ rhd_status ens_launch(rhd_ctx* ctx, double chat, int src)
     ep.n_items = ctx->n_items;
     ep.n_pitems = ctx->n_pitems;
     ep.chat = chat;
+    ep.f_chat = (float)chat;
     ep.z_chunk = ctx->grids[0].z_chunk;
     ep.limiter = ctx->grids[0].desc.limiter;
     ep.stats = ctx->dstats;

@@ -38,6 +38,7 @@ struct GridParams {
     // derived on the host: 1/c, (gamma - 1) mu/k_B, and FP32 copies used by the split path
     double inv_c, gm1_mu;
     float f_inv_c, f_gm1_mu, f_c, f_a_rad, f_theta_F, f_theta_E, f_E_floor, f_kappa_P, f_kappa_F;
+    float f_inv_dx[3];
 };
 
 // Device arrays of one grid.  FP32 copies of the frozen inputs are used by the split path.
@@ -67,6 +68,7 @@ struct StepParams {
     GridParams g;
     GridArrays a;
     double chat, dt;
+    float f_chat, f_dt;         // FP32 copies: FP32 code reads them as constant operands (no conversion)
     float4* uhalf;              // two-pass split path: U^{m+1/2} on the grid padded by 2 ghost layers
     int z_chunk;                // planes per CTA
     int tx, ty;                 // tile shape (selects the kernel instantiation)
@@ -81,6 +83,7 @@ struct EnsembleGrid {
     GridParams g;
     GridArrays a;
     double dt;
+    float f_dt;
     int tiles_x, tiles_y, tiles_z;
     long long first_item;       // prefix sum of tiles over the grids before this one
     // two-pass ensembles: U^{m+1/2} of this grid (padded by 2 ghost layers) and the predictor's
@@ -96,6 +99,7 @@ struct EnsembleParams {
     long long n_items;          // corrector (or fused) work items
     long long n_pitems;         // predictor work items (two-pass)
     double chat;
+    float f_chat;
     int z_chunk;
     int limiter;                // shared by all grids (the two-pass corrector is instantiated per limiter)
     unsigned long long* counter;  // work-queue head, reset before each launch

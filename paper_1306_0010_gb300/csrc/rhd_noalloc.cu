@@ -125,6 +125,8 @@ extern "C" rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double 
     p.g = gp;
     p.chat = chat;
     p.dt = dt;
+    p.f_chat = (float)chat;
+    p.f_dt = (float)dt;
     p.z_chunk = z_chunk;
     p.tx = 16;
     p.ty = 8;

@@ -152,8 +152,8 @@ struct GeoPred {
 
 // Predictor over the padded column tile (x0, y0) (coordinates in [-2, n+2)) for planes [z0, z1).
 template <int TX, int TY>
-__device__ __forceinline__ void predictor_tile(const GridParams& g, const GridArrays& a, float4* uh, double chat_d,
-                                               double dt_d, int x0, int y0, int z0, int z1, float4* sm, Counters& cnt)
+__device__ __forceinline__ void predictor_tile(const GridParams& g, const GridArrays& a, float4* uh, float chat,
+                                               float dt, int x0, int y0, int z0, int z1, float4* sm, Counters& cnt)
 {
     using G = GeoPred<TX, TY>;
     const int t = threadIdx.x;
@@ -164,8 +164,8 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     float4* Fx = sm + G::FXo;
     float4* Fy = sm + G::FYo;
     float4* gsl = sm + G::GSo + t;  // gsl[(p % 3) NT]: the own cell's (rho, vx, vy, vz) of plane p
-    const float chat = (float)chat_d, hdt = 0.5f * (float)dt_d;
-    const float idx = (float)g.inv_dx[0], idy = (float)g.inv_dx[1], idz = (float)g.inv_dx[2];
+    const float hdt = 0.5f * dt;
+    const float idx = g.f_inv_dx[0], idy = g.f_inv_dx[1], idz = g.f_inv_dx[2];
     const int p1 = g.closure == 1, fixed = g.speeds == 1;
     const bool needT = g.exchange == EX_FROZEN_T;
     const long long nxy = (long long)g.n[0] * g.n[1];
@@ -406,7 +406,7 @@ struct GeoCorr {
 // and mbar are then required, and sm must be 128-byte aligned); otherwise by per-thread cp.async.
 template <int TX, int TY, bool TMA = false, int LIMK = -1>
 __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridArrays& a, const float4* uh,
-                                               double chat_d, double dt_d, int x0, int y0, int z0, int z1, float4* sm,
+                                               float chat, float dt, int x0, int y0, int z0, int z1, float4* sm,
                                                Counters& cnt, const CUtensorMap* map = nullptr,
                                                uint64_t* mbar = nullptr)
 {
@@ -419,8 +419,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     float4* Cy = sm + G::CYo;
     double* oD = reinterpret_cast<double*>(sm + G::END4) + t;                       // oD[q NT]: E, Gx, Gy, Gz, T
     float4* oG = reinterpret_cast<float4*>(reinterpret_cast<double*>(sm + G::END4) + G::OD * G::NT) + t;  // gas
-    const float chat = (float)chat_d, dt = (float)dt_d;
-    const float idx = (float)g.inv_dx[0], idy = (float)g.inv_dx[1], idz = (float)g.inv_dx[2];
+    const float idx = g.f_inv_dx[0], idy = g.f_inv_dx[1], idz = g.f_inv_dx[2];
     // LIMK >= 0: the limiter is a compile-time constant (only its code is generated); -1: g.limiter
     const int p1 = g.closure == 1, fixed = g.speeds == 1, lim = LIMK >= 0 ? LIMK : g.limiter;
     const bool needT = g.exchange == EX_FULL || g.exchange == EX_FROZEN_T;
@@ -740,7 +739,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_kernel(
     const int z0 = (int)blockIdx.y * P.z_chunk - 2;
     const int z1 = min(z0 + P.z_chunk, P.g.n[2] + 2);
     Counters cnt = {0, 0, 0, 0, 0, 0};
-    predictor_tile<TX, TY>(P.g, P.a, P.uhalf, P.chat, P.dt, x0, y0, z0, z1, reinterpret_cast<float4*>(smem_raw), cnt);
+    predictor_tile<TX, TY>(P.g, P.a, P.uhalf, P.f_chat, P.f_dt, x0, y0, z0, z1, reinterpret_cast<float4*>(smem_raw), cnt);
     add_counter(&P.stats->n_fix, cnt.fix);
 }
 
@@ -757,7 +756,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(
     // TMA destinations need 128-byte alignment: the launch adds 128 bytes of slack
     float4* sm = reinterpret_cast<float4*>(smem_raw);
     if constexpr (TMA) sm = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    corrector_tile<TX, TY, TMA, LIMK>(P.g, P.a, P.uhalf, P.chat, P.dt, x0, y0, z0, z1, sm, cnt, &P.uh_map, mbar);
+    corrector_tile<TX, TY, TMA, LIMK>(P.g, P.a, P.uhalf, P.f_chat, P.f_dt, x0, y0, z0, z1, sm, cnt, &P.uh_map, mbar);
     add_counter(&P.stats->n_fix, cnt.fix);
     add_counter(&P.stats->n_face, cnt.face);
     add_counter(&P.stats->n_theta, cnt.theta);
@@ -814,7 +813,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_ens_ker
         const int txy = (int)(local % nxy), tz = (int)(local / nxy);
         const int x0 = (txy % eg.ptiles_x) * TX - 2, y0 = (txy / eg.ptiles_x) * TY - 2;
         const int z0 = tz * P.z_chunk - 2, z1 = min(z0 + P.z_chunk, eg.g.n[2] + 2);
-        predictor_tile<TX, TY>(eg.g, eg.a, eg.uhalf, P.chat, eg.dt, x0, y0, z0, z1,
+        predictor_tile<TX, TY>(eg.g, eg.a, eg.uhalf, P.f_chat, eg.f_dt, x0, y0, z0, z1,
                                reinterpret_cast<float4*>(smem_raw), cnt);
         __syncthreads();
     }
@@ -835,7 +834,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_ens_ker
         const int txy = (int)(local % nxy), tz = (int)(local / nxy);
         const int x0 = (txy % eg.tiles_x) * TX, y0 = (txy / eg.tiles_x) * TY;
         const int z0 = tz * P.z_chunk, z1 = min(z0 + P.z_chunk, eg.g.n[2]);
-        corrector_tile<TX, TY, false, LIMK>(eg.g, eg.a, eg.uhalf, P.chat, eg.dt, x0, y0, z0, z1,
+        corrector_tile<TX, TY, false, LIMK>(eg.g, eg.a, eg.uhalf, P.f_chat, eg.f_dt, x0, y0, z0, z1,
                                reinterpret_cast<float4*>(smem_raw), cnt);
         __syncthreads();
     }
