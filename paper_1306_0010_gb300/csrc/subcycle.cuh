@@ -530,8 +530,9 @@ __device__ __forceinline__ ExchangeOut exchange_fp64(const GridParams& g, double
     return o;
 }
 
-// FP32 Newton for delta with the same iteration; the caller applies E - (chat/c) delta and
-// T + q delta to the FP64 state.
+// FP32 Newton for delta with the same iteration, which also stops once a step is small enough that
+// the next could not change the FP32 result; the caller applies E - (chat/c) delta and T + q delta
+// to the FP64 state.
 __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float chat, float dt, float rho, float kP,
                                                      float E, float T, ExchangeOut& o, float& qout)
 {
@@ -569,6 +570,15 @@ __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float 
         dn = fminf(fmaxf(dn, dlo), dhi);
         if (it > 0 && !(dn < d)) {
             conv = true;
+            break;
+        }
+        // a step below 2^-13 x: Newton's error after it is at most (g''/2g') step^2 <= 1.5 step^2 / x
+        // (g'' = 12 A x^2, g' >= 4 A x^3), i.e. under 2^-25 x, below half an FP32 ulp of x, so the
+        // iterate is final without the extra iteration that would find the fixed point
+        if (fabsf(dn - d) <= 1.220703125e-4f * x) {
+            d = dn;
+            conv = true;
+            ++it;
             break;
         }
         d = dn;

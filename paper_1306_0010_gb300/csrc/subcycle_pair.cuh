@@ -104,15 +104,15 @@ __device__ __forceinline__ void closure_ab_pair(float2 E, float2 gx, float2 gy, 
     l3 = p_mul(p_add(fd, sr), cs);
 }
 
-// Flux chat (G_D, P_D.) of state U in direction D from its closure coefficients (same operations as
-// the flux of closure_pair).
+// Flux per unit chat, (G_D, P_D.), of state U in direction D from its closure coefficients; the HLL
+// weights of hll_pair / hll4 carry the factor chat.
 template <int D>
-__device__ __forceinline__ float4 flux_ab(float4 U, float a, float b, float chat)
+__device__ __forceinline__ float4 flux_ab(float4 U, float a, float b)
 {
     const float gd = D == 0 ? U.y : (D == 1 ? U.z : U.w);
     const float bg = b * gd;
-    return make_float4(chat * gd, chat * (D == 0 ? fmaf(bg, U.y, a) : bg * U.y),
-                       chat * (D == 1 ? fmaf(bg, U.z, a) : bg * U.z), chat * (D == 2 ? fmaf(bg, U.w, a) : bg * U.w));
+    return make_float4(gd, D == 0 ? fmaf(bg, U.y, a) : bg * U.y, D == 1 ? fmaf(bg, U.z, a) : bg * U.z,
+                       D == 2 ? fmaf(bg, U.w, a) : bg * U.w);
 }
 
 // minmod(a, b): the one of a, b nearer zero if they have the same sign, else 0.  One of the two terms
@@ -192,40 +192,42 @@ __device__ __forceinline__ int face_record_ab(float4 um, float4 u0, float4 up, f
     return fb;
 }
 
-// HLL flux (Eq. hyperbolic:hllflux2) with the four components as two FP32 pairs.
+// HLL flux (Eq. hyperbolic:hllflux2) with the four components as two FP32 pairs; FL, FR are the
+// states' fluxes per unit chat and the weights carry the factor chat.
 __device__ __forceinline__ float4 hll_pair(float4 UL, float4 UR, float4 FL, float4 FR, float l1L, float l3L,
-                                           float l1R, float l3R)
+                                           float l1R, float l3R, float chat)
 {
     const float SRp = fmaxf(fmaxf(l3L, l3R), 0.f), SLm = fminf(fminf(l1L, l1R), 0.f);
     const float den = SRp - SLm;
     if (den > 0.f) {
-        const float2 a = p_s(SRp), b = p_s(-SLm), c = p_s(SRp * SLm), iv = p_s(rcp(den));
+        const float2 a = p_s(SRp * chat), b = p_s(-SLm * chat), c = p_s(SRp * SLm), iv = p_s(rcp(den));
         const float2 lo =
             p_mul(p_fma(c, p_sub(p_lo(UR), p_lo(UL)), p_fma(b, p_lo(FR), p_mul(a, p_lo(FL)))), iv);
         const float2 hi =
             p_mul(p_fma(c, p_sub(p_hi(UR), p_hi(UL)), p_fma(b, p_hi(FR), p_mul(a, p_hi(FL)))), iv);
         return make_float4(lo.x, lo.y, hi.x, hi.y);
     }
-    const float2 lo = p_mul(p_add(p_lo(FL), p_lo(FR)), p_s(0.5f));
-    const float2 hi = p_mul(p_add(p_hi(FL), p_hi(FR)), p_s(0.5f));
+    const float2 lo = p_mul(p_add(p_lo(FL), p_lo(FR)), p_s(0.5f * chat));
+    const float2 hi = p_mul(p_add(p_hi(FL), p_hi(FR)), p_s(0.5f * chat));
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 // The same HLL flux with scalar FP32 operations (same operation order and fused multiply-adds as
 // hll_pair, so the same bits): cheaper where the operands are not already register pairs.
 __device__ __forceinline__ float4 hll4(float4 UL, float4 UR, float4 FL, float4 FR, float l1L, float l3L, float l1R,
-                                       float l3R)
+                                       float l3R, float chat)
 {
     const float SRp = fmaxf(fmaxf(l3L, l3R), 0.f), SLm = fminf(fminf(l1L, l1R), 0.f);
     const float den = SRp - SLm;
     if (den > 0.f) {
-        const float a = SRp, b = -SLm, c = SRp * SLm, iv = rcp(den);
+        const float a = SRp * chat, b = -SLm * chat, c = SRp * SLm, iv = rcp(den);
         return make_float4(fmaf(c, UR.x - UL.x, fmaf(b, FR.x, a * FL.x)) * iv,
                            fmaf(c, UR.y - UL.y, fmaf(b, FR.y, a * FL.y)) * iv,
                            fmaf(c, UR.z - UL.z, fmaf(b, FR.z, a * FL.z)) * iv,
                            fmaf(c, UR.w - UL.w, fmaf(b, FR.w, a * FL.w)) * iv);
     }
-    return make_float4((FL.x + FR.x) * 0.5f, (FL.y + FR.y) * 0.5f, (FL.z + FR.z) * 0.5f, (FL.w + FR.w) * 0.5f);
+    const float h = 0.5f * chat;
+    return make_float4((FL.x + FR.x) * h, (FL.y + FR.y) * h, (FL.z + FR.z) * h, (FL.w + FR.w) * h);
 }
 
 __device__ __forceinline__ float4 f4(const float U[4]) { return make_float4(U[0], U[1], U[2], U[3]); }

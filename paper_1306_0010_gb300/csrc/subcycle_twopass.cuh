@@ -249,15 +249,15 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     const float4* Um = Um0;  // the current plane's buffer
     auto xface = [&](int iL, int iR) {
         const float4 UL = Um[iL], UR = Um[iR], CL = CX[iL], CR = CX[iR];
-        const float4 FL = make_float4(chat * UL.y, chat * CL.x, chat * CL.y, chat * CL.z);
-        const float4 FR = make_float4(chat * UR.y, chat * CR.x, chat * CR.y, chat * CR.z);
-        return hll4(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x);
+        const float4 FL = make_float4(UL.y, CL.x, CL.y, CL.z);  // fluxes per unit chat
+        const float4 FR = make_float4(UR.y, CR.x, CR.y, CR.z);
+        return hll4(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x, chat);
     };
     auto yface = [&](int iL, int iR) {
         const float4 UL = Um[iL], UR = Um[iR], CL = CY[iL], CR = CY[iR];
-        const float4 FL = make_float4(chat * UL.z, chat * CL.x, chat * CL.y, chat * CL.z);
-        const float4 FR = make_float4(chat * UR.z, chat * CR.x, chat * CR.y, chat * CR.z);
-        return hll4(UL, UR, FL, FR, CL.w, L3[iL].y, CR.w, L3[iR].y);
+        const float4 FL = make_float4(UL.z, CL.x, CL.y, CL.z);
+        const float4 FR = make_float4(UR.z, CR.x, CR.y, CR.z);
+        return hll4(UL, UR, FL, FR, CL.w, L3[iL].y, CR.w, L3[iR].y, chat);
     };
 
     float4 zU = make_float4(0.f, 0.f, 0.f, 0.f), zP = zU, dxy = zU, zfl = zU;
@@ -325,9 +325,9 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
                                           (bxf.w - ax.w) * idx + (by.w - ay.w) * idy);
             float4 zfh = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q > qbeg) {
-                const float4 FL = make_float4(chat * zU.w, chat * zP.x, chat * zP.y, chat * zP.z);
-                const float4 FR = make_float4(chat * nU.w, chat * nP.x, chat * nP.y, chat * nP.z);
-                zfh = hll4(zU, nU, FL, FR, zP.w, zl3, nP.w, nl3);
+                const float4 FL = make_float4(zU.w, zP.x, zP.y, zP.z);
+                const float4 FR = make_float4(nU.w, nP.x, nP.y, nP.z);
+                zfh = hll4(zU, nU, FL, FR, zP.w, zl3, nP.w, nl3, chat);
             }
             const int p = q - 1;
             if (emit) {
@@ -492,15 +492,13 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         const float4 UL = Sx[G::NSX + iL], UR = Sx[iR];
         const float4 cL = Sx[2 * G::NSX + iL], cR = Sx[2 * G::NSX + iR];
         const float4 LL = Sx[3 * G::NSX + iL], LR = Sx[3 * G::NSX + iR];
-        return hll_pair(UL, UR, flux_ab<0>(UL, cL.z, cL.w, chat), flux_ab<0>(UR, cR.x, cR.y, chat), LL.z, LL.w, LR.x,
-                        LR.y);
+        return hll_pair(UL, UR, flux_ab<0>(UL, cL.z, cL.w), flux_ab<0>(UR, cR.x, cR.y), LL.z, LL.w, LR.x, LR.y, chat);
     };
     auto hll_y = [&](int iL, int iR) {
         const float4 UL = Sy[G::NSY + iL], UR = Sy[iR];
         const float4 cL = Sy[2 * G::NSY + iL], cR = Sy[2 * G::NSY + iR];
         const float4 LL = Sy[3 * G::NSY + iL], LR = Sy[3 * G::NSY + iR];
-        return hll_pair(UL, UR, flux_ab<1>(UL, cL.z, cL.w, chat), flux_ab<1>(UR, cR.x, cR.y, chat), LL.z, LL.w, LR.x,
-                        LR.y);
+        return hll_pair(UL, UR, flux_ab<1>(UL, cL.z, cL.w), flux_ab<1>(UR, cR.x, cR.y), LL.z, LL.w, LR.x, LR.y, chat);
     };
 
     // lower z face of the first plane: face states of cells z0-1 and z0 from U^{m+1/2} at z0-2 .. z0+1
@@ -513,8 +511,8 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         face_record_ab<2>(u_m2, u_m1, u_0, chat, lim, p1, fixed, ra);
         const int fb = face_record_ab<2>(u_m1, u_0, u_1, chat, lim, p1, fixed, rb);
         cnt.face += (unsigned)(fb & (int)own_col);
-        cfl = hll_pair(ra[1], rb[0], flux_ab<2>(ra[1], ra[2].z, ra[2].w, chat), flux_ab<2>(rb[0], rb[2].x, rb[2].y, chat),
-                       ra[3].z, ra[3].w, rb[3].x, rb[3].y);
+        cfl = hll_pair(ra[1], rb[0], flux_ab<2>(ra[1], ra[2].z, ra[2].w), flux_ab<2>(rb[0], rb[2].x, rb[2].y), ra[3].z,
+                       ra[3].w, rb[3].x, rb[3].y, chat);
         zpS = rb[1];
         zpa = rb[2].z;
         zpb = rb[2].w;
@@ -601,8 +599,8 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             float4 rec[4];
             const int fb = face_record_ab<2>(Uk[ihc], ukp1, ukp2, chat, lim, p1, fixed, rec);
             cnt.face += (unsigned)(fb & (int)(k + 1 < z1) & (int)own_col);
-            cfh = hll_pair(zpS, rec[0], flux_ab<2>(zpS, zpa, zpb, chat), flux_ab<2>(rec[0], rec[2].x, rec[2].y, chat), zpl1,
-                           zpl3, rec[3].x, rec[3].y);
+            cfh = hll_pair(zpS, rec[0], flux_ab<2>(zpS, zpa, zpb), flux_ab<2>(rec[0], rec[2].x, rec[2].y), zpl1, zpl3,
+                           rec[3].x, rec[3].y, chat);
             zpS = rec[1];
             zpa = rec[2].z;
             zpb = rec[2].w;
