@@ -66,23 +66,24 @@ __device__ __forceinline__ float rcp(float x)
 // inf), and the exact widening of an FP32 value (denormals flushed), by integer bit operations.
 __device__ __forceinline__ float d2f_trunc(double x)
 {
-    unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    unsigned sign = hi & 0x80000000u;
-    int fe = (int)((hi >> 20) & 0x7ffu) - 896;
-    unsigned r = sign | ((unsigned)fe << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    r = fe <= 0 ? sign : r;
-    r = fe >= 255 ? (sign | 0x7f800000u) : r;
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u, a = hi & 0x7fffffffu;
+    // (hi:lo) << 3 puts the exponent's low 8 bits above the 23 leading mantissa bits; in the FP32
+    // normal range the rebias (exponent - 896) mod 256 is those 8 bits with the top one flipped
+    unsigned r = ((__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u) | sign;
+    r = a < 0x38100000u ? sign : r;                   // below the FP32 normal range: signed zero
+    r = a >= 0x47f00000u ? (sign | 0x7f800000u) : r;  // beyond it: signed infinity
     return __uint_as_float(r);
 }
 __device__ __forceinline__ double f2d_exact(float f)
 {
-    unsigned b = __float_as_uint(f);
-    unsigned sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-    unsigned hi = sign | ((ex + 896u) << 20) | (m >> 3);
-    unsigned lo = m << 29;
-    hi = ex == 0u ? sign : hi;
-    lo = ex == 0u ? 0u : lo;
-    hi = ex == 255u ? (sign | 0x7ff00000u | (m >> 3)) : hi;
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u, a = b & 0x7fffffffu;
+    // exponent and mantissa shifted into place with the exponent rebiased by 896 (1023 - 127)
+    unsigned hi = ((a >> 3) + 0x38000000u) | sign, lo = b << 29;
+    hi = a < 0x00800000u ? sign : hi;  // zero and denormals: signed zero
+    lo = a < 0x00800000u ? 0u : lo;
+    hi = a >= 0x7f800000u ? ((a >> 3) | 0x7ff00000u | sign) : hi;
     return __hiloint2double((int)hi, (int)lo);
 }
 // Asynchronous global->shared copies (cp.async): the next plane is fetched while the current one
