@@ -115,9 +115,10 @@ __device__ __forceinline__ float4 flux_ab(float4 U, float a, float b)
                        D == 2 ? fmaf(bg, U.w, a) : bg * U.w);
 }
 
-// minmod(a, b): the one of a, b nearer zero if they have the same sign, else 0.  One of the two terms
-// is always a signed zero, so the sum is exactly a, b or 0.
-__device__ __forceinline__ float minmod_f(float a, float b) { return fmaxf(0.0f, fminf(a, b)) + fminf(0.0f, fmaxf(a, b)); }
+// minmod(a, b): the one of a, b nearer zero if they have the same sign, else 0, as three min / max:
+// both positive -> min(a, b); both negative -> min(0, max(a, b)) = max(a, b); mixed signs -> max of
+// a negative number and 0.
+__device__ __forceinline__ float minmod_f(float a, float b) { return fmaxf(fminf(a, b), fminf(0.0f, fmaxf(a, b))); }
 
 // Limited slope from the left and right differences (minmod, MC or none): the same values as
 // `limited` in subcycle.cuh (MC = minmod(2 minmod(dl, dr), (dl + dr)/2)), as straight-line min / max
