@@ -301,6 +301,40 @@ rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double dirichlet[2
                                 double* E_out, double* Fx_out, double* Fy_out, double* Fz_out, double* T_out,
                                 rhd_stats* stats);
 
+/* ---------------------------------------------------------------------------------------------
+ * Reduced-speed-of-light helpers (Sections 3.1 and 3.2): the signal speeds and time steps around the
+ * subcycle loop.  The two grid maxima run as reductions on the context's stream and synchronise it;
+ * single-grid contexts only (RHD_ERR_STATE on an ensemble).
+ * --------------------------------------------------------------------------------------------- */
+
+/* v_max = max over cells of |v| + c_eff, with the effective sound speed of Eq. algorithm:ceff
+ * c_eff = sqrt((gamma P + (4/9) E (1 - exp(-k_F dx))) / rho), P = rho T / mu_over_kB, from the frozen
+ * gas state (current T) and the current E; k_F is the per-cell flux-mean absorption coefficient (the
+ * kF array, else the opacity law) and dx the smallest active spacing.  Errors: RHD_ERR_ARG,
+ * RHD_ERR_STATE (gas or moments not set), RHD_ERR_NONFINITE (*v_max is then NaN or inf), RHD_ERR_OOM,
+ * RHD_ERR_CUDA. */
+rhd_status rhd_max_signal_speed(rhd_ctx* ctx, double* v_max);
+
+/* tau_max = the largest optical depth sum(k_F dx_d) along any grid line parallel to an active axis:
+ * the domain's optical depth along the axes, the tau_max of Eq. rsla:diffcrit measured on the grid.
+ * Errors as rhd_max_signal_speed (only the gas state is required). */
+rhd_status rhd_max_optical_depth(rhd_ctx* ctx, double* tau_max);
+
+/* chat from the RSLA static-diffusion criterion (Eq. rsla:staticdiffreq), "much greater than" taken
+ * as the factor ratio (the paper uses R ~ 10 to 100): chat = min(c, ratio v_max max(1, tau_max)), i.e.
+ * chat = c where c is not far above the gas speeds (Section 3.1).  Pure host arithmetic.  Errors:
+ * RHD_ERR_ARG (c, v_max, ratio not positive and finite, tau_max negative or not finite, NULL chat). */
+rhd_status rhd_suggest_chat(double c, double v_max, double tau_max, double ratio, double* chat);
+
+/* Time steps of one gas cycle: dt_gas = cfl dx_min / v_max (Eq. algorithm:gastimestep) and the
+ * radiation subcycles that span it (Eq. algorithm:radtimestep, "about R" of them, Section 3.1 step 5):
+ * n_sub = the smallest n with dt_gas / n <= cfl dx_min / chat, dt_rad = dt_gas / n_sub, so that
+ * n_sub subcycles end exactly at t + dt_gas and dt_rad passes rhd_radiation_subcycle's CFL check.  Pure
+ * host arithmetic.  Errors: RHD_ERR_ARG (non-positive or non-finite input, NULL output, more than
+ * 2^31 - 1 subcycles). */
+rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, double* dt_gas, double* dt_rad,
+                          int* n_sub);
+
 /* Library identification: ABI version and the compute capability it was built for (e.g. 103). */
 int rhd_abi_version(void);
 int rhd_built_arch(void);

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librhd.so")
-SOURCES = ["rhd_api.cu", "k_fp64.cu", "k_split.cu", "k_aux.cu", "rhd_noalloc.cu"]
+SOURCES = ["rhd_api.cu", "k_fp64.cu", "k_split.cu", "k_aux.cu", "k_rsla.cu", "rhd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

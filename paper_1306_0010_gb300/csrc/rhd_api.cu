@@ -95,6 +95,7 @@ struct rhd_ctx {
     int cur = 0;  // buffer index holding the current state (shared by all grids)
     DevStats* dstats = nullptr;
     double* red_partials = nullptr;
+    double* rsla_partial = nullptr;  // reduced-speed-of-light reductions: rsla_blocks() + 1 doubles
     double* red_out = nullptr;
     int red_blocks = 1;
     long long n_subcycles = 0;
@@ -395,6 +396,7 @@ void destroy_ctx(rhd_ctx* ctx)
     dfree(ctx->dstats);
     dfree(ctx->red_partials);
     dfree(ctx->red_out);
+    dfree(ctx->rsla_partial);
     dfree(ctx->d_egrids[0]);
     dfree(ctx->d_egrids[1]);
     dfree(ctx->d_counter);
@@ -1185,6 +1187,46 @@ rhd_status ensemble_tune_once(rhd_ctx* ctx, double chat, const double* dt_per_gr
 // =============================================================================================
 // C ABI
 // =============================================================================================
+// ---------------------------------------------------------------------------------------------
+// reduced-speed-of-light helpers (Sections 3.1, 3.2)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+double active_dx_min(const rhd_grid_desc& d)
+{
+    double m = INFINITY;
+    for (int k = 0; k < 3; ++k)
+        if (d.n[k] > 1) m = std::min(m, d.dx[k]);
+    return std::isfinite(m) ? m : d.dx[0];
+}
+
+// one grid-wide maximum: the single grid of a context with its state set, the reduction buffer,
+// the launch (fill), the result copied back
+template <class Fill>
+rhd_status grid_maximum(rhd_ctx* ctx, double* out, bool need_moments, const char* what, Fill fill)
+{
+    if (!ctx || !out) return fail(ctx, RHD_ERR_ARG, "ctx and the output are required");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not available on an ensemble context");
+    GridState& gs = ctx->grids[0];
+    if (!gs.has_gas || (need_moments && !gs.has_moments))
+        return fail(ctx, RHD_ERR_STATE, need_moments ? "set the moments and the gas state first" : "set the gas state first");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    const int nb = rsla_blocks(ctx->num_sms);
+    if (!ctx->rsla_partial && (st = dalloc(ctx, (void**)&ctx->rsla_partial, sizeof(double) * (size_t)(nb + 1))))
+        return st;
+    RHD_CUDA(ctx, fill(gs, nb, ctx->rsla_partial));
+    double h = 0.0;
+    RHD_CUDA(ctx, cudaMemcpyAsync(&h, ctx->rsla_partial + nb, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((st = leave(ctx))) return st;
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *out = h;
+    if (!std::isfinite(h)) return fail(ctx, RHD_ERR_NONFINITE, std::string(what) + " is not finite");
+    return RHD_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int rhd_abi_version(void) { return RHD_ABI_VERSION; }
@@ -1325,6 +1367,50 @@ rhd_status rhd_get_gas_state(rhd_ctx* ctx, double* T, int on_device)
     if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
     if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "use rhd_ensemble_get_gas_state on an ensemble");
     return get_T(ctx, ctx->grids[0], T, on_device);
+}
+
+rhd_status rhd_max_signal_speed(rhd_ctx* ctx, double* v_max)
+{
+    ApiRange range_("rhd_max_signal_speed");
+    return grid_maximum(ctx, v_max, true, "v_max", [&](GridState& gs, int nb, double* part) {
+        const double* v[3] = {gs.v[0], gs.v[1], gs.v[2]};
+        return launch_signal_speed(gs.gp, gs.rho, gs.T, gs.U[ctx->cur][0], v, gs.has_kF ? gs.kF : nullptr,
+                                   active_dx_min(gs.desc), gs.ncell, nb, part, ctx->stream);
+    });
+}
+
+rhd_status rhd_max_optical_depth(rhd_ctx* ctx, double* tau_max)
+{
+    ApiRange range_("rhd_max_optical_depth");
+    return grid_maximum(ctx, tau_max, false, "tau_max", [&](GridState& gs, int nb, double* part) {
+        return launch_max_optical_depth(gs.gp, gs.has_kF ? gs.kF : nullptr, gs.rho, gs.desc.dx, nb, part, ctx->stream);
+    });
+}
+
+rhd_status rhd_suggest_chat(double c, double v_max, double tau_max, double ratio, double* chat)
+{
+    if (!chat) return fail(nullptr, RHD_ERR_ARG, "chat is NULL");
+    if (!finite_pos(c) || !finite_pos(v_max) || !finite_pos(ratio) || !(std::isfinite(tau_max) && tau_max >= 0.0))
+        return fail(nullptr, RHD_ERR_ARG, "c, v_max and ratio must be positive and finite, tau_max finite and >= 0");
+    *chat = std::min(c, ratio * v_max * std::max(1.0, tau_max));
+    return RHD_OK;
+}
+
+rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, double* dt_gas, double* dt_rad,
+                          int* n_sub)
+{
+    if (!dt_gas || !dt_rad || !n_sub) return fail(nullptr, RHD_ERR_ARG, "dt_gas, dt_rad and n_sub are required");
+    if (!finite_pos(cfl) || !finite_pos(dx_min) || !finite_pos(v_max) || !finite_pos(chat))
+        return fail(nullptr, RHD_ERR_ARG, "cfl, dx_min, v_max and chat must be positive and finite");
+    const double dg = cfl * dx_min / v_max, dmax = cfl * dx_min / chat;
+    const double q = std::ceil(dg / dmax);
+    if (!(q < 2147483647.0)) return fail(nullptr, RHD_ERR_ARG, "more than 2^31 subcycles per gas step");
+    int n = std::max(1, (int)q);
+    while (dg / n > dmax) ++n;
+    *dt_gas = dg;
+    *dt_rad = dg / n;
+    *n_sub = n;
+    return RHD_OK;
 }
 
 rhd_status rhd_reset_stats(rhd_ctx* ctx)

@@ -141,6 +141,13 @@ cudaError_t launch_to_float(float* dst, const double* src, long long n, cudaStre
 cudaError_t launch_reduce_state(const double* E, const double* G0, const double* G1, const double* G2,
                                 long long n, double* partials, int n_blocks, cudaStream_t s);
 cudaError_t launch_reduce_finish(const double* partials, int n_blocks, double* out5, cudaStream_t s);
+// reduced-speed-of-light helpers (k_rsla.cu): maxima over the grid into partial[nb] (partial holds nb + 1)
+int rsla_blocks(int num_sms);
+cudaError_t launch_signal_speed(const GridParams& g, const double* rho, const double* T, const double* E,
+                                const double* const v[3], const double* kF, double dx_min, long long n, int nb,
+                                double* partial, cudaStream_t s);
+cudaError_t launch_max_optical_depth(const GridParams& g, const double* kF, const double* rho, const double dx[3],
+                                     int nb, double* partial, cudaStream_t s);
 int reduce_blocks_for(long long n);
 
 }  // namespace rhd

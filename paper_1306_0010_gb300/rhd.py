@@ -169,6 +169,11 @@ _SIGS = {
     "rhd_set_launch_config": (ctypes.c_int, [_P, ctypes.POINTER(LaunchConfig)]),
     "rhd_set_kernel_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "rhd_get_kernel_times": (ctypes.c_int, [_P, ctypes.POINTER(KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "rhd_max_signal_speed": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "rhd_max_optical_depth": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "rhd_suggest_chat": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)]),
+    "rhd_time_steps": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2
+                       + [ctypes.POINTER(ctypes.c_int)]),
     "rhd_abi_version": (ctypes.c_int, []),
     "rhd_built_arch": (ctypes.c_int, []),
 }
@@ -317,6 +322,18 @@ class Grid:
         od = _same_residency(ps)
         _check(self._ctx, lib().rhd_get_moments(self._ctx, *[p for p, _ in ps], od))
         return {"E": E, "Fx": Fx, "Fy": Fy, "Fz": Fz}
+
+    def max_signal_speed(self):
+        """v_max = max(|v| + c_eff) over the grid (Eq. algorithm:ceff), from the gas state and current E."""
+        out = ctypes.c_double()
+        _check(self._ctx, lib().rhd_max_signal_speed(self._ctx, ctypes.byref(out)))
+        return out.value
+
+    def max_optical_depth(self):
+        """The largest optical depth sum(k_F dx) along any grid line parallel to an active axis."""
+        out = ctypes.c_double()
+        _check(self._ctx, lib().rhd_max_optical_depth(self._ctx, ctypes.byref(out)))
+        return out.value
 
     def set_conserved(self, E, Gx, Gy, Gz):
         """Set the solver's own variables E and G = F/c (no conversion; see get_conserved)."""
@@ -534,3 +551,18 @@ def subcycle_noalloc(desc: dict, n_sub, chat, dt, E, Fx, Fy, Fz, rho, T, E_out, 
                                         *[p for p, _ in ps], ctypes.byref(st) if want_stats else None)
     _check(None, status)
     return st.as_dict() if want_stats else None
+
+
+def suggest_chat(c, v_max, tau_max, ratio=10.0):
+    """chat = min(c, ratio v_max max(1, tau_max)) (Eq. rsla:staticdiffreq with 'much greater' as ratio)."""
+    out = ctypes.c_double()
+    _check(None, lib().rhd_suggest_chat(float(c), float(v_max), float(tau_max), float(ratio), ctypes.byref(out)))
+    return out.value
+
+
+def time_steps(cfl, dx_min, v_max, chat):
+    """(dt_gas, dt_rad, n_sub) of one gas cycle (Eqs. algorithm:gastimestep and algorithm:radtimestep)."""
+    dg, dr, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(None, lib().rhd_time_steps(float(cfl), float(dx_min), float(v_max), float(chat), ctypes.byref(dg),
+                                      ctypes.byref(dr), ctypes.byref(n)))
+    return dg.value, dr.value, n.value
