@@ -248,7 +248,34 @@ def parse_launch(spec):
     return {"variant": v, "tile": (tx, ty), "z_chunk": int(z.lstrip("z")), "staging": stg}
 
 
-def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=True, launch_spec="auto"):
+def time_rsla(torch, g, case, stream, hbm_peak, reps=5):
+    """The reduced-speed-of-light reductions on the same grid (inputs larger than L2): CUDA events on
+    the library's stream around each call (the call synchronises after its kernels and an 8-byte
+    copy).  Algorithmic bytes: v_max reads rho, T, E and each velocity component and kF array the
+    grid has; tau_max reads kF (or rho for the opacity law) once per active axis."""
+    f = case["fields"]
+    cells = int(np.prod(f["rho"].shape))
+    n_v = sum(f.get(k) is not None for k in ("vx", "vy", "vz"))
+    has_kF = f.get("kF") is not None
+    n_axes = sum(int(v) > 1 for v in case["desc"]["n"])
+    out = {}
+    for name, call, bpc in (("max_signal_speed", g.max_signal_speed, 8 * (3 + n_v + has_kF)),
+                            ("max_optical_depth", g.max_optical_depth, 8 * n_axes)):
+        call()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for r in range(reps):
+            ev[2 * r].record(stream)
+            call()
+            ev[2 * r + 1].record(stream)
+        stream.synchronize()
+        ms = min(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(reps))
+        gbs = bpc * cells / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes_per_cell": bpc, "achieved_gbs": gbs, "frac": gbs / hbm_peak}
+    return out
+
+
+def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=True, launch_spec="auto",
+              rsla_peak=None):
     """Device-resident run: autotune the launch configuration (untimed), warm up, then time `steps`
     calls of n_sub subcycles with CUDA events on the library's stream.  The kernel timer brackets
     every kernel of the timed region with events on the same stream (plain launches)."""
@@ -283,9 +310,11 @@ def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=Tr
     total_ms = ev[0].elapsed_time(ev[-1])
     kt = g.kernel_times()
     st = g.get_stats(allow_nonfinite=True)
+    g.set_kernel_timing(False)
+    rsla = time_rsla(torch, g, case, stream, rsla_peak) if rsla_peak else None
     g.close()
     del dev
-    return total_ms, per_step_ms, st, kt, launch, tuning
+    return total_ms, per_step_ms, st, kt, launch, tuning, rsla
 
 
 # FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
@@ -504,8 +533,9 @@ def main():
     torch.cuda.synchronize()
     clk = ClockSampler(lrank)
     clk.start()
-    total_ms, per_step, st, kt, launch, tuning = time_path(torch, rhd, case, "split", args.n_sub, args.steps,
-                                                           args.warmup, stream, launch_spec=args.launch)
+    total_ms, per_step, st, kt, launch, tuning, rsla = time_path(torch, rhd, case, "split", args.n_sub, args.steps,
+                                                                 args.warmup, stream, launch_spec=args.launch,
+                                                                 rsla_peak=hbm_peak)
     clocks = clk.stop()
     if ws > 1:
         total_ms = max_over_ranks(total_ms, dist, device="cuda")
@@ -532,7 +562,7 @@ def main():
 
     extra = {}
     if not args.no_fp64:
-        fp_ms, fp_steps, fst, fkt, flaunch, _ = time_path(torch, rhd, case, "fp64", args.fp64_n_sub,
+        fp_ms, fp_steps, fst, fkt, flaunch, _, _ = time_path(torch, rhd, case, "fp64", args.fp64_n_sub,
                                                           max(2, args.steps // 2), args.warmup, stream, tune=False)
         fn = max(2, args.steps // 2)
         if ws > 1:
@@ -559,7 +589,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clocks,
                 "subcycle_roofline": subcycle_roofline, "alu_roofline": alu_roofline(value / ws),
-                "kernels": kt, "autotune": tuning,
+                "kernels": kt, "autotune": tuning, "rsla": rsla,
                 "stats": {k: st[k] for k in ("n_realizability_fix", "n_face_fallback", "n_theta_fallback",
                                              "n_nonfinite", "newton_iter_max")},
                 "per_step_ms": per_step}

@@ -54,7 +54,8 @@ typedef enum {
     RHD_ERR_CFL = 5,        /* dt > cfl * min(dx) / chat, or chat > c (Eqs. algorithm:radtimestep) */
     RHD_ERR_NONFINITE = 6,  /* non-finite values were produced (reported by rhd_get_stats) */
     RHD_ERR_TIMEOUT = 7,    /* a bounded wait gave up */
-    RHD_ERR_UNSUPPORTED = 8 /* the operation is not part of this library */
+    RHD_ERR_UNSUPPORTED = 8, /* the operation is not part of this library */
+    RHD_ERR_BOUNDS = 9       /* debug build only: kernels met out-of-range array indices (rhd_get_stats) */
 } rhd_status;
 
 /* Environment (read by the library, none required):
@@ -131,6 +132,12 @@ typedef struct {
     double sum_E;                /* sum of E over the interior (current state), FP64, fixed order */
     double sum_F[3];             /* sums of Fx, Fy, Fz */
     double max_f;                /* max |F|/(cE) */
+    int64_t bounds_violations;   /* debug build (librhd_debug.so, rhd_bounds_checked() = 1): array indices
+                                    found out of range by the kernels' checks since the last reset (each
+                                    access was redirected to element 0); nonzero makes rhd_get_stats
+                                    return RHD_ERR_BOUNDS.  The counter is per process (shared by all
+                                    contexts; rhd_reset_stats of any context clears it).  Always 0 in
+                                    the release build. */
 } rhd_stats;
 
 /* Create a context for one grid (Section 3.1).  Validates d, allocates the device state and makes
@@ -334,6 +341,11 @@ rhd_status rhd_suggest_chat(double c, double v_max, double tau_max, double ratio
  * 2^31 - 1 subcycles). */
 rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, double* dt_gas, double* dt_rad,
                           int* n_sub);
+
+/* 1 for the debug library librhd_debug.so, whose kernels check every global-memory index and the
+ * shared-memory indices of the two-pass kernels against their arrays' extents (a substitute for a
+ * memory checker: an out-of-range index is counted and redirected to element 0, no trap), else 0. */
+int rhd_bounds_checked(void);
 
 /* Library identification: ABI version and the compute capability it was built for (e.g. 103). */
 int rhd_abi_version(void);

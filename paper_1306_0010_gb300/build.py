@@ -16,6 +16,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librhd.so")
 SOURCES = ["rhd_api.cu", "k_fp64.cu", "k_split.cu", "k_aux.cu", "k_rsla.cu", "rhd_noalloc.cu"]
+# librhd_debug.so: the kernel translation units again with -DRHD_BOUNDS_CHECK (index checks that count
+# out-of-range indices and redirect the access), linked with the other objects of the release build
+DEBUG_LIB = os.path.join(PKG, "librhd_debug.so")
+DEBUG_SOURCES = ["k_fp64.cu", "k_split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +36,9 @@ def _newest_input() -> float:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
+    newest = _newest_input()
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and os.path.exists(DEBUG_LIB)
+            and os.path.getmtime(DEBUG_LIB) >= newest):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -40,26 +46,31 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         common += ["-Xptxas", "-v"]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *common, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, debug = job
+        obj = os.path.join(BUILD, src.replace(".cu", "_dbg.o" if debug else ".o"))
+        cmd = [cc, *common, *(["-DRHD_BOUNDS_CHECK"] if debug else []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    jobs = [(s, False) for s in SOURCES] + [(s, True) for s in DEBUG_SOURCES]
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        results = list(ex.map(compile_one, jobs))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
-    cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    objs = [o for o, _ in results[:len(SOURCES)]]
+    dbg = {src: o for (src, _), (o, _) in zip(jobs[len(SOURCES):], results[len(SOURCES):])}
+    debug_objs = [dbg.get(s, o) for s, o in zip(SOURCES, objs)]
+    for lib, lib_objs in ((LIB, objs), (DEBUG_LIB, debug_objs)):
+        tmp = lib + ".tmp"
+        cmd = [cc, "-shared", *ARCH, "-o", tmp, *lib_objs, "-cudart", "static"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -77,4 +77,31 @@ cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream
 
 int ensemble_ctas_per_sm_fp64() { return ens_occupancy<double, 16, 8, false>(); }
 
+// Out-of-range index record of this module's kernels (debug builds; the release build has none and
+// reports 0): copied to *out on stream s and, with reset, zeroed after the copy.
+cudaError_t oob_read_fp64(OobRecord* out, int reset, cudaStream_t s)
+{
+#ifdef RHD_BOUNDS_CHECK
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_oob);
+    if (e != cudaSuccess) return e;
+    if (out && (e = cudaMemcpyAsync(out, p, sizeof(OobRecord), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    return reset ? cudaMemsetAsync(p, 0, sizeof(OobRecord), s) : cudaSuccess;
+#else
+    (void)reset;
+    (void)s;
+    if (out) *out = OobRecord{0, 0, 0, 0, 0};
+    return cudaSuccess;
+#endif
+}
+bool bounds_checked_fp64()
+{
+#ifdef RHD_BOUNDS_CHECK
+    return true;
+#else
+    return false;
+#endif
+}
+
 }  // namespace rhd

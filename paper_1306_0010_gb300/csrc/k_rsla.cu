@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "fp_convert.cuh"
 #include "rhd_internal.h"
 
 namespace rhd {
@@ -40,23 +41,36 @@ __device__ __forceinline__ void block_max(double v, double* out)
     if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
-// v_max over the cells: |v| + sqrt((gamma P + (4/9) E (1 - exp(-k_F dx))) / rho) with P = rho T / (mu/k_B)
+// v_max over the cells: |v| + sqrt((gamma P + (4/9) E (1 - exp(-k_F dx))) / rho) with P = rho T / (mu/k_B).
+// The FP64 value (the result) costs an exponential, two square roots and two divisions on the FP64
+// pipe; only the maximum matters, so each cell is first screened in FP32 (inputs truncated, relative
+// error about 1e-6) and evaluated in FP64 only if its FP32 value is not below the thread's running FP32
+// maximum by more than 2^-12, or is NaN or inf.  The cell holding the FP64 maximum always passes the
+// screen, so the result is the FP64 maximum itself; FP32 underflow or overflow only sends more cells
+// to the FP64 evaluation.
 __global__ void __launch_bounds__(RS_THREADS) signal_speed_kernel(GridParams g, const double* rho, const double* T,
                                                                   const double* E, const double* v0, const double* v1,
                                                                   const double* v2, const double* kF, double dx_min,
                                                                   long long n, double* partial)
 {
+    const float gam = (float)g.gamma, inv_mu = (float)(1.0 / g.mu_over_kB), dxf = (float)dx_min;
     double m = 0.0;
+    float m32 = 0.0f;
     for (long long i = (long long)blockIdx.x * RS_THREADS + threadIdx.x; i < n; i += (long long)gridDim.x * RS_THREADS) {
-        const double r = rho[i];
-        const double P = r * T[i] / g.mu_over_kB;
-        const double rad = (4.0 / 9.0) * E[i] * (-expm1(-flux_absorption(g, kF, rho, i) * dx_min));
-        const double ceff = sqrt((g.gamma * P + rad) / r);
-        double v2s = 0.0;
-        if (v0) v2s += v0[i] * v0[i];
-        if (v1) v2s += v1[i] * v1[i];
-        if (v2) v2s += v2[i] * v2[i];
-        m = max_nan(m, sqrt(v2s) + ceff);
+        const double r = rho[i], Ti = T[i], Ei = E[i], kFi = kF ? kF[i] : 0.0;
+        const double a = v0 ? v0[i] : 0.0, b = v1 ? v1[i] : 0.0, c = v2 ? v2[i] : 0.0;
+        const float rf = d2f_trunc(r), af = d2f_trunc(a), bf = d2f_trunc(b), cf = d2f_trunc(c);
+        const float kf = kF ? d2f_trunc(kFi) : (g.kpow == 0 ? g.f_kappa_F : (g.kpow == 1 ? g.f_kappa_F * rf : (g.f_kappa_F * rf) * rf));
+        const float Pf = rf * d2f_trunc(Ti) * inv_mu;
+        const float radf = (4.0f / 9.0f) * d2f_trunc(Ei) * (-expm1f(-kf * dxf));
+        const float s32 = sqrtf(af * af + bf * bf + cf * cf) + sqrtf((gam * Pf + radf) / rf);
+        if (!(s32 < m32 * 0.999755859375f)) {
+            m32 = fmaxf(m32, s32);
+            const double k = kF ? kFi : flux_absorption(g, nullptr, rho, i);
+            const double P = r * Ti / g.mu_over_kB;
+            const double rad = (4.0 / 9.0) * Ei * (-expm1(-k * dx_min));
+            m = max_nan(m, sqrt(a * a + b * b + c * c) + sqrt((g.gamma * P + rad) / r));
+        }
     }
     block_max(m, partial);
 }

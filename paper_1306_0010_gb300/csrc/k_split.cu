@@ -212,4 +212,31 @@ int ensemble_ctas_per_sm_corrector()
 
 int ensemble_ctas_per_sm_split() { return ens_occupancy<float, 32, 8, true>(); }
 
+// Out-of-range index record of this module's kernels (debug builds; the release build has none and
+// reports 0): copied to *out on stream s and, with reset, zeroed after the copy.
+cudaError_t oob_read_split(OobRecord* out, int reset, cudaStream_t s)
+{
+#ifdef RHD_BOUNDS_CHECK
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_oob);
+    if (e != cudaSuccess) return e;
+    if (out && (e = cudaMemcpyAsync(out, p, sizeof(OobRecord), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    return reset ? cudaMemsetAsync(p, 0, sizeof(OobRecord), s) : cudaSuccess;
+#else
+    (void)reset;
+    (void)s;
+    if (out) *out = OobRecord{0, 0, 0, 0, 0};
+    return cudaSuccess;
+#endif
+}
+bool bounds_checked_split()
+{
+#ifdef RHD_BOUNDS_CHECK
+    return true;
+#else
+    return false;
+#endif
+}
+
 }  // namespace rhd

@@ -1231,6 +1231,7 @@ extern "C" {
 
 int rhd_abi_version(void) { return RHD_ABI_VERSION; }
 int rhd_built_arch(void) { return 103; }
+int rhd_bounds_checked(void) { return (bounds_checked_fp64() && bounds_checked_split()) ? 1 : 0; }
 
 const char* rhd_last_error(const rhd_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
 
@@ -1419,6 +1420,8 @@ rhd_status rhd_reset_stats(rhd_ctx* ctx)
     rhd_status st = enter(ctx);
     if (st) return st;
     RHD_CUDA(ctx, cudaMemsetAsync(ctx->dstats, 0, sizeof(DevStats), ctx->stream));
+    RHD_CUDA(ctx, oob_read_fp64(nullptr, 1, ctx->stream));
+    RHD_CUDA(ctx, oob_read_split(nullptr, 1, ctx->stream));
     ctx->n_subcycles = 0;
     return leave(ctx);
 }
@@ -1447,8 +1450,12 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
         for (int d = 0; d < 3; ++d) sums[1 + d] += gs.desc.c * h[1 + d];
         sums[4] = std::max(sums[4], h[4]);
     }
+    OobRecord oob[2];
+    RHD_CUDA(ctx, oob_read_fp64(&oob[0], 0, ctx->stream));
+    RHD_CUDA(ctx, oob_read_split(&oob[1], 0, ctx->stream));
     if ((st = leave(ctx))) return st;
     RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    out->bounds_violations = (int64_t)(oob[0].count + oob[1].count);
     out->n_subcycles = ctx->n_subcycles;
     out->n_realizability_fix = (int64_t)hs.n_fix;
     out->n_face_fallback = (int64_t)hs.n_face;
@@ -1460,6 +1467,13 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
     out->sum_E = sums[0];
     for (int d = 0; d < 3; ++d) out->sum_F[d] = sums[1 + d];
     out->max_f = sums[4];
+    if (out->bounds_violations) {
+        const OobRecord& r = oob[0].count ? oob[0] : oob[1];
+        return fail(ctx, RHD_ERR_BOUNDS,
+                    std::to_string(out->bounds_violations) + " out-of-range array indices; first in the " +
+                        (oob[0].count ? "FP64" : "split") + " kernels at source line " + std::to_string(r.line) +
+                        ": index " + std::to_string(r.index) + " of extent " + std::to_string(r.extent));
+    }
     if (out->wait_timeouts) return fail(ctx, RHD_ERR_TIMEOUT, "a device-side wait ran out; some tiles were not updated");
     if (out->n_nonfinite)
         return fail(ctx, RHD_ERR_NONFINITE,

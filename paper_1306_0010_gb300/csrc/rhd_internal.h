@@ -141,6 +141,17 @@ cudaError_t launch_to_float(float* dst, const double* src, long long n, cudaStre
 cudaError_t launch_reduce_state(const double* E, const double* G0, const double* G1, const double* G2,
                                 long long n, double* partials, int n_blocks, cudaStream_t s);
 cudaError_t launch_reduce_finish(const double* partials, int n_blocks, double* out5, cudaStream_t s);
+// out-of-range index records of the kernel modules (nonzero only in the debug build, RHD_BOUNDS_CHECK):
+// the count and the source line, index and extent (-1: grid coordinates packed by lin) of the first
+struct OobRecord {
+    unsigned long long count;
+    int line, pad;
+    long long index, extent;
+};
+cudaError_t oob_read_fp64(OobRecord* out, int reset, cudaStream_t s);
+cudaError_t oob_read_split(OobRecord* out, int reset, cudaStream_t s);
+bool bounds_checked_fp64();
+bool bounds_checked_split();
 // reduced-speed-of-light helpers (k_rsla.cu): maxima over the grid into partial[nb] (partial holds nb + 1)
 int rsla_blocks(int num_sms);
 cudaError_t launch_signal_speed(const GridParams& g, const double* rho, const double* T, const double* E,

@@ -26,6 +26,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "fp_convert.cuh"
 #include "rhd_internal.h"
 
 namespace rhd {
@@ -61,31 +62,34 @@ __device__ __forceinline__ float rcp(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-// FP64 <-> FP32 conversions without the FP64 pipe (which runs at a small fraction of the FP32 rate
-// on this part): truncation of the FP64 value to FP32 (normal range; underflow to 0, overflow to
-// inf), and the exact widening of an FP32 value (denormals flushed), by integer bit operations.
-__device__ __forceinline__ float d2f_trunc(double x)
+// Index checks of the debug build (-DRHD_BOUNDS_CHECK, librhd_debug.so): chk(i, n) compares an index
+// with its array's extent; an index outside it is counted in this translation unit's device record
+// (with the source line, index and extent of the first one) and replaced by 0, so the access stays
+// inside the array (no trap, no fault) and the host reports it (rhd_stats.bounds_violations,
+// RHD_ERR_BOUNDS).  In the release build chk is the identity.
+#ifdef RHD_BOUNDS_CHECK
+static __device__ OobRecord g_oob;
+__device__ __forceinline__ void oob_note(long long i, long long n, int line)
 {
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned sign = hi & 0x80000000u, a = hi & 0x7fffffffu;
-    // (hi:lo) << 3 puts the exponent's low 8 bits above the 23 leading mantissa bits; in the FP32
-    // normal range the rebias (exponent - 896) mod 256 is those 8 bits with the top one flipped
-    unsigned r = ((__funnelshift_l(lo, hi, 3) & 0x7fffffffu) ^ 0x40000000u) | sign;
-    r = a < 0x38100000u ? sign : r;                   // below the FP32 normal range: signed zero
-    r = a >= 0x47f00000u ? (sign | 0x7f800000u) : r;  // beyond it: signed infinity
-    return __uint_as_float(r);
+    if (atomicAdd(&g_oob.count, 1ull) == 0ull) {
+        g_oob.line = line;
+        g_oob.index = i;
+        g_oob.extent = n;
+    }
 }
-__device__ __forceinline__ double f2d_exact(float f)
+template <typename I>
+__device__ __forceinline__ I chk_at(I i, long long n, int line)
 {
-    const unsigned b = __float_as_uint(f);
-    const unsigned sign = b & 0x80000000u, a = b & 0x7fffffffu;
-    // exponent and mantissa shifted into place with the exponent rebiased by 896 (1023 - 127)
-    unsigned hi = ((a >> 3) + 0x38000000u) | sign, lo = b << 29;
-    hi = a < 0x00800000u ? sign : hi;  // zero and denormals: signed zero
-    lo = a < 0x00800000u ? 0u : lo;
-    hi = a >= 0x7f800000u ? ((a >> 3) | 0x7ff00000u | sign) : hi;
-    return __hiloint2double((int)hi, (int)lo);
+    if ((unsigned long long)(long long)i >= (unsigned long long)n) {
+        oob_note((long long)i, n, line);
+        return I(0);
+    }
+    return i;
 }
+#define chk(i, n) chk_at((i), (long long)(n), __LINE__)
+#else
+#define chk(i, n) (i)
+#endif
 // Asynchronous global->shared copies (cp.async): the next plane is fetched while the current one
 // is being computed; completion is awaited with cp.async.wait_all before the data are read.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src)
@@ -303,7 +307,21 @@ static __device__ __noinline__ int remap_cell(const GridParams& g, int pos[3], i
 
 __device__ __forceinline__ long long lin(const GridParams& g, int x, int y, int z)
 {
+#ifdef RHD_BOUNDS_CHECK
+    if ((unsigned)x >= (unsigned)g.n[0] || (unsigned)y >= (unsigned)g.n[1] || (unsigned)z >= (unsigned)g.n[2]) {
+        // the coordinates packed into one number: x + 2^20 (y + 2^20 z), offset by 2^19 each
+        oob_note((long long)(x + (1 << 19)) + ((long long)(y + (1 << 19)) << 20) + ((long long)(z + (1 << 19)) << 40),
+                 -1, __LINE__);
+        return 0;
+    }
+#endif
     return (long long)x + (long long)g.n[0] * ((long long)y + (long long)g.n[1] * (long long)z);
+}
+// cells of the interior arrays and of the grid padded by two ghost layers (U^{m+1/2} of the two-pass path)
+__device__ __forceinline__ long long n_cells(const GridParams& g) { return (long long)g.n[0] * g.n[1] * g.n[2]; }
+__device__ __forceinline__ long long n_padded(const GridParams& g)
+{
+    return (long long)(g.n[0] + 4) * (g.n[1] + 4) * (g.n[2] + 4);
 }
 
 // U^m = (E, Gx, Gy, Gz) at any cell, ghosts by the boundary rule.
@@ -773,7 +791,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
             int c = t + r * G::NT;
             if (c < G::N3) {
                 if (fast) {
-                    long long i = zoff + c_off[r];
+                    long long i = chk(zoff + c_off[r], n_cells(g));
                     cp_async8(stU + 0 * G::N3 + c, a.E + i);
                     cp_async8(stU + 1 * G::N3 + c, a.G[0] + i);
                     cp_async8(stU + 2 * G::N3 + c, a.G[1] + i);

@@ -86,6 +86,7 @@ __device__ __forceinline__ GasCell<float> gas_at(const GridParams& g, const Grid
     GasCell<float> c;
     c.T = 0.0;
     c.rho = 0.0;
+    li = chk(li, n_cells(g));
     const float r = __ldg(a.rho32 + li);
     c.rho32 = r;
     c.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, r);
@@ -199,7 +200,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     // once the copy has landed, by flip_ghosts) or, at a Dirichlet face, the face state truncated
     auto stage = [&](float4* d, int xr, int yr, int fl, int df, int off, int q, bool fast, long long zoff) {
         if (fast) {
-            cp_async16(d, a.um32 + zoff + off);
+            cp_async16(d, a.um32 + chk(zoff + off, n_cells(g)));
             return;
         }
         const int qr = ghost1(g, 2, q, true, fl, df);
@@ -233,7 +234,8 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
             int fl = gx_fl, df = -1;
             const int qr = ghost1(g, 2, q, false, fl, df);
             cp_async16(gsl + ((q + 3) % 3) * G::NT,
-                       a.gas4 + ((own_interior && (unsigned)q < (unsigned)g.n[2]) ? zoff + off_own : lin(g, gxr, gyr, qr)));
+                       a.gas4 + chk((own_interior && (unsigned)q < (unsigned)g.n[2]) ? zoff + off_own : lin(g, gxr, gyr, qr),
+                                    n_cells(g)));
         }
     };
     auto closure_xy = [&](int i, const float4& U, const ClosureScalars<float>& k) {
@@ -248,12 +250,16 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     };
     const float4* Um = Um0;  // the current plane's buffer
     auto xface = [&](int iL, int iR) {
+        iL = chk(iL, G::N1);
+        iR = chk(iR, G::N1);
         const float4 UL = Um[iL], UR = Um[iR], CL = CX[iL], CR = CX[iR];
         const float4 FL = make_float4(UL.y, CL.x, CL.y, CL.z);  // fluxes per unit chat
         const float4 FR = make_float4(UR.y, CR.x, CR.y, CR.z);
         return hll4(UL, UR, FL, FR, CL.w, L3[iL].x, CR.w, L3[iR].x, chat);
     };
     auto yface = [&](int iL, int iR) {
+        iL = chk(iL, G::N1);
+        iR = chk(iR, G::N1);
         const float4 UL = Um[iL], UR = Um[iR], CL = CY[iL], CR = CY[iR];
         const float4 FL = make_float4(UL.z, CL.x, CL.y, CL.z);
         const float4 FR = make_float4(UR.z, CR.x, CR.y, CR.z);
@@ -303,14 +309,14 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
         }
         __syncthreads();
         // x face left of the own cell, y face below it, then the tile's top row and right column
-        Fx[tly * (TX + 1) + tlx] = xface(i_own - 1, i_own);
-        Fy[tly * TX + tlx] = yface(i_own - G::W1, i_own);
+        Fx[chk(tly * (TX + 1) + tlx, G::NFX)] = xface(i_own - 1, i_own);
+        Fy[chk(tly * TX + tlx, G::NFY)] = yface(i_own - G::W1, i_own);
         if (t < TX) {
             const int iL = G::i1(t, TY - 1);
-            Fy[TY * TX + t] = yface(iL, iL + G::W1);
+            Fy[chk(TY * TX + t, G::NFY)] = yface(iL, iL + G::W1);
         } else if (t < TX + TY) {
             const int ly = t - TX, iL = G::i1(TX - 1, ly);
-            Fx[ly * (TX + 1) + TX] = xface(iL, iL + 1);
+            Fx[chk(ly * (TX + 1) + TX, G::NFX)] = xface(iL, iL + 1);
         }
         __syncthreads();
         // own cell: x/y divergence of plane q, z face (q-1 | q), U^{m+1/2} of plane q - 1.  No barrier
@@ -348,10 +354,11 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
                     gc.v[0] = (fl & 1) ? -gv.y : gv.y;
                     gc.v[1] = (fl & 2) ? -gv.z : gv.z;
                     gc.v[2] = (fl & 4) ? -gv.w : gv.w;
-                    const long long li = (long long)off_own + zoff - 2 * nxy;  // interior cells only (opt)
-                    gc.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, gv.x);
-                    gc.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, gv.x);
-                    gc.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
+                    // read only with the optional arrays, which take this branch for interior cells alone
+                    const long long li = (long long)off_own + zoff - 2 * nxy;
+                    gc.kP = a.kP32 ? __ldg(a.kP32 + chk(li, n_cells(g))) : kappa_law_f(g.f_kappa_P, g.kpow, gv.x);
+                    gc.kF = a.kF32 ? __ldg(a.kF32 + chk(li, n_cells(g))) : kappa_law_f(g.f_kappa_F, g.kpow, gv.x);
+                    gc.j = a.j32 ? __ldg(a.j32 + chk(li, n_cells(g))) : 0.0f;
                 } else {
                     gc = load_gas<float, true>(g, a, gx, gy, q - 1, needT, false);
                 }
@@ -366,7 +373,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
                 theta_updates(g, gc, chat, hdt, U);
                 const int fx_ = realize(U, g.f_E_floor);
                 if (own_interior && p >= 0 && p < g.n[2]) cnt.fix += fx_;
-                uh[uoff] = f4(U);
+                uh[chk(uoff, n_padded(g))] = f4(U);
             }
             zfl = zfh;
             zU = nU;
@@ -458,13 +465,15 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
                 const int c = t + r * G::NT;
                 if (c < G::N2) {
                     const unsigned dsm = c_dsm[r] + (buf ? buf_bytes : 0u);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dsm), "l"(base + c_gpos[r])
-                                 : "memory");
+                    const float4* src = uh + chk((base - uh) + c_gpos[r], n_padded(g));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dsm), "l"(src) : "memory");
                 }
             }
         }
     };
-    const int ihc = G::i2(tlx, tly);
+    // the own cell in the plane buffer; its x and y neighbours (+-1, +-W2) are read, so the index must
+    // lie in [W2, N2 - W2)
+    const int ihc = G::W2 + chk(G::i2(tlx, tly) - G::W2, G::N2 - 2 * G::W2);
     const int sx_own = G::sx(tlx, tly), sy_own = G::sy(tlx, tly);
     // this thread's halo record, if any
     const bool has_hr = t < G::NHR, hr_is_y = t < 2 * TX;
@@ -472,29 +481,34 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     if (has_hr) {
         if (hr_is_y) {
             const int ly = t < TX ? -1 : TY, lx = t % TX;
-            hr_i = G::i2(lx, ly);
+            hr_i = G::W2 + chk(G::i2(lx, ly) - G::W2, G::N2 - 2 * G::W2);
             hr_slot = G::sy(lx, ly);
         } else {
             const int hh = t - 2 * TX, ly = hh >> 1, lx = (hh & 1) ? TX : -1;
-            hr_i = G::i2(lx, ly);
+            hr_i = G::W2 + chk(G::i2(lx, ly) - G::W2, G::N2 - 2 * G::W2);
             hr_slot = G::sx(lx, ly);
         }
     }
     // the own column of U^{m+1/2} (clamped for columns beyond ragged tile edges, whose values are unused)
     const float4* colp = uh + (min(gx, g.n[0] + 1) + 2) + (long long)(g.n[0] + 4) * (min(gy, g.n[1] + 1) + 2);
-    auto col = [&](int k) { return colp[(long long)(k + 2) * pz]; };
+    auto col = [&](int k) { return uh[chk((colp - uh) + (long long)(k + 2) * pz, n_padded(g))]; };
     auto store_rec = [](float4* S, int n, int slot, const float4 (&rec)[4]) {
+        slot = chk(slot, n);
 #pragma unroll
         for (int v = 0; v < 4; ++v) S[v * n + slot] = rec[v];
     };
     // HLL at the face between record slots iL (its plus state) and iR (its minus state)
     auto hll_x = [&](int iL, int iR) {
+        iL = chk(iL, G::NSX);
+        iR = chk(iR, G::NSX);
         const float4 UL = Sx[G::NSX + iL], UR = Sx[iR];
         const float4 cL = Sx[2 * G::NSX + iL], cR = Sx[2 * G::NSX + iR];
         const float4 LL = Sx[3 * G::NSX + iL], LR = Sx[3 * G::NSX + iR];
         return hll_pair(UL, UR, flux_ab<0>(UL, cL.z, cL.w), flux_ab<0>(UR, cR.x, cR.y), LL.z, LL.w, LR.x, LR.y, chat);
     };
     auto hll_y = [&](int iL, int iR) {
+        iL = chk(iL, G::NSY);
+        iR = chk(iR, G::NSY);
         const float4 UL = Sy[G::NSY + iL], UR = Sy[iR];
         const float4 cL = Sy[2 * G::NSY + iL], cR = Sy[2 * G::NSY + iR];
         const float4 LL = Sy[3 * G::NSY + iL], LR = Sy[3 * G::NSY + iR];
@@ -542,7 +556,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
 #pragma unroll 1
     for (int k = z0; k < z1; ++k, li += nxy, next_plane += pz, colk2 += pz) {
         const int buf = (k - z0) & 1;
-        ukp2 = *colk2;
+        ukp2 = uh[chk(colk2 - uh, n_padded(g))];
         if constexpr (TMA) {
             // completion of this plane's copy: buffer buf's ((k - z0) >> 1)-th use, phase parity = that & 1
             const unsigned ph = ((k - z0) >> 1) & 1;
@@ -559,12 +573,13 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         }
         // the own cell's data of this plane, one commit group, awaited before the own-cell block
         if (own_col) {
-            cp_async8(oD + 0 * G::NT, a.E + li);
-            cp_async8(oD + 1 * G::NT, a.G[0] + li);
-            cp_async8(oD + 2 * G::NT, a.G[1] + li);
-            cp_async8(oD + 3 * G::NT, a.G[2] + li);
-            if (needT) cp_async8(oD + 4 * G::NT, a.T + li);
-            cp_async16(oG, a.gas4 + li);
+            const long long lc = chk(li, n_cells(g));
+            cp_async8(oD + 0 * G::NT, a.E + lc);
+            cp_async8(oD + 1 * G::NT, a.G[0] + lc);
+            cp_async8(oD + 2 * G::NT, a.G[1] + lc);
+            cp_async8(oD + 3 * G::NT, a.G[2] + lc);
+            if (needT) cp_async8(oD + 4 * G::NT, a.T + lc);
+            cp_async16(oG, a.gas4 + lc);
         }
         cp_async_commit();
         if (k + 1 < z1) issue_plane(next_plane, buf ^ 1, k + 1);
@@ -609,13 +624,13 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         }
         __syncthreads();
         // fluxes: the x face left of the own cell, the y face below it, then the tile's top row and right column
-        Cx[tly * (TX + 1) + tlx] = hll_x(sx_own - 1, sx_own);
-        Cy[tly * TX + tlx] = hll_y(sy_own - TX, sy_own);
+        Cx[chk(tly * (TX + 1) + tlx, G::NCX)] = hll_x(sx_own - 1, sx_own);
+        Cy[chk(tly * TX + tlx, G::NCY)] = hll_y(sy_own - TX, sy_own);
         if (t < TX) {
-            Cy[TY * TX + t] = hll_y(G::sy(t, TY - 1), G::sy(t, TY));
+            Cy[chk(TY * TX + t, G::NCY)] = hll_y(G::sy(t, TY - 1), G::sy(t, TY));
         } else if (t < TX + TY) {
             const int ly = t - TX;
-            Cx[ly * (TX + 1) + TX] = hll_x(G::sx(TX - 1, ly), G::sx(TX, ly));
+            Cx[chk(ly * (TX + 1) + TX, G::NCX)] = hll_x(G::sx(TX - 1, ly), G::sx(TX, ly));
         }
         __syncthreads();
         // own cell.  No barrier follows: every shared array written in the next plane is written after
@@ -638,9 +653,10 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             gc.v[0] = gv.y;
             gc.v[1] = gv.z;
             gc.v[2] = gv.w;
-            gc.kP = a.kP32 ? __ldg(a.kP32 + li) : kappa_law_f(g.f_kappa_P, g.kpow, rr);
-            gc.kF = a.kF32 ? __ldg(a.kF32 + li) : kappa_law_f(g.f_kappa_F, g.kpow, rr);
-            gc.j = a.j32 ? __ldg(a.j32 + li) : 0.0f;
+            const long long lo = chk(li, n_cells(g));
+            gc.kP = a.kP32 ? __ldg(a.kP32 + lo) : kappa_law_f(g.f_kappa_P, g.kpow, rr);
+            gc.kF = a.kF32 ? __ldg(a.kF32 + lo) : kappa_law_f(g.f_kappa_F, g.kpow, rr);
+            gc.j = a.j32 ? __ldg(a.j32 + lo) : 0.0f;
             const int fl = tly * (TX + 1) + tlx, fb = tly * TX + tlx;
             const float4 ax = Cx[fl], bxf = Cx[fl + 1], ay = Cy[fb], by = Cy[fb + TX];
             const float div[4] = {(bxf.x - ax.x) * idx + (by.x - ay.x) * idy + (cfh.x - cfl.x) * idz,
@@ -702,13 +718,13 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             const bool bad = !(finite_d(Un[0]) && finite_d(Un[1]) && finite_d(Un[2]) && finite_d(Un[3]) &&
                                (!full || finite_d(Tn)));
             cnt.nonfinite += bad;
-            a.Eo[li] = Un[0];
-            a.Go[0][li] = Un[1];
-            a.Go[1][li] = Un[2];
-            a.Go[2][li] = Un[3];
+            a.Eo[lo] = Un[0];
+            a.Go[0][lo] = Un[1];
+            a.Go[1][lo] = Un[2];
+            a.Go[2][lo] = Un[3];
             // the FP32 mirror of U^{m+1} for the next subcycle's predictor
-            a.um32[li] = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
-            if (full) a.T[li] = Tn;
+            a.um32[lo] = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
+            if (full) a.T[lo] = Tn;
         }
         cfl = cfh;
         ukp1 = ukp2;

@@ -17,10 +17,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librhd.so")
+# the same library with bounds-checked kernels (rhd_bounds_checked() = 1); pass it to lib() first
+DEBUG_LIB_PATH = os.path.join(_HERE, "librhd_debug.so")
 
-OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_CFL, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(9)
+OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_OOM, ERR_CFL, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_BOUNDS = range(10)
 STATUS_NAMES = {0: "RHD_OK", 1: "RHD_ERR_ARG", 2: "RHD_ERR_STATE", 3: "RHD_ERR_CUDA", 4: "RHD_ERR_OOM",
-                5: "RHD_ERR_CFL", 6: "RHD_ERR_NONFINITE", 7: "RHD_ERR_TIMEOUT", 8: "RHD_ERR_UNSUPPORTED"}
+                5: "RHD_ERR_CFL", 6: "RHD_ERR_NONFINITE", 7: "RHD_ERR_TIMEOUT", 8: "RHD_ERR_UNSUPPORTED",
+                9: "RHD_ERR_BOUNDS"}
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3}
 EXCHANGE = {"full": 0, "absorb": 1, "equilibrium": 2, "frozen_t": 3}
 LIMITER = {"minmod": 0, "mc": 1, "none": 2}
@@ -82,6 +85,7 @@ class Stats(ctypes.Structure):
         ("sum_E", ctypes.c_double),
         ("sum_F", ctypes.c_double * 3),
         ("max_f", ctypes.c_double),
+        ("bounds_violations", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -174,6 +178,7 @@ _SIGS = {
     "rhd_suggest_chat": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)]),
     "rhd_time_steps": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2
                        + [ctypes.POINTER(ctypes.c_int)]),
+    "rhd_bounds_checked": (ctypes.c_int, []),
     "rhd_abi_version": (ctypes.c_int, []),
     "rhd_built_arch": (ctypes.c_int, []),
 }
@@ -515,6 +520,9 @@ class Ensemble:
         if not (allow_nonfinite and st == ERR_NONFINITE):
             _check(self._ctx, st)
         return s.as_dict()
+
+    def reset_stats(self):
+        _check(self._ctx, lib().rhd_reset_stats(self._ctx))
 
     def synchronize(self, timeout_ms=-1):
         _check(self._ctx, lib().rhd_synchronize(self._ctx, int(timeout_ms)))
