@@ -167,20 +167,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-HOST_ONLY_SOURCES = ("rhd_api.cu", "rhd_noalloc.cu")
+# the sources the split path's kernels (predictor, corrector) are compiled from
+SPLIT_KERNEL_SOURCES = ("fp_convert.cuh", "k_split.cu", "rhd_internal.h", "subcycle.cuh", "subcycle_pair.cuh",
+                        "subcycle_twopass.cuh")
 
 
 def kernel_source_hash():
-    """SHA-256 over the CUDA sources that define or launch kernels (host-only API files excluded):
-    ncu traffic recorded for other kernel sources is stale."""
+    """SHA-256 over the sources of the split path's kernels: ncu traffic recorded for other kernel
+    sources is stale."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1306_0010_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")) and name not in HOST_ONLY_SOURCES:
-            h.update(name.encode())
-            h.update(open(os.path.join(d, name), "rb").read())
+    for name in SPLIT_KERNEL_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(d, name), "rb").read())
     return h.hexdigest()
 
 
