@@ -63,13 +63,13 @@ cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s)
     constexpr int TX = 32, TY = 8;
     const int zc = p.z_chunk;
     StepParams pp = p;
-    pp.tiles_x = (p.g.n[0] + 4 + TX - 1) / TX;
-    pp.tiles_y = (p.g.n[1] + 4 + TY - 1) / TY;
+    pp.tiles_x = (upad_extent(p.g, 0) + TX - 1) / TX;
+    pp.tiles_y = (upad_extent(p.g, 1) + TY - 1) / TY;
     auto k = predictor_kernel<TX, TY>;
     const size_t smem = GeoPred<TX, TY>::bytes();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)(pp.tiles_x * pp.tiles_y), (unsigned)((p.g.n[2] + 4 + zc - 1) / zc));
+    dim3 grid((unsigned)(pp.tiles_x * pp.tiles_y), (unsigned)((upad_extent(p.g, 2) + zc - 1) / zc));
     k<<<grid, TX * TY, smem, s>>>(pp);
     return cudaGetLastError();
 }
@@ -155,15 +155,16 @@ cudaError_t launch_to_gas4(float4* dst, const float* rho32, const float* vx, con
     return cudaGetLastError();
 }
 
-bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const int n[3])
+bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const GridParams& g)
 {
     auto enc = tensor_map_encoder();
-    if (!enc || !uhalf) return false;
+    if (!enc || !uhalf || !g.pad[0] || !g.pad[1]) return false;
     constexpr int TX = 32, TY = 8;
     using G = GeoCorr<TX, TY>;
-    // uhalf as floats: x = 4 (n0 + 4) floats per row, n1 + 4 rows, n2 + 4 planes; strides in bytes
-    const cuuint64_t dims[3] = {4ull * (n[0] + 4), (cuuint64_t)(n[1] + 4), (cuuint64_t)(n[2] + 4)};
-    const cuuint64_t strides[2] = {16ull * (n[0] + 4), 16ull * (n[0] + 4) * (n[1] + 4)};
+    // uhalf as floats: x = 4 (n0 + 4) floats per row, n1 + 4 rows, its stored planes; strides in bytes
+    const cuuint64_t e0 = upad_extent(g, 0), e1 = upad_extent(g, 1), e2 = upad_extent(g, 2);
+    const cuuint64_t dims[3] = {4ull * e0, e1, e2};
+    const cuuint64_t strides[2] = {16ull * e0, 16ull * e0 * e1};
     const cuuint32_t box[3] = {4u * G::W2, (cuuint32_t)G::H2, 1u};  // the tile + 2-cell halo of one plane
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, uhalf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -246,6 +246,7 @@ void fill_params(GridState& gs)
     g.f_kappa_P = (float)d.kappa_P;
     g.f_kappa_F = (float)d.kappa_F;
     for (int k = 0; k < 3; ++k) g.f_inv_dx[k] = (float)g.inv_dx[k];
+    for (int k = 0; k < 3; ++k) g.pad[k] = (d.bc_lo[k] == RHD_BC_PERIODIC && d.bc_hi[k] == RHD_BC_PERIODIC) ? 0 : 2;
     tile_shape(d.precision, g.nact, &gs.tx, &gs.ty);
     if (const char* ov = std::getenv("RHD_TILE")) {  // "TXxTY": measurement override of the tile shape
         int tx = 0, ty = 0;
@@ -326,7 +327,7 @@ rhd_status alloc_twopass(rhd_ctx* ctx, GridState& gs)
 {
     rhd_status st;
     if (!gs.uhalf) {
-        size_t np = (size_t)(gs.desc.n[0] + 4) * (gs.desc.n[1] + 4) * (gs.desc.n[2] + 4);
+        size_t np = (size_t)upad_extent(gs.gp, 0) * upad_extent(gs.gp, 1) * upad_extent(gs.gp, 2);
         if ((st = dalloc(ctx, (void**)&gs.uhalf, sizeof(float4) * np))) return st;
     }
     if (!gs.um32) {
@@ -770,11 +771,11 @@ rhd_status ens_prepare(rhd_ctx* ctx, double chat, const double* dt_per_grid, dou
             eg[i].tiles_z = (gs.desc.n[2] + gs.z_chunk - 1) / gs.z_chunk;
             eg[i].first_item = first;
             first += (long long)eg[i].tiles_x * eg[i].tiles_y * eg[i].tiles_z;
-            if (twopass) {  // predictor items: 32 x 8 tiles of the grid padded by two ghost layers
+            if (twopass) {  // predictor items: 32 x 8 tiles of the stored U^{m+1/2} (ghost layers included)
                 eg[i].uhalf = gs.uhalf;
-                eg[i].ptiles_x = (gs.desc.n[0] + 4 + 31) / 32;
-                eg[i].ptiles_y = (gs.desc.n[1] + 4 + 7) / 8;
-                eg[i].ptiles_z = (gs.desc.n[2] + 4 + gs.z_chunk - 1) / gs.z_chunk;
+                eg[i].ptiles_x = (upad_extent(gs.gp, 0) + 31) / 32;
+                eg[i].ptiles_y = (upad_extent(gs.gp, 1) + 7) / 8;
+                eg[i].ptiles_z = (upad_extent(gs.gp, 2) + gs.z_chunk - 1) / gs.z_chunk;
                 eg[i].first_pitem = pfirst;
                 pfirst += (long long)eg[i].ptiles_x * eg[i].ptiles_y * eg[i].ptiles_z;
             }
@@ -854,8 +855,10 @@ bool config_supported(const GridState& gs, const rhd_launch_config& c)
     const int nact = gs.gp.nact, prec = gs.desc.precision;
     if (c.z_chunk < 1) return false;
     if (c.variant == RHD_VARIANT_TWOPASS)
+        // TMA copies one box per plane, which cannot wrap around a periodic x or y
         return prec == RHD_SPLIT && nact == 3 && c.tile_x == 32 && c.tile_y == 8 &&
-               (c.staging == RHD_STAGING_CPASYNC || (c.staging == RHD_STAGING_TMA && tma_available()));
+               (c.staging == RHD_STAGING_CPASYNC ||
+                (c.staging == RHD_STAGING_TMA && tma_available() && gs.gp.pad[0] && gs.gp.pad[1]));
     if (c.variant != RHD_VARIANT_FUSED || c.staging != RHD_STAGING_CPASYNC) return false;
     return tile_supported(prec, nact, c.tile_x, c.tile_y);
 }
@@ -871,7 +874,7 @@ rhd_status apply_config(rhd_ctx* ctx, GridState& gs, const rhd_launch_config& c)
     }
     gs.um32_ok = false;
     if (c.staging == RHD_STAGING_TMA) {
-        gs.uh_map_ok = encode_uhalf_map(&gs.uh_map, gs.uhalf, gs.desc.n);
+        gs.uh_map_ok = encode_uhalf_map(&gs.uh_map, gs.uhalf, gs.gp);
         if (!gs.uh_map_ok) return fail(ctx, RHD_ERR_CUDA, "tensor map of U^{m+1/2} could not be encoded");
     } else {
         gs.uh_map_ok = false;

@@ -39,7 +39,13 @@ struct GridParams {
     double inv_c, gm1_mu;
     float f_inv_c, f_gm1_mu, f_c, f_a_rad, f_theta_F, f_theta_E, f_E_floor, f_kappa_P, f_kappa_F;
     float f_inv_dx[3];
+    // two-pass split path: ghost layers of U^{m+1/2} stored per direction, 2, or 0 where both faces are
+    // periodic (a periodic ghost value is the wrapped interior value, computed from the same cells)
+    int pad[3];
 };
+
+// extent of the stored U^{m+1/2} in direction d (two-pass split path)
+__host__ __device__ inline int upad_extent(const GridParams& g, int d) { return g.n[d] + 2 * g.pad[d]; }
 
 // Device arrays of one grid.  FP32 copies of the frozen inputs are used by the split path.
 struct GridArrays {
@@ -121,7 +127,7 @@ cudaError_t launch_to_gas4(float4* dst, const float* rho32, const float* vx, con
                            long long n, cudaStream_t s);
 // Encode the corrector's tensor map over a padded U^{m+1/2} array; false if the driver entry point is
 // missing or the encoding is refused.
-bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const int n[3]);
+bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const GridParams& g);
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 int ensemble_ctas_per_sm_fp64();

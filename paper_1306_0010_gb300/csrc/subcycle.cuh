@@ -321,7 +321,7 @@ __device__ __forceinline__ long long lin(const GridParams& g, int x, int y, int 
 __device__ __forceinline__ long long n_cells(const GridParams& g) { return (long long)g.n[0] * g.n[1] * g.n[2]; }
 __device__ __forceinline__ long long n_padded(const GridParams& g)
 {
-    return (long long)(g.n[0] + 4) * (g.n[1] + 4) * (g.n[2] + 4);
+    return (long long)upad_extent(g, 0) * upad_extent(g, 1) * upad_extent(g, 2);
 }
 
 // U^m = (E, Gx, Gy, Gz) at any cell, ghosts by the boundary rule.

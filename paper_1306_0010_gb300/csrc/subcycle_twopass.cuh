@@ -67,11 +67,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned ph, unsigned m
 }
 constexpr unsigned kMaxPolls = 1u << 22;
 
-// index of (x, y, z), each in [-2, n+2), in the padded U^{m+1/2} array
+// index of (x, y, z), each in [-pad, n + pad) of its direction, in the stored U^{m+1/2} array
 __device__ __forceinline__ long long pad_index(const GridParams& g, int x, int y, int z)
 {
-    const long long px = g.n[0] + 4, py = g.n[1] + 4;
-    return (long long)(x + 2) + px * ((long long)(y + 2) + py * (long long)(z + 2));
+    const long long px = upad_extent(g, 0), py = upad_extent(g, 1);
+    return (long long)(x + g.pad[0]) + px * ((long long)(y + g.pad[1]) + py * (long long)(z + g.pad[2]));
+}
+// stored position, in direction d, of the U^{m+1/2} of coordinate p in [-2, n + 2) (further beyond the
+// high face only for cells whose values are never used): p + 2 where ghost layers are stored, p wrapped
+// into [0, n) where both faces are periodic
+__device__ __forceinline__ int upad_pos(const GridParams& g, int d, int p)
+{
+    const int n = g.n[d];
+    return g.pad[d] ? min(p, n + 1) + 2 : ((p % n) + n) % n;
 }
 
 // Work layout shared by both kernels: every thread owns one cell (tlx, tly) of the tile; the loops
@@ -172,7 +180,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     const long long nxy = (long long)g.n[0] * g.n[1];
     const int tlx = t % TX, tly = t / TX;
     const int gx = x0 + tlx, gy = y0 + tly;
-    const bool own_in_pad = gx < g.n[0] + 2 && gy < g.n[1] + 2;
+    const bool own_in_pad = gx < g.n[0] + g.pad[0] && gy < g.n[1] + g.pad[1];
     const bool own_interior = gx >= 0 && gx < g.n[0] && gy >= 0 && gy < g.n[1];
     const bool has_h = t < G::NH;
     int hlx = 0, hly = 0;
@@ -272,7 +280,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     // running 64-bit offsets: the staged plane's, and the own cell's U^{m+1/2} at plane q - 1 in the
     // padded array
     long long zoff = (long long)qbeg * nxy;
-    const long long pzs = (long long)(g.n[0] + 4) * (g.n[1] + 4);
+    const long long pzs = (long long)upad_extent(g, 0) * upad_extent(g, 1);
     long long uoff = pad_index(g, gx, gy, qbeg - 1);  // negative before the first written plane
     issue_plane(qbeg, zoff, 0);
     zoff += nxy;
@@ -433,18 +441,18 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     const int tlx = t % TX, tly = t / TX;
     const int gx = x0 + tlx, gy = y0 + tly;
     const bool own_col = gx < g.n[0] && gy < g.n[1];
-    const long long pz = (long long)(g.n[0] + 4) * (g.n[1] + 4);
+    const long long pz = (long long)upad_extent(g, 0) * upad_extent(g, 1);
     const long long nxy = (long long)g.n[0] * g.n[1];
 
-    // the R2 plane of U^{m+1/2}: rows of W2 float4 starting at (x0 - 2, y0 + ly); all inside the padded array
-    // except beyond the high edges of ragged tiles, which are clamped (those values are never used)
+    // the R2 plane of U^{m+1/2}: rows of W2 float4 starting at (x0 - 2, y0 + ly), at their stored
+    // positions (ghost layers, or wrapped where the direction is periodic; beyond the high edges of
+    // ragged tiles clamped or wrapped, those values are never used)
     int c_gpos[G::NR2];
 #pragma unroll
     for (int r = 0; r < G::NR2; ++r) {
         const int c = t + r * G::NT;
         const int lx = c % G::W2 - 2, ly = c / G::W2 - 2;
-        const int xx = min(x0 + lx, g.n[0] + 1), yy = min(y0 + ly, g.n[1] + 1);
-        c_gpos[r] = (xx + 2) + (g.n[0] + 4) * (yy + 2);
+        c_gpos[r] = upad_pos(g, 0, x0 + lx) + upad_extent(g, 0) * upad_pos(g, 1, y0 + ly);
     }
     // shared-memory destinations of this thread's copies, for both buffers
     unsigned c_dsm[G::NR2];
@@ -457,7 +465,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             if (t == 0) {
                 fence_proxy_async();  // the buffer's earlier generic reads complete before the copy
                 mbar_arrive_expect_tx(mbar + buf, 16u * G::N2);
-                tma_load_3d(Ubuf + buf * G::N2, map, 4 * x0, y0, k + 2, mbar + buf);
+                tma_load_3d(Ubuf + buf * G::N2, map, 4 * x0, y0, k + g.pad[2], mbar + buf);
             }
         } else {
 #pragma unroll
@@ -490,8 +498,8 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         }
     }
     // the own column of U^{m+1/2} (clamped for columns beyond ragged tile edges, whose values are unused)
-    const float4* colp = uh + (min(gx, g.n[0] + 1) + 2) + (long long)(g.n[0] + 4) * (min(gy, g.n[1] + 1) + 2);
-    auto col = [&](int k) { return uh[chk((colp - uh) + (long long)(k + 2) * pz, n_padded(g))]; };
+    const long long colo = upad_pos(g, 0, gx) + (long long)upad_extent(g, 0) * upad_pos(g, 1, gy);
+    auto col = [&](int k) { return uh[chk(colo + (long long)upad_pos(g, 2, k) * pz, n_padded(g))]; };
     auto store_rec = [](float4* S, int n, int slot, const float4 (&rec)[4]) {
         slot = chk(slot, n);
 #pragma unroll
@@ -537,8 +545,12 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     long long li = own_col ? (long long)gx + (long long)g.n[0] * gy + (long long)z0 * nxy : 0;
     // running pointers (64-bit offsets advanced once per plane): the next plane to stage, and the
     // own column of U^{m+1/2} two planes ahead
-    const float4* next_plane = uh + (long long)(z0 + 2) * pz;
-    const float4* colk2 = colp + (long long)(z0 + 4) * pz;
+    const float4* next_plane = uh + (long long)(z0 + g.pad[2]) * pz;
+    // the own column two planes ahead (k + 2) as a running offset: stored plane zs2 (k + 4 with ghost
+    // layers, below n + 4; k + 2 wrapped into [0, n) where z is periodic)
+    int zs2 = z0 + 2 + g.pad[2];
+    if (zs2 >= upad_extent(g, 2)) zs2 -= g.n[2];
+    long long col2 = colo + (long long)zs2 * pz;
     if constexpr (TMA) {
         if (t == 0) {
             mbar_init(mbar + 0, 1);
@@ -554,9 +566,14 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     int fail_buf = 0;
     unsigned fail_ph = 0;
 #pragma unroll 1
-    for (int k = z0; k < z1; ++k, li += nxy, next_plane += pz, colk2 += pz) {
+    for (int k = z0; k < z1; ++k, li += nxy, next_plane += pz) {
         const int buf = (k - z0) & 1;
-        ukp2 = uh[chk(colk2 - uh, n_padded(g))];
+        ukp2 = uh[chk(col2, n_padded(g))];
+        col2 += pz;
+        if (++zs2 == upad_extent(g, 2)) {  // only where z is periodic
+            zs2 = 0;
+            col2 = colo;
+        }
         if constexpr (TMA) {
             // completion of this plane's copy: buffer buf's ((k - z0) >> 1)-th use, phase parity = that & 1
             const unsigned ph = ((k - z0) >> 1) & 1;
@@ -749,9 +766,9 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_kernel(
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tile = blockIdx.x;
-    const int x0 = (tile % P.tiles_x) * TX - 2, y0 = (tile / P.tiles_x) * TY - 2;
-    const int z0 = (int)blockIdx.y * P.z_chunk - 2;
-    const int z1 = min(z0 + P.z_chunk, P.g.n[2] + 2);
+    const int x0 = (tile % P.tiles_x) * TX - P.g.pad[0], y0 = (tile / P.tiles_x) * TY - P.g.pad[1];
+    const int z0 = (int)blockIdx.y * P.z_chunk - P.g.pad[2];
+    const int z1 = min(z0 + P.z_chunk, P.g.n[2] + P.g.pad[2]);
     Counters cnt = {0, 0, 0, 0, 0, 0};
     predictor_tile<TX, TY>(P.g, P.a, P.uhalf, P.f_chat, P.f_dt, x0, y0, z0, z1, reinterpret_cast<float4*>(smem_raw), cnt);
     add_counter(&P.stats->n_fix, cnt.fix);
@@ -825,8 +842,8 @@ __global__ void __launch_bounds__(TX* TY, RHD_PRED_MIN_BLOCKS) predictor_ens_ker
     while (ens_next<true>(P, eg, &item_s, &local)) {
         const long long nxy = (long long)eg.ptiles_x * eg.ptiles_y;
         const int txy = (int)(local % nxy), tz = (int)(local / nxy);
-        const int x0 = (txy % eg.ptiles_x) * TX - 2, y0 = (txy / eg.ptiles_x) * TY - 2;
-        const int z0 = tz * P.z_chunk - 2, z1 = min(z0 + P.z_chunk, eg.g.n[2] + 2);
+        const int x0 = (txy % eg.ptiles_x) * TX - eg.g.pad[0], y0 = (txy / eg.ptiles_x) * TY - eg.g.pad[1];
+        const int z0 = tz * P.z_chunk - eg.g.pad[2], z1 = min(z0 + P.z_chunk, eg.g.n[2] + eg.g.pad[2]);
         predictor_tile<TX, TY>(eg.g, eg.a, eg.uhalf, P.f_chat, eg.f_dt, x0, y0, z0, z1,
                                reinterpret_cast<float4*>(smem_raw), cnt);
         __syncthreads();

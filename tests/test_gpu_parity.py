@@ -202,8 +202,9 @@ def test_config4_reduced_split(rhd, variant, flags):
 def test_split_twopass_tma_staging(rhd):
     """The corrector's tile + 2-cell halo of U^{m+1/2} staged by one tensor (TMA) copy per plane:
     ragged tiles at the high x / y edges (the box reads past the array and is zero-filled there),
-    several z chunks, every boundary kind."""
-    case = wl.parity_case("tma", (37, 11, 23), bc=(["periodic", "outflow", "reflect"], ["periodic", "outflow", "outflow"]),
+    several z chunks, non-periodic x and y (a box cannot wrap) and a periodic z, whose planes are
+    stored without ghost layers."""
+    case = wl.parity_case("tma", (37, 11, 23), bc=(["reflect", "outflow", "periodic"], ["outflow", "reflect", "periodic"]),
                           exchange="full", beta_tau=True, with_j=True, n_sub=3, seed=19, precision="split")
     ref, _ = orc.subcycles(case)
     for zc in (1, 5, 23):
@@ -220,6 +221,30 @@ def test_split_twopass_tma_staging(rhd):
         st = g.get_stats()
         g.close()
         assert st["wait_timeouts"] == 0 and st["n_nonfinite"] == 0
+        e = errors(out, ref, case["desc"])
+        assert max(e.values()) <= SPLIT_TOL, (zc, e)
+    # with a periodic x or y the U^{m+1/2} ghost columns are not stored: TMA staging is refused
+    for bc in ("periodic", (["outflow", "periodic", "outflow"], ["outflow", "periodic", "outflow"])):
+        c2 = wl.parity_case("tma_per", (37, 11, 9), bc=bc, n_sub=1, seed=20, precision="split")
+        g = rhd.Grid(c2["desc"])
+        with pytest.raises(rhd.RhdError) as ei:
+            g.set_launch_config(dict(variant="twopass", tile=(32, 8), z_chunk=4, staging="tma"))
+        assert ei.value.status == rhd.ERR_ARG
+        g.close()
+
+
+@pytest.mark.parametrize("bc", ["periodic", (["periodic", "outflow", "periodic"], ["periodic", "reflect", "periodic"])],
+                         ids=["all_periodic", "xz_periodic"])
+def test_split_twopass_periodic_wrap(rhd, bc):
+    """Where both faces of a direction are periodic the U^{m+1/2} ghost layers are not stored and the
+    corrector reads the wrapped interior values: ragged tiles and z chunks, including chunks shorter
+    than the corrector's reach of two planes."""
+    case = wl.parity_case("wrap", (37, 11, 13), bc=bc, exchange="full", beta_tau=True, with_j=True, n_sub=3, seed=21,
+                          precision="split")
+    ref, _ = orc.subcycles(case)
+    for zc in (1, 2, 5, 13):
+        out, st = run_gpu(rhd, case, desc_over={"z_chunk": zc})
+        assert st["n_nonfinite"] == 0
         e = errors(out, ref, case["desc"])
         assert max(e.values()) <= SPLIT_TOL, (zc, e)
 
