@@ -564,7 +564,7 @@ def main():
     extra = {}
     if not args.no_fp64:
         fp_ms, fp_steps, fst, fkt, flaunch, _, _ = time_path(torch, rhd, case, "fp64", args.fp64_n_sub,
-                                                          max(2, args.steps // 2), args.warmup, stream, tune=False)
+                                                             max(2, args.steps // 2), args.warmup, stream)
         fn = max(2, args.steps // 2)
         if ws > 1:
             fp_ms = max_over_ranks(fp_ms, dist, device="cuda")

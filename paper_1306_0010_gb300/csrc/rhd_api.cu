@@ -906,10 +906,10 @@ std::vector<rhd_launch_config> grid_candidates(const GridState& gs)
         rhd_launch_config c = current_config(gs);
         add(c.variant, c.tile_x, c.tile_y, c.z_chunk, c.staging);
     } else if (gs.desc.precision == RHD_FP64) {
-        for (int zc : {8, 16, 32, 64, 128}) add(RHD_VARIANT_FUSED, 16, 8, zc, RHD_STAGING_CPASYNC);
+        for (int zc : {8, 16, 32, 64, 128, 256, 512}) add(RHD_VARIANT_FUSED, 16, 8, zc, RHD_STAGING_CPASYNC);
     } else {
         for (int stg : {RHD_STAGING_CPASYNC, RHD_STAGING_TMA})
-            for (int zc : {16, 32, 64}) add(RHD_VARIANT_TWOPASS, 32, 8, zc, stg);
+            for (int zc : {16, 32, 64, 128}) add(RHD_VARIANT_TWOPASS, 32, 8, zc, stg);
         const int tiles[3][2] = {{32, 8}, {32, 16}, {64, 8}};
         for (auto& t : tiles)
             for (int zc : {32, 64, 128}) add(RHD_VARIANT_FUSED, t[0], t[1], zc, RHD_STAGING_CPASYNC);
