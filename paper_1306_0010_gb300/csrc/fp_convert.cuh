@@ -1,5 +1,5 @@
-// fp_convert.cuh -- FP64 <-> FP32 conversions by integer bit operations (shared by the kernel
-// translation units).
+// fp_convert.cuh -- FP64 <-> FP32 conversions by integer bit operations, and the square roots and
+// reciprocals of the kernels (shared by the kernel translation units).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -29,6 +29,36 @@ __device__ __forceinline__ double f2d_exact(float f)
     lo = a < 0x00800000u ? 0u : lo;
     hi = a >= 0x7f800000u ? ((a >> 3) | 0x7ff00000u | sign) : hi;
     return __hiloint2double((int)hi, (int)lo);
+}
+
+// Square root and reciprocal.  Split path: the hardware approximations (MUFU, about 1-2 ulp), well
+// inside the FP32 error budget of the fluxes.  FP64 path: IEEE square root; the reciprocal is the
+// hardware FP64 approximation refined by two Newton-Raphson steps r <- r + r (1 - x r), each of which
+// squares the relative error (from below 2^-20 to below 2^-40, then to rounding): within an ulp or
+// two of 1/x, not the correctly rounded quotient, which the FP64 path does not need (its bound
+// against the oracle is 1e-12) and which costs several more FP64 operations.  x = 0, +-inf and FP64
+// denormals (flushed) give NaN.
+__device__ __forceinline__ double rsq(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsq(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 }  // namespace rhd

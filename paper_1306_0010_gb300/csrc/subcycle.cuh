@@ -46,22 +46,6 @@ struct Tol<float> {
     static constexpr float face = 1e-5f;
 };
 
-// Square root and reciprocal: IEEE in FP64; in the split path the hardware approximations
-// (MUFU, about 1-2 ulp), which are well inside the FP32 error budget of the fluxes.
-__device__ __forceinline__ double rsq(double x) { return sqrt(x); }
-__device__ __forceinline__ float rsq(float x)
-{
-    float r;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 // Index checks of the debug build (-DRHD_BOUNDS_CHECK, librhd_debug.so): chk(i, n) compares an index
 // with its array's extent; an index outside it is counted in this translation unit's device record
 // (with the source line, index and extent of the first one) and replaced by 0, so the access stays
