@@ -15,7 +15,7 @@ _c_int = ctypes.c_int
 _c_double = ctypes.c_double
 
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3}
-EXCHANGE = {"full": 0, "absorb": 1, "equilibrium": 2, "frozen_t": 3}
+EXCHANGE = {"full": 0, "absorb": 1, "equilibrium": 2, "frozen_t": 3, "linear": 4}
 LIMITER = {"minmod": 0, "mc": 1, "none": 2}
 CLOSURE = {"m1": 0, "p1": 1}
 SPEEDS = {"m1": 0, "fixed": 1}
@@ -44,6 +44,7 @@ class OrcParams(ctypes.Structure):
         ("kappa_P", _c_double),
         ("kappa_F", _c_double),
         ("kappa_rho_pow", _c_int),
+        ("linear_eps", _c_double),
     ]
 
 
@@ -82,6 +83,8 @@ def lib():
         L.orc_exchange_full.restype = _c_int
         L.orc_exchange_full.argtypes = [ctypes.POINTER(OrcParams), _c_double, _c_double, _c_double,
                                         _c_double, dp, dp]
+        L.orc_exchange_linear.restype = None
+        L.orc_exchange_linear.argtypes = [ctypes.POINTER(OrcParams), _c_double, _c_double, _c_double, dp, dp]
         args = [ctypes.POINTER(OrcParams), _c_int, _c_double, _c_double] + [dp] * 5 + [dp] * 7 + [
             ctypes.POINTER(OrcStats)]
         L.orc_subcycles.restype = _c_int
@@ -130,6 +133,7 @@ def params(desc) -> OrcParams:
     p.kappa_P = desc["kappa_P"]
     p.kappa_F = desc["kappa_F"]
     p.kappa_rho_pow = int(desc["kappa_rho_pow"])
+    p.linear_eps = float(desc.get("linear_eps", 1.0))
     return p
 
 
@@ -183,6 +187,15 @@ def exchange_full(desc, chat, dt, rho, kP, E, T):
     t = np.array([T], dtype=np.float64)
     fb = lib().orc_exchange_full(ctypes.byref(p), float(chat), float(dt), float(rho), float(kP), _dp(e), _dp(t))
     return float(e[0]), float(t[0]), int(fb)
+
+
+def exchange_linear(desc, chat, dt, kP, E, T):
+    """One linear (Pomraning material) exchange of a single cell; returns (E, T)."""
+    p = params(desc)
+    e = np.array([E], dtype=np.float64)
+    t = np.array([T], dtype=np.float64)
+    lib().orc_exchange_linear(ctypes.byref(p), float(chat), float(dt), float(kP), _dp(e), _dp(t))
+    return float(e[0]), float(t[0])
 
 
 # ----------------------------------------------------------------------------- grid functions

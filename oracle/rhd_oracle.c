@@ -213,6 +213,28 @@ int orc_exchange_full(const orc_params* p, double chat, double dt, double rho, d
  * Grid blocks with ghost layers
  * ---------------------------------------------------------------------------------------- */
 
+/* Eqs. (marshak:energyexchange) with c_v = alpha T^3 read in v = a_R T^4:
+ *   dv/dt = -eps c kP (v - E),   dE/dt = chat kP (v - E),   eps = 4 a_R / alpha
+ * (the paper writes the second row with chat = c).  Eqs. (marshak:update): with
+ * dtau = eps c kP dt, the theta-scheme step of v is dv = -(v - E) dtau / (1 + theta (1 + chat/(eps c)) dtau)
+ * (the paper's 1 + 1/eps at chat = c), and E changes by -(chat / (eps c)) dv, which keeps
+ * v / (eps c) + E / chat fixed (the paper's du = -dv / eps).  T follows from v (reading: v is kept
+ * >= 0, which theta < 1 need not do). */
+void orc_exchange_linear(const orc_params* p, double chat, double dt, double kP, double* E, double* T)
+{
+    double eps = p->linear_eps, c = p->c, theta = p->theta_E;
+    double v = p->a_rad * (*T) * (*T) * (*T) * (*T);
+    double u = *E;
+    double dtau = eps * c * kP * dt;
+    double dv = -(v - u) * dtau / (1.0 + theta * (1.0 + chat / (eps * c)) * dtau);
+    double du = -(chat / (eps * c)) * dv;
+    v = v + dv;
+    u = u + du;
+    if (v < 0.0) v = 0.0;
+    *E = u;
+    *T = sqrt(sqrt(v / p->a_rad));
+}
+
 typedef struct {
     int act[3];          /* direction active (n_d > 1) */
     int g[3];            /* ghost width: 3 in active directions, 0 otherwise */
@@ -594,10 +616,12 @@ static void run_block(work_t* w, double* Eo, double* Gxo, double* Gyo, double* G
                          * theta = 1 */
                         if (U[0] < p->E_floor) U[0] = p->E_floor;
                         n_theta += orc_exchange_full(p, chat, dt, w->rho[c], w->kP[c], &U[0], &Tn);
+                    } else if (p->exchange == ORC_EX_LINEAR) {
+                        orc_exchange_linear(p, chat, dt, w->kP[c], &U[0], &Tn);
                     }
                     n_fix += realizability(p, U);
                     if (!(isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]) &&
-                          (p->exchange != ORC_EX_FULL || isfinite(Tn))))
+                          ((p->exchange != ORC_EX_FULL && p->exchange != ORC_EX_LINEAR) || isfinite(Tn))))
                         n_nonfinite += 1;
                     long o = (long)(i - b->lo[0]) + nbx * ((long)(jy - b->lo[1]) + nby * (long)(k - b->lo[2]));
                     Eo[o] = U[0];
@@ -658,7 +682,7 @@ int orc_subcycle_box(const orc_params* p, double chat, double dt, const int lo[3
                      const double* kF, const double* j, orc_stats* stats)
 {
     if (check_params(p, chat, dt) || !E || !Fx || !Fy || !Fz || !rho) return 1;
-    if ((p->exchange == ORC_EX_FULL || p->exchange == ORC_EX_FROZEN_T) && !T) return 1;
+    if ((p->exchange == ORC_EX_FULL || p->exchange == ORC_EX_FROZEN_T || p->exchange == ORC_EX_LINEAR) && !T) return 1;
     int d;
     for (d = 0; d < 3; ++d)
         if (lo[d] < 0 || hi[d] > p->n[d] || lo[d] >= hi[d]) return 1;
@@ -689,7 +713,7 @@ int orc_subcycle_box(const orc_params* p, double chat, double dt, const int lo[3
                 Fx[gi] = p->c * out[nb + o];
                 Fy[gi] = p->c * out[2 * nb + o];
                 Fz[gi] = p->c * out[3 * nb + o];
-                if (T && p->exchange == ORC_EX_FULL) T[gi] = out[4 * nb + o];
+                if (T && (p->exchange == ORC_EX_FULL || p->exchange == ORC_EX_LINEAR)) T[gi] = out[4 * nb + o];
             }
     free(out);
     free_work(&w);
@@ -702,7 +726,7 @@ int orc_subcycles(const orc_params* p, int n_sub, double chat, double dt, double
                   const double* j, orc_stats* stats)
 {
     if (check_params(p, chat, dt) || n_sub < 0 || !E || !Fx || !Fy || !Fz || !rho) return 1;
-    if ((p->exchange == ORC_EX_FULL || p->exchange == ORC_EX_FROZEN_T) && !T) return 1;
+    if ((p->exchange == ORC_EX_FULL || p->exchange == ORC_EX_FROZEN_T || p->exchange == ORC_EX_LINEAR) && !T) return 1;
     long n = (long)p->n[0] * p->n[1] * p->n[2];
     int lo[3] = {0, 0, 0};
     int hi[3] = {p->n[0], p->n[1], p->n[2]};
@@ -735,7 +759,7 @@ int orc_subcycles(const orc_params* p, int n_sub, double chat, double dt, double
         const double* X[3] = {Ga[0], Ga[1], Ga[2]};
         load_block(&w, Ea, X, 1.0, Ta, rho, vin, kP, kF, j);
         run_block(&w, Eb, Gb[0], Gb[1], Gb[2], Tb, stats);
-        if (p->exchange != ORC_EX_FULL) memcpy(Tb, Ta, sizeof(double) * (size_t)n);
+        if (p->exchange != ORC_EX_FULL && p->exchange != ORC_EX_LINEAR) memcpy(Tb, Ta, sizeof(double) * (size_t)n);
         free_work(&w);
         /* swap */
         double* t;
@@ -748,7 +772,7 @@ int orc_subcycles(const orc_params* p, int n_sub, double chat, double dt, double
         Fx[i] = p->c * Ga[0][i];
         Fy[i] = p->c * Ga[1][i];
         Fz[i] = p->c * Ga[2][i];
-        if (T && p->exchange == ORC_EX_FULL) T[i] = Ta[i];
+        if (T && (p->exchange == ORC_EX_FULL || p->exchange == ORC_EX_LINEAR)) T[i] = Ta[i];
     }
     free(st);
     return 0;

@@ -23,7 +23,7 @@ extern "C" {
 #endif
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_OUTFLOW = 1, ORC_BC_REFLECT = 2, ORC_BC_DIRICHLET = 3 };
-enum { ORC_EX_FULL = 0, ORC_EX_ABSORB = 1, ORC_EX_EQUILIBRIUM = 2, ORC_EX_FROZEN_T = 3 };
+enum { ORC_EX_FULL = 0, ORC_EX_ABSORB = 1, ORC_EX_EQUILIBRIUM = 2, ORC_EX_FROZEN_T = 3, ORC_EX_LINEAR = 4 };
 enum { ORC_LIM_MINMOD = 0, ORC_LIM_MC = 1, ORC_LIM_NONE = 2 };
 enum { ORC_CLOSURE_M1 = 0, ORC_CLOSURE_P1 = 1 };
 enum { ORC_SPEEDS_M1 = 0, ORC_SPEEDS_FIXED = 1 };
@@ -39,6 +39,7 @@ typedef struct {
     int exchange, beta_tau, limiter, closure, speeds;
     double kappa_P, kappa_F;     /* opacity law used where kP / kF is NULL */
     int kappa_rho_pow;           /* 0, 1 or 2 */
+    double linear_eps;           /* ORC_EX_LINEAR: retardation eps = 4 a_R / alpha of c_v = alpha T^3 */
 } orc_params;
 
 typedef struct {
@@ -79,6 +80,11 @@ double orc_quartic_root(double c4, double c1, double c0);
  * a single cell over dt.  Updates *E and *T in place.  Returns 1 if the theta = 1 fallback was used. */
 int orc_exchange_full(const orc_params* p, double chat, double dt, double rho, double kP,
                       double* E, double* T);
+
+/* Linear exchange of the Pomraning material (Section 4.1.4: c_v = alpha T^3, so v = a_R T^4 is
+ * linear in the internal energy) of a single cell over dt, Eqs. (marshak:update) with chat in place
+ * of c in the radiation rows (reading): updates *E and *T in place. */
+void orc_exchange_linear(const orc_params* p, double chat, double dt, double kP, double* E, double* T);
 
 /* n_sub subcycles of the radiation update.  E, Fx, Fy, Fz (and T in FULL mode) are read and
  * overwritten.  vx, vy, vz, kP, kF, j may be NULL (zero velocity, opacity law, no emissivity).
