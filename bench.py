@@ -48,9 +48,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "ensemble"],
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "ensemble", "marshak"],
                     help="throughput: one 512^3 grid (the headline); ensemble: 64 independent grids of "
-                         "32^3..128^3, one persistent launch per subcycle, against per-grid plain launches")
+                         "32^3..128^3, one persistent launch per subcycle, against per-grid plain launches; "
+                         "marshak: the paper's timing benchmark, the 1D non-equilibrium Marshak wave to "
+                         "tau = 1, 10, 100 on N = 32 .. 2048 cells")
+    ap.add_argument("--marshak-cpu-cells", type=float, default=3e5,
+                    help="marshak: time the oracle only on runs of at most this many cell-updates")
     ap.add_argument("--n-grids", type=int, default=64)
     ap.add_argument("--traffic-from", default=None,
                     help="write profiles/traffic.json from this ncu raw CSV (measured at --N, scaled to 512^3; "
@@ -445,6 +449,75 @@ def time_per_grid(torch, rhd, cases, precision, n_sub, steps, warmup, stream):
     return ms
 
 
+def run_marshak(args):
+    """Section 4.2's benchmark: wall-clock time to reach tau on the Marshak wave (FP64 path, the host
+    driver setting the boundary from the Su & Olson quadrature before every subcycle, as the paper's
+    code does), for each N and tau; the oracle timed the same way on the runs it finishes quickly."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1306_0010_gb300 import build, rhd, workloads as wl
+
+    build.build()
+    rhd.lib()
+    Ns, taus = (32, 64, 128, 256, 512, 1024, 2048), (1.0, 10.0, 100.0)
+    # warm-up (first launches, library set-up)
+    w = wl.marshak_case(64)
+    g = rhd.Grid(dict(w["desc"], flags=rhd.FLAG_NO_GRAPH))
+    g.load_case(w)
+    g.marshak_advance(20, w["chat"], w["dt"], 0.0, w["marshak"])
+    g.synchronize()
+    g.close()
+    table = []
+    for N in Ns:
+        for tau in taus:
+            case = wl.marshak_case(N)
+            n_sub = wl.marshak_subcycles(tau, case)
+            g = rhd.Grid(dict(case["desc"], flags=rhd.FLAG_NO_GRAPH))
+            g.load_case(case)
+            g.synchronize()
+            t0 = time.perf_counter()
+            g.marshak_advance(n_sub, case["chat"], case["dt"], 0.0, case["marshak"])
+            g.synchronize()
+            el = time.perf_counter() - t0
+            g.close()
+            row = {"N": N, "tau": tau, "n_sub": n_sub, "gpu_s": el, "gpu_cell_updates_per_s": N * n_sub / el,
+                   "cpu_s": None}
+            if N * n_sub <= args.marshak_cpu_cells:
+                row["cpu_s"] = marshak_oracle_seconds(case, n_sub)
+            table.append(row)
+    big = table[-1]
+    line = {"metric": "non-equilibrium Marshak wave (Section 4.1.4): wall-clock time to reach tau", "value": big["gpu_s"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "1D Marshak wave, chi in [0, 100], rho = kappa_0 = 1, eps = 1, a_R = c = chat = 1, "
+                                   "F_inc = 1/4, linear exchange, theta = 1, CFL 0.4, boundary from the midpoint "
+                                   "quadrature (1024 points) before every subcycle; value: N = 2048, tau = 100",
+                       "N": big["N"], "tau": big["tau"]},
+            "table": table, "vs_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+def marshak_oracle_seconds(case, n_sub):
+    """The oracle driven like the library: the boundary state before every subcycle, one subcycle per call."""
+    import copy
+
+    from oracle import marshak, oracle as orc
+
+    c = copy.deepcopy(case)
+    m = c["marshak"]
+    t0 = time.perf_counter()
+    for k in range(n_sub):
+        tau = m["tau_rate"] * (k + 0.5) * c["dt"]
+        E_b, F_b = marshak.boundary_state(tau, m["eps"], m["F_inc"], c["desc"]["c"], 1024)
+        c["desc"]["dirichlet_lo"][0] = [E_b, F_b, 0.0, 0.0]
+        st, _ = orc.subcycles(c, n_sub=1)
+        c["fields"] = dict(c["fields"], E=st["E"], Fx=st["Fx"], Fy=st["Fy"], Fz=st["Fz"], T=st["T"])
+    return time.perf_counter() - t0
+
+
 def run_ensemble(args):
     import torch
 
@@ -508,6 +581,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "marshak":
+        return run_marshak(args)
     import torch
 
     ws, rank, lrank = dist_env()

@@ -75,7 +75,7 @@ typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_OUTFLOW = 1, RHD_BC_REFLECT = 2, RHD_
  *   EQUILIBRIUM radiative equilibrium: no exchange term
  *   FROZEN_T    absorption and emission against the fixed gas temperature,
  *               E <- [E(1-(1-theta)x) + x a_R T^4]/[1+theta x], in both stages */
-typedef enum { RHD_EX_FULL = 0, RHD_EX_ABSORB = 1, RHD_EX_EQUILIBRIUM = 2, RHD_EX_FROZEN_T = 3 } rhd_exchange;
+typedef enum { RHD_EX_FULL = 0, RHD_EX_ABSORB = 1, RHD_EX_EQUILIBRIUM = 2, RHD_EX_FROZEN_T = 3, RHD_EX_LINEAR = 4 } rhd_exchange;
 typedef enum { RHD_LIM_MINMOD = 0, RHD_LIM_MC = 1, RHD_LIM_NONE = 2 } rhd_limiter;
 typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_P1 = 1 } rhd_closure;     /* P1: T = I/3 (Section 2.3) */
 typedef enum { RHD_SPEEDS_M1 = 0, RHD_SPEEDS_FIXED = 1 } rhd_speeds;     /* FIXED: -+chat/sqrt(3) */
@@ -117,6 +117,9 @@ typedef struct {
     double kappa_P, kappa_F;    /* opacity law used where kP / kF arrays are not given: */
     int kappa_rho_pow;          /*   k = kappa * rho^p, p in {0, 1, 2} (absorption coefficients) */
     void* cuda_stream;          /* cudaStream_t to run on (NULL: legacy default stream, see above) */
+    double linear_eps;          /* RHD_EX_LINEAR only: retardation eps = 4 a_R / alpha (> 0) of the Pomraning
+                                   material c_v = alpha T^3 (Section 4.1.4); v = a_R T^4 and E relax by
+                                   Eqs. marshak:update, with chat in the radiation rows (T is updated) */
 } rhd_grid_desc;
 
 typedef struct {
@@ -346,6 +349,14 @@ rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, 
  * shared-memory indices of the two-pass kernels against their arrays' extents (a substitute for a
  * memory checker: an out-of-range index is counted and redirected to element 0, no trap), else 0. */
 int rhd_bounds_checked(void);
+
+/* Left-boundary state of the non-equilibrium Marshak wave (Section 4.1.4): E(0, t) from the Su & Olson
+ * surface value u(0, tau) of Eq. marshak:suolson at chi = 0 (integrals by the midpoint rule with n_quad
+ * points, as in the paper), F(0, t) from c E + 2 F = 4 F_inc (Eq. marshak:bc_ix1); tau = eps c rho kappa_0 t.
+ * state = (E, F, 0, 0), the Dirichlet state of the low x face (rhd_set_dirichlet face 0) for the
+ * subcycles starting at t.  Pure host arithmetic.  Errors: RHD_ERR_ARG (tau < 0, eps <= 0, F_inc < 0,
+ * c <= 0, n_quad < 1, non-finite input, NULL state). */
+rhd_status rhd_marshak_boundary(double tau, double eps, double F_inc, double c, int n_quad, double state[4]);
 
 /* Library identification: ABI version and the compute capability it was built for (e.g. 103). */
 int rhd_abi_version(void);

@@ -188,7 +188,9 @@ rhd_status validate_desc(rhd_ctx* ctx, const rhd_grid_desc* d)
         return fail(ctx, RHD_ERR_ARG, "theta must lie in (0, 1]");
     if (!finite_pos(d->E_floor)) return fail(ctx, RHD_ERR_ARG, "E_floor must be positive");
     if (!(d->cfl > 0 && d->cfl <= 1)) return fail(ctx, RHD_ERR_ARG, "cfl must lie in (0, 1]");
-    if (d->exchange < 0 || d->exchange > 3) return fail(ctx, RHD_ERR_ARG, "unknown exchange mode");
+    if (d->exchange < 0 || d->exchange > 4) return fail(ctx, RHD_ERR_ARG, "unknown exchange mode");
+    if (d->exchange == RHD_EX_LINEAR && !finite_pos(d->linear_eps))
+        return fail(ctx, RHD_ERR_ARG, "the linear exchange needs linear_eps > 0");
     if (d->limiter < 0 || d->limiter > 2) return fail(ctx, RHD_ERR_ARG, "unknown limiter");
     if (d->closure < 0 || d->closure > 1) return fail(ctx, RHD_ERR_ARG, "unknown closure");
     if (d->speeds < 0 || d->speeds > 1) return fail(ctx, RHD_ERR_ARG, "unknown wave-speed option");
@@ -230,6 +232,7 @@ void fill_params(GridState& gs)
     g.kappa_F = d.kappa_F;
     g.kpow = d.kappa_rho_pow;
     g.exchange = d.exchange;
+    g.linear_eps = d.linear_eps;
     g.beta_tau = d.beta_tau ? 1 : 0;
     g.limiter = d.limiter;
     g.closure = d.closure;
@@ -614,7 +617,8 @@ double alg_bytes_per_cell(const GridState& gs, int k)
     const double opt = w * ((gs.has_kP ? 1 : 0) + (gs.has_kF ? 1 : 0) + (gs.has_j ? 1 : 0));
     const double gas = w * (1 + (gs.has_v ? 3 : 0)) + opt;
     const int ex = gs.desc.exchange;
-    const double Tr = (ex == RHD_EX_FULL || ex == RHD_EX_FROZEN_T) ? 8.0 : 0.0, Tw = ex == RHD_EX_FULL ? 8.0 : 0.0;
+    const bool tw = ex == RHD_EX_FULL || ex == RHD_EX_LINEAR;
+    const double Tr = (tw || ex == RHD_EX_FROZEN_T) ? 8.0 : 0.0, Tw = tw ? 8.0 : 0.0;
     switch (k) {
     case K_PREDICTOR: return 16.0 + 16.0 + opt + (ex == RHD_EX_FROZEN_T ? 8.0 : 0.0) + 16.0;
     case K_CORRECTOR: return 16.0 + 32.0 + 16.0 + opt + Tr + 32.0 + Tw + 16.0;
@@ -855,8 +859,9 @@ bool config_supported(const GridState& gs, const rhd_launch_config& c)
     const int nact = gs.gp.nact, prec = gs.desc.precision;
     if (c.z_chunk < 1) return false;
     if (c.variant == RHD_VARIANT_TWOPASS)
-        // TMA copies one box per plane, which cannot wrap around a periodic x or y
-        return prec == RHD_SPLIT && nact == 3 && c.tile_x == 32 && c.tile_y == 8 &&
+        // TMA copies one box per plane, which cannot wrap around a periodic x or y; the linear
+        // exchange runs in the fused kernels only
+        return prec == RHD_SPLIT && nact == 3 && gs.desc.exchange != RHD_EX_LINEAR && c.tile_x == 32 && c.tile_y == 8 &&
                (c.staging == RHD_STAGING_CPASYNC ||
                 (c.staging == RHD_STAGING_TMA && tma_available() && gs.gp.pad[0] && gs.gp.pad[1]));
     if (c.variant != RHD_VARIANT_FUSED || c.staging != RHD_STAGING_CPASYNC) return false;
@@ -929,7 +934,7 @@ rhd_status tune_backup(rhd_ctx* ctx, TuneBackup& b)
     b.T.assign(ctx->grids.size(), nullptr);
     for (size_t i = 0; i < ctx->grids.size(); ++i) {
         GridState& gs = ctx->grids[i];
-        if (gs.desc.exchange != RHD_EX_FULL) continue;
+        if (gs.desc.exchange != RHD_EX_FULL && gs.desc.exchange != RHD_EX_LINEAR) continue;
         rhd_status st = dalloc(ctx, (void**)&b.T[i], sizeof(double) * (size_t)gs.ncell);
         if (st) return st;
         RHD_CUDA(ctx, cudaMemcpyAsync(b.T[i], gs.T, sizeof(double) * (size_t)gs.ncell, cudaMemcpyDeviceToDevice,
@@ -1255,7 +1260,7 @@ rhd_status rhd_init_grid(rhd_ctx** out, const rhd_grid_desc* d)
         gs.ncell = (long long)d->n[0] * d->n[1] * d->n[2];
         fill_params(gs);
         // split 3D grids: the two-pass kernels unless the fused kernel is asked for
-        if (d->precision == RHD_SPLIT && gs.gp.nact == 3) {
+        if (d->precision == RHD_SPLIT && gs.gp.nact == 3 && d->exchange != RHD_EX_LINEAR) {
             gs.variant = (d->flags & RHD_FLAG_SPLIT_FUSED) ? 0 : 1;
             if (const char* v = std::getenv("RHD_VARIANT")) gs.variant = std::strcmp(v, "fused") == 0 ? 0 : 1;
             // the two kernels recompute nothing across z chunks but two predictor planes: short chunks
@@ -1414,6 +1419,33 @@ rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, 
     *dt_gas = dg;
     *dt_rad = dg / n;
     *n_sub = n;
+    return RHD_OK;
+}
+
+rhd_status rhd_marshak_boundary(double tau, double eps, double F_inc, double c, int n_quad, double state[4])
+{
+    if (!state) return fail(nullptr, RHD_ERR_ARG, "state is NULL");
+    if (!(std::isfinite(tau) && tau >= 0.0) || !finite_pos(eps) || !(std::isfinite(F_inc) && F_inc >= 0.0) ||
+        !finite_pos(c) || n_quad < 1)
+        return fail(nullptr, RHD_ERR_ARG, "need tau >= 0, eps > 0, F_inc >= 0, c > 0, n_quad >= 1 (finite)");
+    // at chi = 0: sin(Theta) = 2 Gamma / sqrt(3 + 4 Gamma^2) since cos(Theta) = sqrt(3 / (3 + 4 Gamma^2))
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < n_quad; ++k) {
+        const double eta = (k + 0.5) / n_quad;
+        const double g1 = eta * std::sqrt(eps + 1.0 / (1.0 - eta * eta));
+        const double q1 = 3.0 + 4.0 * g1 * g1;
+        s1 += std::exp(-tau * eta * eta) * std::sin(std::acos(std::sqrt(3.0 / q1))) / (eta * std::sqrt(q1));
+        const double g2 = std::sqrt((1.0 - eta) * (eps + 1.0 / eta));
+        const double q2 = 3.0 + 4.0 * g2 * g2;
+        s2 += std::exp(-tau / (eps * eta)) * std::sin(std::acos(std::sqrt(3.0 / q2))) /
+              (eta * (1.0 + eps * eta) * std::sqrt(q2));
+    }
+    const double r3 = std::sqrt(3.0), pi = 3.14159265358979323846;
+    const double u = 1.0 - (2.0 * r3 / pi) * s1 / n_quad - (r3 / pi) * std::exp(-tau) * s2 / n_quad;
+    const double E = 4.0 * F_inc * u / c;
+    state[0] = E;
+    state[1] = (4.0 * F_inc - c * E) / 2.0;
+    state[2] = state[3] = 0.0;
     return RHD_OK;
 }
 

@@ -8,7 +8,7 @@
 namespace rhd {
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
-enum { EX_FULL = 0, EX_ABSORB = 1, EX_EQUILIBRIUM = 2, EX_FROZEN_T = 3 };
+enum { EX_FULL = 0, EX_ABSORB = 1, EX_EQUILIBRIUM = 2, EX_FROZEN_T = 3, EX_LINEAR = 4 };
 enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
 
 // Device-side event counters of the subcycles (zeroed by a reset).
@@ -33,6 +33,7 @@ struct GridParams {
     double c, a_rad, gamma, mu_over_kB;
     double theta_F, theta_E, E_floor;
     double kappa_P, kappa_F;
+    double linear_eps;          // EX_LINEAR: retardation eps = 4 a_R / alpha of the material c_v = alpha T^3
     int kpow;
     int exchange, beta_tau, limiter, closure, speeds;
     // derived on the host: 1/c, (gamma - 1) mu/k_B, and FP32 copies used by the split path

@@ -533,6 +533,23 @@ __device__ __forceinline__ ExchangeOut exchange_fp64(const GridParams& g, double
     return o;
 }
 
+// Linear exchange of the Pomraning material (c_v = alpha T^3, Section 4.1.4): Eqs. (marshak:update)
+// in v = a_R T^4 with dtau = eps c kP dt, dv = -(v - E) dtau / (1 + theta (1 + chat/(eps c)) dtau),
+// dE = -(chat / (eps c)) dv (the paper's chat = c gives 1 + 1/eps and -dv/eps), so v/(eps c) + E/chat
+// is kept; v is kept >= 0 and T follows from it.
+__device__ __forceinline__ void exchange_linear_fp64(const GridParams& g, double chat, double dt, double kP, double& E,
+                                                     double& T)
+{
+    const double eps = g.linear_eps, c = g.c;
+    double v = g.a_rad * T * T * T * T;
+    const double dtau = eps * c * kP * dt;
+    const double dv = -(v - E) * dtau / (1.0 + g.theta_E * (1.0 + chat / (eps * c)) * dtau);
+    E = E + (-(chat / (eps * c)) * dv);
+    v = v + dv;
+    if (v < 0.0) v = 0.0;
+    T = sqrt(sqrt(v / g.a_rad));
+}
+
 // FP32 Newton for delta with the same iteration, which also stops once a step is small enough that
 // the next could not change the FP32 result; the caller applies E - (chat/c) delta and T + q delta
 // to the FP64 state.
@@ -792,7 +809,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
         }
     };
     // fetch the FP64 state (and T) of the own tile cell of corrector plane k
-    const bool needT_corr = g.exchange == EX_FULL || g.exchange == EX_FROZEN_T;
+    const bool needT_corr = g.exchange == EX_FULL || g.exchange == EX_FROZEN_T || g.exchange == EX_LINEAR;
     auto issue_corr = [&](int k) {
         if (x0 + tlx0 < g.n[0] && y0 + tly0 < g.n[1] && (unsigned)k < (unsigned)g.n[2]) {
             long long i = lin(g, x0 + tlx0, y0 + tly0, k);
@@ -1130,7 +1147,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                 int ih = G::i2(tlx, tly);
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) Uhk[qq] = Uk[qq * G::N2 + ih];
-                const bool full = g.exchange == EX_FULL;
+                const bool full = g.exchange == EX_FULL, linear = g.exchange == EX_LINEAR;
                 GasCell<R> gc = load_gas<R, SPLIT>(g, a, gx, gy, k, false, full && !SPLIT);
                 R S[4];
                 explicit_sources(g, gc, Uhk, chat, S);
@@ -1161,6 +1178,8 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                         cnt.theta += o.theta_fb;
                         cnt.newton_fb += o.newton_fb;
                         cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
+                    } else if (linear) {
+                        exchange_linear_fp64(g, chat_d, dt_d, (double)gc.kP, U[0], Tn);
                     }
                     cnt.fix += realize(U, g.E_floor);
 #pragma unroll
@@ -1205,6 +1224,10 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                         cnt.theta += o.theta_fb;
                         cnt.newton_fb += o.newton_fb;
                         cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
+                    } else if (linear) {
+                        // the linear exchange in FP64 on the FP64 energy and temperature
+                        exchange_linear_fp64(g, chat_d, dt_d, (double)gc.kP, Etr, Tn);
+                        d[0] = d2f_trunc(Etr) - u0f[0];
                     }
                     Un[0] = Etr;
 #pragma unroll
@@ -1220,13 +1243,13 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
                     if (!(ef > g.f_E_floor * 1.001f) || g2f > 0.9999f * ef * ef) cnt.fix += realize(Un, g.E_floor);
                 }
                 bool bad = !(finite_d(Un[0]) && finite_d(Un[1]) && finite_d(Un[2]) && finite_d(Un[3]) &&
-                             (!full || finite_d(Tn)));
+                             (!(full || linear) || finite_d(Tn)));
                 cnt.nonfinite += bad;
                 a.Eo[li] = Un[0];
                 a.Go[0][li] = Un[1];
                 a.Go[1][li] = Un[2];
                 a.Go[2][li] = Un[3];
-                if (full) a.T[li] = Tn;
+                if (full || linear) a.T[li] = Tn;
             }
             if (DIM == 3) {
 #pragma unroll

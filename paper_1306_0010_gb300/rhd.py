@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "RHD_OK", 1: "RHD_ERR_ARG", 2: "RHD_ERR_STATE", 3: "RHD_ERR_C
                 5: "RHD_ERR_CFL", 6: "RHD_ERR_NONFINITE", 7: "RHD_ERR_TIMEOUT", 8: "RHD_ERR_UNSUPPORTED",
                 9: "RHD_ERR_BOUNDS"}
 BC = {"periodic": 0, "outflow": 1, "reflect": 2, "dirichlet": 3}
-EXCHANGE = {"full": 0, "absorb": 1, "equilibrium": 2, "frozen_t": 3}
+EXCHANGE = {"full": 0, "absorb": 1, "equilibrium": 2, "frozen_t": 3, "linear": 4}
 LIMITER = {"minmod": 0, "mc": 1, "none": 2}
 CLOSURE = {"m1": 0, "p1": 1}
 SPEEDS = {"m1": 0, "fixed": 1}
@@ -69,6 +69,7 @@ class GridDesc(ctypes.Structure):
         ("kappa_F", ctypes.c_double),
         ("kappa_rho_pow", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
+        ("linear_eps", ctypes.c_double),
     ]
 
 
@@ -179,6 +180,7 @@ _SIGS = {
     "rhd_time_steps": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2
                        + [ctypes.POINTER(ctypes.c_int)]),
     "rhd_bounds_checked": (ctypes.c_int, []),
+    "rhd_marshak_boundary": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rhd_abi_version": (ctypes.c_int, []),
     "rhd_built_arch": (ctypes.c_int, []),
 }
@@ -235,6 +237,7 @@ def desc_struct(d: dict, stream=None) -> GridDesc:
     s.kappa_F = d["kappa_F"]
     s.kappa_rho_pow = int(d["kappa_rho_pow"])
     s.cuda_stream = stream
+    s.linear_eps = float(d.get("linear_eps", 1.0))
     return s
 
 
@@ -327,6 +330,15 @@ class Grid:
         od = _same_residency(ps)
         _check(self._ctx, lib().rhd_get_moments(self._ctx, *[p for p, _ in ps], od))
         return {"E": E, "Fx": Fx, "Fy": Fy, "Fz": Fz}
+
+    def marshak_advance(self, n_sub, chat, dt, t0, marshak, n_quad=1024):
+        """n_sub subcycles of the non-equilibrium Marshak wave from time t0: before each, the low x face
+        gets the Marshak boundary state at the subcycle's midpoint tau (rhd_marshak_boundary)."""
+        c = float(self.desc["c"])
+        for m in range(int(n_sub)):
+            tau = marshak["tau_rate"] * (t0 + (m + 0.5) * dt)
+            self.set_dirichlet(0, marshak_boundary(tau, marshak["eps"], marshak["F_inc"], c, n_quad))
+            self.radiation_subcycle(1, chat, dt)
 
     def max_signal_speed(self):
         """v_max = max(|v| + c_eff) over the grid (Eq. algorithm:ceff), from the gas state and current E."""
@@ -574,3 +586,10 @@ def time_steps(cfl, dx_min, v_max, chat):
     _check(None, lib().rhd_time_steps(float(cfl), float(dx_min), float(v_max), float(chat), ctypes.byref(dg),
                                       ctypes.byref(dr), ctypes.byref(n)))
     return dg.value, dr.value, n.value
+
+
+def marshak_boundary(tau, eps, F_inc, c, n_quad=4096):
+    """(E, Fx, 0, 0) of the low x face of the Marshak wave at tau (Eqs. marshak:suolson, marshak:bc_ix1)."""
+    out = (ctypes.c_double * 4)()
+    _check(None, lib().rhd_marshak_boundary(float(tau), float(eps), float(F_inc), float(c), int(n_quad), out))
+    return tuple(out)

@@ -53,6 +53,7 @@ def base_desc(n, dx, bc="periodic", **kw):
         "kappa_rho_pow": 0,
         "cfl": 0.4,
         "precision": "fp64",
+        "linear_eps": 1.0,
     }
     d.update(kw)
     return d
@@ -343,3 +344,32 @@ def config5(n_grids=64, sizes=(32, 48, 64, 96, 128), n_sub=50, precision="split"
         cases.append({"name": f"config5_grid{i}_N{N}", "desc": desc, "fields": fields, "chat": 1.0,
                       "dt": cfl_dt(desc, 1.0), "n_sub": n_sub})
     return cases
+
+
+# ----------------------------------------------------------------------------- non-equilibrium Marshak wave
+
+def marshak_case(N, eps=1.0, precision="fp64", chi_max=100.0, F_inc=0.25, E_floor=1e-10):
+    """Section 4.1.4: a cold, static, absorbing slab chi = sqrt(3) rho kappa_0 x in [0, chi_max] with
+    rho = kappa_0 = 1, a_R = c = chat = 1, F_inc = 1/4 (so u = E and v = T^4), the linear exchange
+    of the Pomraning material with retardation eps, theta = 1.  E = E_floor and T = 0 initially (the
+    cold medium; E > 0 keeps the closure defined), F = 0.  The low x face is the Marshak boundary
+    (set before every subcycle from the Su & Olson surface value), the high face the Dirichlet state
+    (E_floor, 0).  tau = eps c rho kappa_0 t = eps t."""
+    L = chi_max / math.sqrt(3.0)
+    desc = base_desc((N, 1, 1), (L / N, 1.0, 1.0), bc="dirichlet", c=1.0, exchange="linear", kappa_P=1.0,
+                     kappa_F=1.0, kappa_rho_pow=1, theta_F=1.0, theta_E=1.0, E_floor=E_floor, precision=precision)
+    desc["linear_eps"] = float(eps)
+    desc["dirichlet_hi"] = [[E_floor, 0.0, 0.0, 0.0] for _ in range(3)]
+    desc["dirichlet_lo"] = [[E_floor, 0.0, 0.0, 0.0] for _ in range(3)]
+    shp = (1, 1, N)
+    fields = {"E": np.full(shp, E_floor), "Fx": np.zeros(shp), "Fy": np.zeros(shp), "Fz": np.zeros(shp),
+              "T": np.zeros(shp), "rho": np.ones(shp), "vx": None, "vy": None, "vz": None, "kP": None, "kF": None,
+              "j": None}
+    dt = desc["cfl"] * (L / N) / 1.0
+    return {"name": f"marshak_{N}", "desc": desc, "fields": fields, "chat": 1.0, "dt": dt, "n_sub": 1,
+            "marshak": {"eps": float(eps), "F_inc": F_inc, "tau_rate": float(eps) * 1.0 * 1.0 * 1.0}}
+
+
+def marshak_subcycles(tau_end, case):
+    """Subcycles of length case['dt'] that reach tau_end (the last one may end past it)."""
+    return int(math.ceil(tau_end / (case["marshak"]["tau_rate"] * case["dt"]) - 1e-12))

@@ -1,0 +1,61 @@
+"""GPU: the non-equilibrium Marshak wave (Section 4.1.4) through the library, the low x face set before
+every subcycle from the Su & Olson surface value, against the oracle run with the same boundary
+schedule: the linear (Pomraning) exchange, the time-dependent Dirichlet face and the 1D kernels."""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import marshak, oracle as orc
+from paper_1306_0010_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+N_QUAD = 1024
+
+
+@pytest.fixture(scope="module")
+def rhd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1306_0010_gb300 import build, rhd as binding
+
+    build.build()
+    binding.lib()
+    return binding
+
+
+def oracle_run(case, n_sub):
+    c = copy.deepcopy(case)
+    m = c["marshak"]
+    state = None
+    for k in range(n_sub):
+        tau = m["tau_rate"] * (k + 0.5) * c["dt"]
+        E_b, F_b = marshak.boundary_state(tau, m["eps"], m["F_inc"], c["desc"]["c"], N_QUAD)
+        c["desc"]["dirichlet_lo"][0] = [E_b, F_b, 0.0, 0.0]
+        state, _ = orc.subcycles(c, n_sub=1)
+        c["fields"] = dict(c["fields"], E=state["E"], Fx=state["Fx"], Fy=state["Fy"], Fz=state["Fz"], T=state["T"])
+    return state
+
+
+@pytest.mark.parametrize("precision,tol,N,tau,eps", [("fp64", 1e-12, 64, 10.0, 1.0), ("fp64", 1e-12, 100, 3.0, 0.5),
+                                                     ("split", 2e-5, 64, 10.0, 1.0)])
+def test_marshak_wave_matches_oracle(rhd, precision, tol, N, tau, eps):
+    case = wl.marshak_case(N, eps=eps, precision=precision)
+    n_sub = wl.marshak_subcycles(tau, case)
+    ref = oracle_run(case, n_sub)
+    g = rhd.Grid(dict(case["desc"], flags=rhd.FLAG_NO_GRAPH))
+    g.load_case(case)
+    g.marshak_advance(n_sub, case["chat"], case["dt"], 0.0, case["marshak"], n_quad=N_QUAD)
+    out = g.get_moments()
+    T = g.get_gas_state()
+    st = g.get_stats()
+    g.close()
+    assert st["n_nonfinite"] == 0 and st["n_subcycles"] == n_sub
+    sE = float(np.max(ref["E"]))
+    assert float(np.max(np.abs(out["E"] - ref["E"]))) <= tol * sE
+    assert float(np.max(np.abs(out["Fx"] - ref["Fx"]))) <= tol * case["desc"]["c"] * sE
+    assert float(np.max(np.abs(T - ref["T"]))) <= tol * float(np.max(ref["T"]))
+    # the wave has entered the slab: heated near the boundary, cold far away (v = T^4 with a_R = 1)
+    assert ref["T"][0, 0, 0] ** 4 > 0.1 and ref["T"][0, 0, -1] ** 4 < 1e-6
