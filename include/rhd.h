@@ -358,6 +358,16 @@ int rhd_bounds_checked(void);
  * c <= 0, n_quad < 1, non-finite input, NULL state). */
 rhd_status rhd_marshak_boundary(double tau, double eps, double F_inc, double c, int n_quad, double state[4]);
 
+/* n_sub subcycles of the Marshak wave from time t0, the low x face's Dirichlet state of subcycle m
+ * computed on the device by the same quadrature as rhd_marshak_boundary at tau = tau_rate (t0 + (m + 1/2) dt)
+ * (the subcycle's midpoint; tau_rate = eps c rho kappa_0): one launch computes all n_sub states (one block
+ * each, kept in a context buffer of 32 n_sub bytes), then one plain launch per subcycle reads its own.  Needs a single-grid context with
+ * a Dirichlet low x face, state set, and the fused kernels (FP64, or split with RHD_FLAG_SPLIT_FUSED or
+ * fewer than 3 dimensions).  Returns without synchronising.  Errors: RHD_ERR_ARG, RHD_ERR_CFL,
+ * RHD_ERR_STATE, RHD_ERR_UNSUPPORTED (two-pass split grid), RHD_ERR_OOM, RHD_ERR_CUDA. */
+rhd_status rhd_marshak_advance(rhd_ctx* ctx, int n_sub, double chat, double dt, double t0, double tau_rate,
+                               double eps, double F_inc, int n_quad);
+
 /* Library identification: ABI version and the compute capability it was built for (e.g. 103). */
 int rhd_abi_version(void);
 int rhd_built_arch(void);

@@ -109,4 +109,54 @@ cudaError_t launch_reduce_finish(const double* partials, int n_blocks, double* o
     return cudaGetLastError();
 }
 
+// Low x face of the non-equilibrium Marshak wave (Section 4.1.4) for a run of subcycles, one block per
+// subcycle m at tau = tau_rate (t0 + (m + 1/2) dt): the Su & Olson surface value u(0, tau) of
+// Eq. (marshak:suolson) at chi = 0, its two integrals by the midpoint rule over n points (thread-strided
+// partial sums, then a fixed tree), E = 4 F_inc u / c and F from c E + 2 F = 4 F_inc (Eq. marshak:bc_ix1);
+// out[4 m ..] = (E, F / c, 0, 0), the solver's (E, G) of the Dirichlet ghost cells of that subcycle.
+__global__ void marshak_boundary_kernel(double t0, double dt, double tau_rate, double eps, double F_inc, double c,
+                                        int n, double* out_all)
+{
+    const double tau = tau_rate * (t0 + (blockIdx.x + 0.5) * dt);
+    double* out = out_all + 4 * (long long)blockIdx.x;
+    __shared__ double sh1[RED_THREADS], sh2[RED_THREADS];
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < n; k += RED_THREADS) {
+        const double eta = (k + 0.5) / n;
+        const double g1 = eta * sqrt(eps + 1.0 / (1.0 - eta * eta));
+        const double q1 = 3.0 + 4.0 * g1 * g1;
+        s1 += exp(-tau * eta * eta) * sin(acos(sqrt(3.0 / q1))) / (eta * sqrt(q1));
+        const double g2 = sqrt((1.0 - eta) * (eps + 1.0 / eta));
+        const double q2 = 3.0 + 4.0 * g2 * g2;
+        s2 += exp(-tau / (eps * eta)) * sin(acos(sqrt(3.0 / q2))) / (eta * (1.0 + eps * eta) * sqrt(q2));
+    }
+    sh1[threadIdx.x] = s1;
+    sh2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh1[threadIdx.x] += sh1[threadIdx.x + w];
+            sh2[threadIdx.x] += sh2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double r3 = sqrt(3.0), pi = 3.14159265358979323846;
+        const double u = 1.0 - (2.0 * r3 / pi) * sh1[0] / n - (r3 / pi) * exp(-tau) * sh2[0] / n;
+        const double E = 4.0 * F_inc * u / c;
+        out[0] = E;
+        out[1] = ((4.0 * F_inc - c * E) / 2.0) / c;
+        out[2] = 0.0;
+        out[3] = 0.0;
+    }
+}
+
+cudaError_t launch_marshak_boundary(double t0, double dt, double tau_rate, double eps, double F_inc, double c,
+                                    int n_quad, int n_steps, double* out, cudaStream_t s)
+{
+    if (n_steps <= 0) return cudaSuccess;
+    marshak_boundary_kernel<<<n_steps, RED_THREADS, 0, s>>>(t0, dt, tau_rate, eps, F_inc, c, n_quad, out);
+    return cudaGetLastError();
+}
+
 }  // namespace rhd

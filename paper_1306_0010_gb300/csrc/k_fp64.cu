@@ -8,7 +8,8 @@ static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 {
     const size_t smem = tile_smem_bytes<R, TX, TY, DIM, SPLIT>();
     auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(p.tiles_x * p.tiles_y), DIM == 3 ? (unsigned)((p.g.n[2] + p.z_chunk - 1) / p.z_chunk) : 1u);
     k<<<grid, TX * TY, smem, s>>>(p);
@@ -20,7 +21,8 @@ static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaSt
 {
     const size_t smem = tile_smem_bytes<R, TX, TY, 3, SPLIT>();
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     k<<<n_ctas, TX * TY, smem, s>>>(p);
     return cudaGetLastError();

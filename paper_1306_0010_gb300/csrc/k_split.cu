@@ -10,7 +10,8 @@ static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
 {
     const size_t smem = tile_smem_bytes<R, TX, TY, DIM, SPLIT>();
     auto k = subcycle_kernel<R, TX, TY, DIM, SPLIT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(p.tiles_x * p.tiles_y), DIM == 3 ? (unsigned)((p.g.n[2] + p.z_chunk - 1) / p.z_chunk) : 1u);
     k<<<grid, TX * TY, smem, s>>>(p);
@@ -22,7 +23,8 @@ static cudaError_t launch_ens_kernel(const EnsembleParams& p, int n_ctas, cudaSt
 {
     const size_t smem = tile_smem_bytes<R, TX, TY, 3, SPLIT>();
     auto k = ensemble_kernel<R, TX, TY, SPLIT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     k<<<n_ctas, TX * TY, smem, s>>>(p);
     return cudaGetLastError();
@@ -67,7 +69,8 @@ cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s)
     pp.tiles_y = (upad_extent(p.g, 1) + TY - 1) / TY;
     auto k = predictor_kernel<TX, TY>;
     const size_t smem = GeoPred<TX, TY>::bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(pp.tiles_x * pp.tiles_y), (unsigned)((upad_extent(p.g, 2) + zc - 1) / zc));
     k<<<grid, TX * TY, smem, s>>>(pp);
@@ -90,7 +93,8 @@ cudaError_t launch_twopass_corrector(const StepParams& p, cudaStream_t s)
     };
     auto k = p.staging == 1 ? pick(std::true_type{}) : pick(std::false_type{});
     const size_t smem = GeoCorr<TX, TY>::bytes() + 128;  // + alignment slack for TMA destinations
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(pc.tiles_x * pc.tiles_y), (unsigned)((p.g.n[2] + zc - 1) / zc));
     k<<<grid, TX * TY, smem, s>>>(pc);
@@ -185,7 +189,8 @@ cudaError_t launch_ensemble_predictor(const EnsembleParams& p, int n_ctas, cudaS
 {
     auto k = predictor_ens_kernel<32, 8>;
     const size_t smem = GeoPred<32, 8>::bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     k<<<n_ctas, 256, smem, s>>>(p);
     return cudaGetLastError();
@@ -199,7 +204,8 @@ cudaError_t launch_ensemble_corrector(const EnsembleParams& p, int n_ctas, cudaS
              : lim == LIM_NONE ? corrector_ens_kernel<32, 8, LIM_NONE>
                                : corrector_ens_kernel<32, 8, LIM_MINMOD>;
     const size_t smem = GeoCorr<32, 8>::bytes();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static SmemLimitOnce smem_once;
+    cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     k<<<n_ctas, 256, smem, s>>>(p);
     return cudaGetLastError();

@@ -77,6 +77,7 @@ struct GridState {
     bool um32_ok = false, gas4_ok = false;
     CUtensorMap uh_map;           // its tensor map (staging RHD_STAGING_TMA), valid when uh_map_ok
     bool uh_map_ok = false;
+    const double* dir_dev = nullptr;  // low x Dirichlet state in device memory (rhd_marshak_advance only)
     bool tuned = false;           // RHD_FLAG_AUTOTUNE handled
     double tuned_ms = -1.0;       // time per subcycle measured by the last tuning
 };
@@ -96,6 +97,8 @@ struct rhd_ctx {
     DevStats* dstats = nullptr;
     double* red_partials = nullptr;
     double* rsla_partial = nullptr;  // reduced-speed-of-light reductions: rsla_blocks() + 1 doubles
+    double* marshak_state = nullptr;  // rhd_marshak_advance: low x Dirichlet states, 4 doubles per subcycle
+    int marshak_cap = 0;              // subcycles it holds
     double* red_out = nullptr;
     int red_blocks = 1;
     long long n_subcycles = 0;
@@ -401,6 +404,7 @@ void destroy_ctx(rhd_ctx* ctx)
     dfree(ctx->red_partials);
     dfree(ctx->red_out);
     dfree(ctx->rsla_partial);
+    dfree(ctx->marshak_state);
     dfree(ctx->d_egrids[0]);
     dfree(ctx->d_egrids[1]);
     dfree(ctx->d_counter);
@@ -552,6 +556,7 @@ StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double
     a.Eo = gs.U[1 - src][0];
     for (int d = 0; d < 3; ++d) a.Go[d] = gs.U[1 - src][1 + d];
     a.T = gs.T;
+    a.dir_dev = gs.dir_dev;
     a.rho = gs.rho;
     for (int d = 0; d < 3; ++d) {
         a.v[d] = gs.v[d];
@@ -1350,6 +1355,46 @@ rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double d
     if ((st = prepare_twopass(ctx, gs))) return st;
     bool use_graph = !(gs.desc.flags & RHD_FLAG_NO_GRAPH) && !ctx->ktiming;
     st = run_steps(ctx, n_sub, chat, dt, use_graph, [&](int src) { return launch_one(ctx, gs, src, chat, dt); });
+    if (st) return st;
+    ctx->cur = (ctx->cur + n_sub) & 1;
+    ctx->n_subcycles += n_sub;
+    return leave(ctx);
+}
+
+rhd_status rhd_marshak_advance(rhd_ctx* ctx, int n_sub, double chat, double dt, double t0, double tau_rate, double eps,
+                               double F_inc, int n_quad)
+{
+    ApiRange range_("rhd_marshak_advance");
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "not available on an ensemble context");
+    if (n_sub < 0 || n_quad < 1 || !std::isfinite(t0) || !finite_pos(tau_rate) || !finite_pos(eps) ||
+        !(std::isfinite(F_inc) && F_inc >= 0.0))
+        return fail(ctx, RHD_ERR_ARG, "need n_sub >= 0, n_quad >= 1, finite t0, tau_rate > 0, eps > 0, F_inc >= 0");
+    GridState& gs = ctx->grids[0];
+    rhd_status st = check_dt(ctx, gs, chat, dt);
+    if (st) return st;
+    if (!gs.has_moments || !gs.has_gas) return fail(ctx, RHD_ERR_STATE, "set the moments and the gas state first");
+    if (gs.desc.bc_lo[0] != RHD_BC_DIRICHLET) return fail(ctx, RHD_ERR_ARG, "the low x face must be Dirichlet");
+    if (gs.desc.precision == RHD_SPLIT && gs.variant == RHD_VARIANT_TWOPASS)
+        return fail(ctx, RHD_ERR_UNSUPPORTED, "the device boundary state is read by the fused kernels only");
+    if (n_sub == 0) return RHD_OK;
+    if ((st = enter(ctx))) return st;
+    if (ctx->marshak_cap < n_sub) {
+        // the stream may still read the old states: wait before replacing them
+        RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        dfree(ctx->marshak_state);
+        ctx->marshak_cap = 0;
+        if ((st = dalloc(ctx, (void**)&ctx->marshak_state, 4 * sizeof(double) * (size_t)n_sub))) return st;
+        ctx->marshak_cap = n_sub;
+    }
+    // every subcycle's boundary state at once (one block each), then the subcycles, each reading its own
+    RHD_CUDA(ctx, launch_marshak_boundary(t0, dt, tau_rate, eps, F_inc, gs.desc.c, n_quad, n_sub, ctx->marshak_state,
+                                          ctx->stream));
+    for (int m = 0; m < n_sub && !st; ++m) {
+        gs.dir_dev = ctx->marshak_state + 4 * (size_t)m;
+        st = launch_one(ctx, gs, (ctx->cur + m) & 1, chat, dt);
+    }
+    gs.dir_dev = nullptr;
     if (st) return st;
     ctx->cur = (ctx->cur + n_sub) & 1;
     ctx->n_subcycles += n_sub;

@@ -5,6 +5,8 @@
 #include <cuda.h>  // CUtensorMap (types only; the library does not link libcuda)
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 namespace rhd {
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2, BC_DIRICHLET = 3 };
@@ -69,6 +71,8 @@ struct GridArrays {
     float4* um32;               // U^m as FP32 (each component truncated toward zero): read by the predictor,
                                 // rewritten with U^{m+1} by the corrector
     const float4* gas4;         // (rho, vx, vy, vz) as FP32 per cell (the FP32 gas copies interleaved)
+    const double* dir_dev;      // non-NULL: the low x face's Dirichlet state (E, Gx, Gy, Gz) in device memory,
+                                // written by a kernel before each subcycle (fused kernels; else NULL)
 };
 
 struct StepParams {
@@ -111,6 +115,32 @@ struct EnsembleParams {
     int limiter;                // shared by all grids (the two-pass corrector is instantiated per limiter)
     unsigned long long* counter;  // work-queue head, reset before each launch
     DevStats* stats;
+};
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device) (a driver call, so not on every
+// launch).  One instance per launch site, which may choose among a few kernels of one size.
+struct SmemLimitOnce {
+    std::mutex m;
+    const void* fn[16] = {};
+    int dev_of[16] = {};
+    int n = 0;
+    template <typename K>
+    cudaError_t set(K k, size_t smem)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+        const void* f = reinterpret_cast<const void*>(k);
+        std::lock_guard<std::mutex> lock(m);
+        for (int i = 0; i < n; ++i)
+            if (fn[i] == f && dev_of[i] == dev) return cudaSuccess;
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && dev >= 0 && n < 16) {
+            fn[n] = f;
+            dev_of[n] = dev;
+            ++n;
+        }
+        return e;
+    }
 };
 
 // Launch wrappers (defined in the kernel translation units).
@@ -159,6 +189,10 @@ cudaError_t oob_read_fp64(OobRecord* out, int reset, cudaStream_t s);
 cudaError_t oob_read_split(OobRecord* out, int reset, cudaStream_t s);
 bool bounds_checked_fp64();
 bool bounds_checked_split();
+// Marshak boundary (k_aux.cu): block m writes (E, F/c, 0, 0) of the low x face at
+// tau = tau_rate (t0 + (m + 1/2) dt) into out[4 m .. 4 m + 3], m < n_steps
+cudaError_t launch_marshak_boundary(double t0, double dt, double tau_rate, double eps, double F_inc, double c,
+                                    int n_quad, int n_steps, double* out, cudaStream_t s);
 // reduced-speed-of-light helpers (k_rsla.cu): maxima over the grid into partial[nb] (partial holds nb + 1)
 int rsla_blocks(int num_sms);
 cudaError_t launch_signal_speed(const GridParams& g, const double* rho, const double* T, const double* E,

@@ -316,7 +316,7 @@ __device__ __forceinline__ void load_U(const GridParams& g, const GridArrays& a,
         int pos[3] = {x, y, z};
         int df = remap_cell(g, pos, sg, true);
         if (df >= 0) {
-            const double* s = (df & 1) ? g.dir_hi[df >> 1] : g.dir_lo[df >> 1];
+            const double* s = (df == 0 && a.dir_dev) ? a.dir_dev : ((df & 1) ? g.dir_hi[df >> 1] : g.dir_lo[df >> 1]);
             U[0] = s[0];
             U[1] = s[1];
             U[2] = s[2];

@@ -181,6 +181,7 @@ _SIGS = {
                        + [ctypes.POINTER(ctypes.c_int)]),
     "rhd_bounds_checked": (ctypes.c_int, []),
     "rhd_marshak_boundary": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "rhd_marshak_advance": (ctypes.c_int, [_P, ctypes.c_int] + [ctypes.c_double] * 6 + [ctypes.c_int]),
     "rhd_abi_version": (ctypes.c_int, []),
     "rhd_built_arch": (ctypes.c_int, []),
 }
@@ -332,13 +333,11 @@ class Grid:
         return {"E": E, "Fx": Fx, "Fy": Fy, "Fz": Fz}
 
     def marshak_advance(self, n_sub, chat, dt, t0, marshak, n_quad=1024):
-        """n_sub subcycles of the non-equilibrium Marshak wave from time t0: before each, the low x face
-        gets the Marshak boundary state at the subcycle's midpoint tau (rhd_marshak_boundary)."""
-        c = float(self.desc["c"])
-        for m in range(int(n_sub)):
-            tau = marshak["tau_rate"] * (t0 + (m + 0.5) * dt)
-            self.set_dirichlet(0, marshak_boundary(tau, marshak["eps"], marshak["F_inc"], c, n_quad))
-            self.radiation_subcycle(1, chat, dt)
+        """n_sub subcycles of the non-equilibrium Marshak wave from time t0, the low x face's state set on
+        the device before each from the Su & Olson surface value at the subcycle's midpoint tau."""
+        _check(self._ctx, lib().rhd_marshak_advance(self._ctx, int(n_sub), float(chat), float(dt), float(t0),
+                                                    float(marshak["tau_rate"]), float(marshak["eps"]),
+                                                    float(marshak["F_inc"]), int(n_quad)))
 
     def max_signal_speed(self):
         """v_max = max(|v| + c_eff) over the grid (Eq. algorithm:ceff), from the gas state and current E."""
