@@ -485,7 +485,17 @@ def run_marshak(args):
             el = time.perf_counter() - t0
             g.close()
             row = {"N": N, "tau": tau, "n_sub": n_sub, "gpu_s": el, "gpu_cell_updates_per_s": N * n_sub / el,
-                   "cpu_s": None}
+                   "gpu_split_s": None, "cpu_s": None}
+            # the same run on the split path (FP32 fluxes and closure, FP64 accumulation and exchange)
+            cs = wl.marshak_case(N, precision="split")
+            g = rhd.Grid(dict(cs["desc"], flags=rhd.FLAG_NO_GRAPH))
+            g.load_case(cs)
+            g.synchronize()
+            t0 = time.perf_counter()
+            g.marshak_advance(n_sub, cs["chat"], cs["dt"], 0.0, cs["marshak"])
+            g.synchronize()
+            row["gpu_split_s"] = time.perf_counter() - t0
+            g.close()
             if N * n_sub <= args.marshak_cpu_cells:
                 row["cpu_s"] = marshak_oracle_seconds(case, n_sub)
             table.append(row)
