@@ -74,7 +74,11 @@ typedef enum { RHD_BC_PERIODIC = 0, RHD_BC_OUTFLOW = 1, RHD_BC_REFLECT = 2, RHD_
  *               source:stiff:radenergy:soln), in both stages
  *   EQUILIBRIUM radiative equilibrium: no exchange term
  *   FROZEN_T    absorption and emission against the fixed gas temperature,
- *               E <- [E(1-(1-theta)x) + x a_R T^4]/[1+theta x], in both stages */
+ *               E <- [E(1-(1-theta)x) + x a_R T^4]/[1+theta x], in both stages
+ *   LINEAR      the Pomraning material of the Marshak wave (Section 4.1.4, c_v = alpha T^3): v = a_R T^4
+ *               and E relax by Eqs. marshak:update (linear_eps = 4 a_R / alpha), once per subcycle after
+ *               the corrector; updates T.  Runs in the fused kernels (split grids and ensembles with it
+ *               use them) */
 typedef enum { RHD_EX_FULL = 0, RHD_EX_ABSORB = 1, RHD_EX_EQUILIBRIUM = 2, RHD_EX_FROZEN_T = 3, RHD_EX_LINEAR = 4 } rhd_exchange;
 typedef enum { RHD_LIM_MINMOD = 0, RHD_LIM_MC = 1, RHD_LIM_NONE = 2 } rhd_limiter;
 typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_P1 = 1 } rhd_closure;     /* P1: T = I/3 (Section 2.3) */
@@ -84,10 +88,11 @@ typedef enum { RHD_SPEEDS_M1 = 0, RHD_SPEEDS_FIXED = 1 } rhd_speeds;     /* FIXE
 typedef enum { RHD_FP64 = 0, RHD_SPLIT = 1 } rhd_precision;
 /* RHD_FLAG_NO_GRAPH: issue the n_sub launches one by one instead of replaying a captured CUDA graph. */
 #define RHD_FLAG_NO_GRAPH 1
-/* RHD_FLAG_SPLIT_FUSED: for RHD_SPLIT grids with three active directions, run each subcycle as one
- * fused kernel (predictor recomputed on the tile halo) instead of the default predictor + corrector
- * pair, which keeps U^{m+1/2} in an extra FP32 buffer of (n0+4)(n1+4)(n2+4) x 16 bytes.  Ignored
- * elsewhere (ensembles always run fused). */
+/* RHD_FLAG_SPLIT_FUSED: for RHD_SPLIT grids (and ensembles) with three active directions, run each
+ * subcycle as one fused kernel (predictor recomputed on the tile halo) instead of the default
+ * predictor + corrector pair, which keeps U^{m+1/2} in an extra FP32 buffer of 16 bytes per cell of the
+ * grid with two ghost layers in each direction that is not periodic on both faces.  Ignored
+ * elsewhere. */
 #define RHD_FLAG_SPLIT_FUSED 2
 /* RHD_FLAG_AUTOTUNE: the first rhd_radiation_subcycle / rhd_ensemble_subcycle call runs the
  * autotuner (rhd_autotune / rhd_ensemble_autotune, 3 timed subcycles per candidate) on the state

@@ -1131,7 +1131,7 @@ rhd_status ensemble_autotune(rhd_ctx* ctx, double chat, const double* dt_per_gri
         if (v == RHD_VARIANT_TWOPASS) cand.push_back({v, 32, 8, zc, RHD_STAGING_CPASYNC, -1.0});
         else cand.push_back({v, g0.tx, g0.ty, zc, RHD_STAGING_CPASYNC, -1.0});
     };
-    if (split)
+    if (split && g0.desc.exchange != RHD_EX_LINEAR)
         for (int zc : {16, 32, 64}) add(RHD_VARIANT_TWOPASS, zc);
     for (int zc : {8, 16, 32, 64, 128}) add(RHD_VARIANT_FUSED, zc);
     const int v_before = g0.variant, zc_before = g0.z_chunk;
@@ -1607,8 +1607,10 @@ rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* 
             gs.desc = descs[i];
             gs.ncell = (long long)descs[i].n[0] * descs[i].n[1] * descs[i].n[2];
             fill_params(gs);
-            // split ensembles run the two-pass kernels unless descs[0] asks for the fused kernel
-            gs.variant = (descs[0].precision == RHD_SPLIT && !(descs[0].flags & RHD_FLAG_SPLIT_FUSED))
+            // split ensembles run the two-pass kernels unless descs[0] asks for the fused kernel (the
+            // linear exchange runs in the fused kernels only)
+            gs.variant = (descs[0].precision == RHD_SPLIT && !(descs[0].flags & RHD_FLAG_SPLIT_FUSED) &&
+                          descs[0].exchange != RHD_EX_LINEAR)
                              ? RHD_VARIANT_TWOPASS
                              : RHD_VARIANT_FUSED;
             st = alloc_grid(ctx, gs);

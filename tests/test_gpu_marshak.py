@@ -59,3 +59,38 @@ def test_marshak_wave_matches_oracle(rhd, precision, tol, N, tau, eps):
     assert float(np.max(np.abs(T - ref["T"]))) <= tol * float(np.max(ref["T"]))
     # the wave has entered the slab: heated near the boundary, cold far away (v = T^4 with a_R = 1)
     assert ref["T"][0, 0, 0] ** 4 > 0.1 and ref["T"][0, 0, -1] ** 4 < 1e-6
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("split", 2e-5)])
+def test_linear_exchange_3d_grid_and_ensemble(rhd, precision, tol):
+    """The linear exchange on 3D grids: a single grid (split grids with it take the fused kernel) and
+    an ensemble of two grids, against the oracle."""
+    cases = [wl.parity_case(f"lin{i}", n, bc="outflow", exchange="linear", beta_tau=False, kappa=3.0, n_sub=3,
+                            seed=150 + i, precision=precision) for i, n in enumerate([(20, 12, 10), (17, 9, 11)])]
+    for c in cases:
+        c["desc"]["linear_eps"] = 0.6
+    refs = [orc.subcycles(c)[0] for c in cases]
+
+    def errors(out, ref, c):
+        sE = float(np.max(ref["E"]))
+        e = max(float(np.max(np.abs(out[k] - ref[k]))) / (c["desc"]["c"] * sE) for k in ("Fx", "Fy", "Fz"))
+        e = max(e, float(np.max(np.abs(out["E"] - ref["E"]))) / sE)
+        return max(e, float(np.max(np.abs(out["T"] - ref["T"]))) / float(np.max(ref["T"])))
+
+    g = rhd.Grid(cases[0]["desc"])
+    if precision == "split":
+        assert g.launch_config()["variant"] == "fused"
+    g.load_case(cases[0])
+    g.radiation_subcycle(cases[0]["n_sub"], cases[0]["chat"], cases[0]["dt"])
+    out = dict(g.get_moments(), T=g.get_gas_state())
+    g.close()
+    assert errors(out, refs[0], cases[0]) <= tol
+    ens = rhd.Ensemble([c["desc"] for c in cases])
+    assert ens.launch_config()["variant"] == "fused"
+    for i, c in enumerate(cases):
+        ens.load_case(i, c)
+    ens.subcycle(3, cases[0]["chat"], [c["dt"] for c in cases])
+    for i, c in enumerate(cases):
+        out = dict(ens.get_moments(i), T=ens.get_gas_state(i))
+        assert errors(out, refs[i], c) <= tol, i
+    ens.close()
