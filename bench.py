@@ -177,15 +177,19 @@ SPLIT_KERNEL_SOURCES = ("fp_convert.cuh", "k_split.cu", "rhd_internal.h", "subcy
 
 
 def kernel_source_hash():
-    """SHA-256 over the sources of the split path's kernels: ncu traffic recorded for other kernel
-    sources is stale."""
+    """SHA-256 over the code of the split path's kernels (comments and whitespace removed): ncu
+    traffic recorded for other kernel code is stale."""
     import hashlib
+    import re
 
     d = os.path.join(ROOT, "paper_1306_0010_gb300", "csrc")
     h = hashlib.sha256()
     for name in SPLIT_KERNEL_SOURCES:
+        text = open(os.path.join(d, name), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
         h.update(name.encode())
-        h.update(open(os.path.join(d, name), "rb").read())
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

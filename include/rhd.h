@@ -233,8 +233,10 @@ rhd_status rhd_ensemble_subcycle(rhd_ctx* ctx, int n_sub, double chat, const dou
  * gives results within the error bound of its precision.
  *   variant   RHD_VARIANT_FUSED: one kernel per subcycle; the predictor (U^{m+1/2}) is recomputed
  *             on the 2-cell halo of each x-y tile.  RHD_VARIANT_TWOPASS (RHD_SPLIT, 3D grids only):
- *             a predictor kernel writes U^{m+1/2} (FP32) for the grid plus 2 ghost layers, then a
- *             corrector kernel reads it back; extra device memory (n0+4)(n1+4)(n2+4) x 16 bytes.
+ *             a predictor kernel writes U^{m+1/2} (FP32) for the grid plus 2 ghost layers per face
+ *             in each direction that is not periodic on both faces, then a corrector kernel reads
+ *             it back; extra device memory (n0+p0)(n1+p1)(n2+p2) x 16 bytes, p = 0 for a direction
+ *             periodic on both faces, else 4.
  *   tile_x, tile_y   cells per CTA tile in x and y (the supported shapes are those the tuner lists)
  *   z_chunk   planes per CTA along z (each CTA marches its tile through a chunk of planes)
  *   staging   RHD_STAGING_CPASYNC: the tile and its halo are staged into shared memory with per-

@@ -59,7 +59,7 @@ cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStrea
     return launch_ens_kernel<float, 32, 8, true>(p, n_ctas, s);
 }
 
-// Two-pass split subcycle (3D): predictor over the grid padded by two ghost layers, then corrector.
+// Two-pass split subcycle (3D): predictor over the grid and its stored ghost layers, then corrector.
 cudaError_t launch_twopass_predictor(const StepParams& p, cudaStream_t s)
 {
     constexpr int TX = 32, TY = 8;

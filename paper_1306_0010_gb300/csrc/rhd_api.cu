@@ -71,7 +71,7 @@ struct GridState {
     bool has_moments = false, has_gas = false;
     int variant = 0;              // RHD_VARIANT_FUSED / RHD_VARIANT_TWOPASS
     int staging = 0;              // RHD_STAGING_*
-    float4* uhalf = nullptr;      // two-pass: padded U^{m+1/2}
+    float4* uhalf = nullptr;      // two-pass: U^{m+1/2} with its ghost layers
     float4* um32 = nullptr;       // two-pass: FP32 mirror of the current state (valid when um32_ok)
     float4* gas4 = nullptr;       // two-pass: interleaved FP32 (rho, v) (valid when gas4_ok)
     bool um32_ok = false, gas4_ok = false;
@@ -327,7 +327,7 @@ void clear_graphs(rhd_ctx* ctx)
     ctx->graphs.clear();
 }
 
-// Buffers of the two-pass split path: U^{m+1/2} on the padded grid, the FP32 state mirror and the
+// Buffers of the two-pass split path: U^{m+1/2} with its ghost layers, the FP32 state mirror and the
 // interleaved FP32 gas (allocated once, kept until the variant changes).
 rhd_status alloc_twopass(rhd_ctx* ctx, GridState& gs)
 {

@@ -80,7 +80,7 @@ struct StepParams {
     GridArrays a;
     double chat, dt;
     float f_chat, f_dt;         // FP32 copies: FP32 code reads them as constant operands (no conversion)
-    float4* uhalf;              // two-pass split path: U^{m+1/2} on the grid padded by 2 ghost layers
+    float4* uhalf;              // two-pass split path: U^{m+1/2} on the grid plus its ghost layers (pad[])
     int z_chunk;                // planes per CTA
     int tx, ty;                 // tile shape (selects the kernel instantiation)
     int tiles_x, tiles_y;       // tile grid in x, y
@@ -97,8 +97,8 @@ struct EnsembleGrid {
     float f_dt;
     int tiles_x, tiles_y, tiles_z;
     long long first_item;       // prefix sum of tiles over the grids before this one
-    // two-pass ensembles: U^{m+1/2} of this grid (padded by 2 ghost layers) and the predictor's
-    // tiles over the padded grid, with their prefix sum
+    // two-pass ensembles: U^{m+1/2} of this grid (with its ghost layers, pad[]) and the
+    // predictor's tiles over that array, with their prefix sum
     float4* uhalf;
     int ptiles_x, ptiles_y, ptiles_z;
     long long first_pitem;
@@ -156,7 +156,7 @@ cudaError_t launch_to_um32(float4* dst, const double* E, const double* G0, const
 // interleaved FP32 gas: dst[i] = (rho32[i], vx[i], vy[i], vz[i]), absent velocity components zero
 cudaError_t launch_to_gas4(float4* dst, const float* rho32, const float* vx, const float* vy, const float* vz,
                            long long n, cudaStream_t s);
-// Encode the corrector's tensor map over a padded U^{m+1/2} array; false if the driver entry point is
+// Encode the corrector's tensor map over a stored U^{m+1/2} array (ghost layers in x and y); false if the driver entry point is
 // missing or the encoding is refused.
 bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const GridParams& g);
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);

@@ -301,7 +301,8 @@ __device__ __forceinline__ long long lin(const GridParams& g, int x, int y, int 
 #endif
     return (long long)x + (long long)g.n[0] * ((long long)y + (long long)g.n[1] * (long long)z);
 }
-// cells of the interior arrays and of the grid padded by two ghost layers (U^{m+1/2} of the two-pass path)
+// cells of the interior arrays and of the stored U^{m+1/2} of the two-pass path (grid plus its ghost
+// layers in the directions that are not periodic on both faces)
 __device__ __forceinline__ long long n_cells(const GridParams& g) { return (long long)g.n[0] * g.n[1] * g.n[2]; }
 __device__ __forceinline__ long long n_padded(const GridParams& g)
 {

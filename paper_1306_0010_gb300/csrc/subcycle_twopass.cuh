@@ -1,12 +1,13 @@
 // subcycle_twopass.cuh -- the split-precision subcycle for 3D grids as two kernels (included by
 // subcycle.cuh after subcycle_pair.cuh).
 //
-//   predictor kernel: U^{m+1/2} of every cell of the grid padded by two ghost layers (the ghost cells
+//   predictor kernel: U^{m+1/2} of every cell of the grid with its ghost layers (two per face in
+//     each direction that is not periodic on both faces; none in a periodic one) (the ghost cells
 //     are the predictor applied to the ghost values of U^m, exactly as in the fused kernel and the
 //     oracle), written as FP32 float4 (E, Gx, Gy, Gz);
 //   corrector kernel: reconstruction, face states, HLL, divergence, sources, exchange and
-//     realizability of the interior cells, reading U^{m+1/2} from the padded array (no boundary
-//     remapping is needed there) and the FP64 state, updating the FP64 state.
+//     realizability of the interior cells, reading U^{m+1/2} from the stored array (ghost positions,
+//     or wrapped indices in periodic directions) and the FP64 state, updating the FP64 state.
 // Each kernel marches column tiles through z.  Compared with the fused kernel the predictor is not
 // recomputed on the corrector's halo, and each kernel needs far less shared memory and far fewer
 // registers, so more warps are resident; the price is 32 bytes per cell of extra traffic (the FP32
@@ -110,7 +111,7 @@ __device__ __forceinline__ GasCell<float> gas_at(const GridParams& g, const Grid
 // outflow clamps; Dirichlet clamps too, or, when dir_ok and no earlier direction was Dirichlet,
 // records the face (2 d + high) in dface.  The ghost layers whose values the predictor uses are at
 // most three cells deep and active directions have n >= 3, so one step lands inside, as remap_cell's
-// loop does; cells farther out (beyond the padded grid in ragged tiles, values unused) are clamped
+// loop does; cells farther out (beyond the stored U^{m+1/2} in ragged tiles, values unused) are clamped
 // into the grid so that every access stays in bounds.
 __device__ __forceinline__ int ghost1(const GridParams& g, int d, int p, bool dir_ok, int& flip, int& dface)
 {
@@ -159,7 +160,8 @@ struct GeoPred {
     }
 };
 
-// Predictor over the padded column tile (x0, y0) (coordinates in [-2, n+2)) for planes [z0, z1).
+// Predictor over the column tile (x0, y0) of the stored U^{m+1/2} (coordinates in [-pad, n+pad))
+// for planes [z0, z1).
 template <int TX, int TY>
 __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridArrays& a, float4* uh, float chat,
                                                float dt, int x0, int y0, int z0, int z1, float4* sm, Counters& cnt)
@@ -278,7 +280,7 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
     float zl3 = 0.f;
     const int qbeg = z0 - 1, qend = z1 + 1;
     // running 64-bit offsets: the staged plane's, and the own cell's U^{m+1/2} at plane q - 1 in the
-    // padded array
+    // stored array
     long long zoff = (long long)qbeg * nxy;
     const long long pzs = (long long)upad_extent(g, 0) * upad_extent(g, 1);
     long long uoff = pad_index(g, gx, gy, qbeg - 1);  // negative before the first written plane
@@ -459,7 +461,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
 #pragma unroll
     for (int r = 0; r < G::NR2; ++r) c_dsm[r] = (unsigned)__cvta_generic_to_shared(Ubuf + t + r * G::NT);
     const unsigned buf_bytes = 16u * G::N2;
-    // base: the plane's first element in the padded array; k: the plane (TMA)
+    // base: the plane's first element in the stored U^{m+1/2}; k: the plane (TMA)
     auto issue_plane = [&](const float4* base, int buf, int k) {
         if constexpr (TMA) {
             if (t == 0) {
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(
 // ------------------------------------------------------------------------------------------------
 // persistent ensemble kernels: CTAs pull (grid, tile, z chunk) items from a global counter; the item
 // to grid map is a binary search over the grids' item prefix sums (predictor items cover each grid
-// padded by two ghost layers, corrector items its interior)
+// with its stored ghost layers, corrector items its interior)
 // ------------------------------------------------------------------------------------------------
 
 // Claim the next item; returns false when the queue is empty.  On true, eg holds the item's grid
