@@ -1,0 +1,343 @@
+"""The oracle's gas step (Section 3.1 steps 3 and 6, Section 3.4) against what the mathematics fixes:
+the exact Riemann solution of the Euler equations (Sod's problem), an exactly preserved stationary
+contact (which only a solver that restores the contact wave, HLLC, keeps), second-order convergence on
+smooth advection, conservation, closed-form time integrals of the gas sources and symmetries."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from oracle import gas
+
+
+def desc1(n, axis=0, bc="outflow", gamma=1.4, limiter="minmod", length=1.0, **kw):
+    nn = [1, 1, 1]
+    nn[axis] = n
+    d = {"n": tuple(nn), "dx": (length / nn[0], length / nn[1], length / nn[2]), "bc_lo": [bc] * 3,
+         "bc_hi": [bc] * 3, "gamma": gamma, "mu_over_kB": 1.0, "c": 100.0, "kappa_F": 0.0,
+         "kappa_rho_pow": 0, "limiter": limiter, "beta_tau": False}
+    d.update(kw)
+    return d
+
+
+def zero_rad(shp):
+    z = np.zeros(shp)
+    return {"E": z, "Fx": z, "Fy": z, "Fz": z}
+
+
+def state(rho, v, P):
+    shp = rho.shape
+    v = [np.broadcast_to(np.asarray(x, dtype=float), shp).copy() for x in v]
+    return {"rho": rho, "vx": v[0], "vy": v[1], "vz": v[2], "T": P / rho}
+
+
+def run(desc, g, t_end, cfl=0.4, rad=None):
+    rad = zero_rad(g["rho"].shape) if rad is None else rad
+    dxm = min(desc["dx"][d] for d in range(3) if desc["n"][d] > 1)
+    t = 0.0
+    while t < t_end * (1 - 1e-14):
+        P = g["rho"] * g["T"]
+        a = np.sqrt(desc["gamma"] * P / g["rho"])
+        vmax = float(np.max(np.sqrt(g["vx"] ** 2 + g["vy"] ** 2 + g["vz"] ** 2) + a))
+        dt = min(cfl * dxm / vmax, t_end - t)
+        g, pend, _ = gas.gas_step(desc, g, rad, dt)
+        g, _ = gas.gas_correct(desc, g, pend, rad)
+        t += dt
+    return g
+
+
+# ----------------------------------------------------------------------------- exact Riemann solver
+# Toro, "Riemann Solvers and Numerical Methods for Fluid Dynamics", Chapter 4 (pressure function,
+# star region, sampling), written here independently of the oracle.
+
+def exact_riemann(WL, WR, gamma, xi):
+    rL, uL, pL = WL
+    rR, uR, pR = WR
+    aL, aR = math.sqrt(gamma * pL / rL), math.sqrt(gamma * pR / rR)
+    g1, g2 = (gamma - 1) / (2 * gamma), (gamma + 1) / (2 * gamma)
+
+    def fK(p, r, pk, a):
+        if p > pk:
+            A, B = 2 / ((gamma + 1) * r), (gamma - 1) / (gamma + 1) * pk
+            return (p - pk) * math.sqrt(A / (p + B))
+        return 2 * a / (gamma - 1) * ((p / pk) ** g1 - 1)
+
+    ps = brentq(lambda p: fK(p, rL, pL, aL) + fK(p, rR, pR, aR) + uR - uL, 1e-14, 100 * max(pL, pR), xtol=1e-15)
+    us = 0.5 * (uL + uR) + 0.5 * (fK(ps, rR, pR, aR) - fK(ps, rL, pL, aL))
+    out = np.zeros((3, len(xi)))
+    for i, s in enumerate(xi):
+        if s <= us:
+            r, u, p, a, sg = rL, uL, pL, aL, 1.0
+        else:
+            r, u, p, a, sg = rR, uR, pR, aR, -1.0
+        # mirror the right side onto the left-side formulas (u -> -u, xi -> -xi)
+        u_, s_, us_ = sg * u, sg * s, sg * us
+        if ps > p:
+            S = u_ - a * math.sqrt(g2 * ps / p + g1)
+            if s_ <= S:
+                w = (r, u_, p)
+            else:
+                k = (gamma - 1) / (gamma + 1)
+                w = (r * (ps / p + k) / (k * ps / p + 1), us_, ps)
+        else:
+            SH, ast = u_ - a, a * (ps / p) ** g1
+            ST = us_ - ast
+            if s_ <= SH:
+                w = (r, u_, p)
+            elif s_ > ST:
+                w = (r * (ps / p) ** (1 / gamma), us_, ps)
+            else:
+                base = 2 / (gamma + 1) + (gamma - 1) / ((gamma + 1) * a) * (u_ - s_)
+                w = (r * base ** (2 / (gamma - 1)), 2 / (gamma + 1) * (a + (gamma - 1) / 2 * u_ + s_),
+                     p * base ** (2 * gamma / (gamma - 1)))
+        out[:, i] = (w[0], sg * w[1], w[2])
+    return out
+
+
+def sod(n, axis=0, limiter="minmod"):
+    d = desc1(n, axis=axis, limiter=limiter)
+    x = (np.arange(n) + 0.5) / n
+    shp = [1, 1, 1]
+    shp[2 - axis] = n
+    left = (x < 0.5).reshape(shp)
+    rho = np.where(left, 1.0, 0.125)
+    P = np.where(left, 1.0, 0.1)
+    v = [0.0, 0.0, 0.0]
+    g = run(d, state(rho, v, P), 0.2)
+    return d, g, x
+
+
+def test_sod_matches_the_exact_riemann_solution_and_converges():
+    errs = []
+    for n in (100, 200, 400):
+        d, g, x = sod(n)
+        ex = exact_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, (x - 0.5) / 0.2)
+        P = g["rho"] * g["T"]
+        e = [np.mean(np.abs(g["rho"].ravel() - ex[0])), np.mean(np.abs(g["vx"].ravel() - ex[1])),
+             np.mean(np.abs(P.ravel() - ex[2]))]
+        errs.append(e)
+    # first-order convergence in L1 at the discontinuities; the errors of a MUSCL-type scheme on Sod
+    e = np.array(errs)
+    assert e[1, 0] < 0.01 and e[1, 1] < 0.02 and e[1, 2] < 0.01, e
+    assert np.all(e[1] < 0.75 * e[0]) and np.all(e[2] < 0.75 * e[1]), e
+
+
+def test_sod_along_y_and_z_gives_the_same_bits():
+    _, gx, _ = sod(64, 0)
+    for axis, vkey in ((1, "vy"), (2, "vz")):
+        _, g, _ = sod(64, axis)
+        assert np.array_equal(g["rho"].ravel(), gx["rho"].ravel())
+        assert np.array_equal(g["T"].ravel(), gx["T"].ravel())
+        assert np.array_equal(g[vkey].ravel(), gx["vx"].ravel())
+
+
+def test_stationary_contact_is_kept_exactly():
+    # density jump at rest in uniform pressure: HLLC's star states reproduce it, HLL would smear it
+    n = 40
+    d = desc1(n, bc="reflect")
+    x = (np.arange(n) + 0.5) / n
+    rho = np.where(x < 0.37, 1.0, 0.3).reshape(1, 1, n)
+    g0 = state(rho, [0.0, 0.0, 0.0], np.ones_like(rho))
+    g = run(d, g0, 0.3)
+    assert np.max(np.abs(g["rho"] - rho)) <= 1e-15
+    assert np.max(np.abs(g["vx"])) <= 1e-15
+    assert np.max(np.abs(g["rho"] * g["T"] - 1.0)) <= 1e-15
+
+
+def test_hll_in_place_of_hllc_would_smear_the_contact():
+    # the same contact with the star-state branch removed (a planted mistake in a copy of the solver)
+    orig = gas.hllc
+
+    def hll_only(WL, WR, dd, gamma):
+        FL, EL = gas.euler_flux(WL, dd, gamma)
+        FR, ER = gas.euler_flux(WR, dd, gamma)
+        aL, aR = np.sqrt(gamma * WL[4] / WL[0]), np.sqrt(gamma * WR[4] / WR[0])
+        SL = np.minimum(WL[1 + dd] - aL, WR[1 + dd] - aR)
+        SR = np.maximum(WL[1 + dd] + aL, WR[1 + dd] + aR)
+        UL, UR = gas.conserved_from(WL, EL), gas.conserved_from(WR, ER)
+        return [(SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) / (SR - SL) for q in range(5)]
+
+    n = 40
+    d = desc1(n, bc="reflect")
+    x = (np.arange(n) + 0.5) / n
+    rho = np.where(x < 0.37, 1.0, 0.3).reshape(1, 1, n)
+    try:
+        gas.hllc = hll_only
+        g = run(d, state(rho, [0.0, 0.0, 0.0], np.ones_like(rho)), 0.3)
+    finally:
+        gas.hllc = orig
+    assert np.max(np.abs(g["rho"] - rho)) > 1e-2
+
+
+@pytest.mark.parametrize("dims", [1, 2])
+def test_smooth_advection_converges_at_second_order(dims):
+    errs = []
+    for n in (32, 64):
+        nn = (n, n if dims == 2 else 1, 1)
+        d = {"n": nn, "dx": (1.0 / n, 1.0 / n, 1.0), "bc_lo": ["periodic"] * 3, "bc_hi": ["periodic"] * 3,
+             "gamma": 5.0 / 3.0, "mu_over_kB": 1.0, "c": 100.0, "kappa_F": 0.0, "kappa_rho_pow": 0,
+             "limiter": "none", "beta_tau": False}
+        x = (np.arange(n) + 0.5) / n
+        y = (np.arange(nn[1]) + 0.5) / n if dims == 2 else np.zeros(1)
+        Y, X = np.meshgrid(y, x, indexing="ij")
+        phase = X + Y if dims == 2 else X
+        rho = (1.0 + 0.2 * np.sin(2 * np.pi * phase))[None]
+        v = [1.0, 1.0 if dims == 2 else 0.0, 0.0]
+        g = run(d, state(rho, v, np.ones_like(rho)), 1.0)
+        errs.append(np.mean(np.abs(g["rho"] - rho)))
+    assert errs[0] / errs[1] > 3.5, errs
+
+
+def random_gas(desc, seed, vamp=0.3):
+    r = np.random.default_rng(seed)
+    shp = (desc["n"][2], desc["n"][1], desc["n"][0])
+    rho = np.exp(r.normal(0, 0.3, shp))
+    T = np.exp(r.normal(0, 0.3, shp))
+    v = [r.normal(0, vamp, shp) if desc["n"][a] > 1 else r.normal(0, 0.1 * vamp, shp) for a in range(3)]
+    return {"rho": rho, "vx": v[0], "vy": v[1], "vz": v[2], "T": T}
+
+
+def random_rad(desc, seed):
+    r = np.random.default_rng(seed)
+    shp = (desc["n"][2], desc["n"][1], desc["n"][0])
+    E = r.uniform(0.5, 2.0, shp)
+    c = desc["c"]
+    return {"E": E, "Fx": 0.3 * c * E * r.uniform(-1, 1, shp), "Fy": 0.3 * c * E * r.uniform(-1, 1, shp),
+            "Fz": 0.3 * c * E * r.uniform(-1, 1, shp)}
+
+
+def totals(desc, g):
+    W = [g["rho"], g["vx"], g["vy"], g["vz"], g["rho"] * g["T"] / desc["mu_over_kB"]]
+    return np.array([float(np.sum(u)) for u in gas.conserved(desc, W)])
+
+
+def periodic3(n=(9, 7, 5), **kw):
+    d = {"n": n, "dx": (0.1, 0.12, 0.15), "bc_lo": ["periodic"] * 3, "bc_hi": ["periodic"] * 3, "gamma": 5.0 / 3.0,
+         "mu_over_kB": 1.0, "c": 10.0, "kappa_F": 0.0, "kappa_rho_pow": 0, "limiter": "minmod", "beta_tau": False}
+    d.update(kw)
+    return d
+
+
+def test_periodic_step_conserves_mass_momentum_and_energy():
+    d = periodic3()
+    g = random_gas(d, 1)
+    t0 = totals(d, g)
+    rad = zero_rad(g["rho"].shape)
+    for _ in range(3):
+        g, pend, fl = gas.gas_step(d, g, rad, 0.01)
+        g, _ = gas.gas_correct(d, g, pend, rad)
+        assert fl == 0
+    t1 = totals(d, g)
+    scale = np.array([t0[0], np.sum(np.abs(g["rho"] * g["vx"])), np.sum(np.abs(g["rho"] * g["vy"])),
+                      np.sum(np.abs(g["rho"] * g["vz"])), t0[4]])
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale), (t1 - t0) / scale
+
+
+def test_radiation_force_changes_total_momentum_by_the_closed_form():
+    # constant k_F, beta tau off: sum(rho v) gains dt k_F sum(G^n) in the step (any gas motion), and
+    # after the correction with G^{n+1}, dt k_F sum((G^n + G^{n+1}) / 2)
+    d = periodic3(kappa_F=2.5, kappa_rho_pow=0)
+    g = random_gas(d, 2)
+    r0, r1 = random_rad(d, 3), random_rad(d, 4)
+    t0 = totals(d, g)
+    dt = 0.01
+    g1, pend, _ = gas.gas_step(d, g, r0, dt)
+    t1 = totals(d, g1)
+    g2, _ = gas.gas_correct(d, g1, pend, r1)
+    t2 = totals(d, g2)
+    c = d["c"]
+    for a, k in enumerate(("Fx", "Fy", "Fz")):
+        G0, G1 = np.sum(r0[k]) / c, np.sum(r1[k]) / c
+        assert t1[1 + a] - t0[1 + a] == pytest.approx(dt * 2.5 * G0, rel=1e-11, abs=1e-13)
+        assert t2[1 + a] - t0[1 + a] == pytest.approx(dt * 2.5 * 0.5 * (G0 + G1), rel=1e-11, abs=1e-13)
+    # no O(beta tau) terms: the total gas energy only moves by the fluxes, which cancel
+    assert t2[4] == pytest.approx(t0[4], rel=1e-13)
+    assert t2[0] == pytest.approx(t0[0], rel=1e-14)
+
+
+def uniform_case(beta_tau, kpow=1, v0=(0.3, -0.2, 0.1)):
+    d = periodic3(n=(4, 3, 3), kappa_F=3.0, kappa_rho_pow=kpow, beta_tau=beta_tau, c=5.0)
+    shp = (3, 3, 4)
+    g = {"rho": np.full(shp, 1.7), "vx": np.full(shp, v0[0]), "vy": np.full(shp, v0[1]), "vz": np.full(shp, v0[2]),
+         "T": np.full(shp, 2.0)}
+    rad = {"E": np.full(shp, 4.0), "Fx": np.full(shp, 1.0), "Fy": np.full(shp, -2.0), "Fz": np.full(shp, 0.5)}
+    return d, g, rad
+
+
+def test_uniform_sources_follow_the_exact_ode_at_third_order_local_error():
+    # uniform gas and radiation: no fluxes; d(rho v)/dt = k (G - 4/3 v E / c), dE_gas/dt = -k v.G with
+    # rho and k constant: v(t) = v_inf + (v0 - v_inf) exp(-b t), b = 4 k E / (3 c rho), v_inf = 3 c G / (4 E)
+    d, g, rad = uniform_case(True)
+    k, rho, c, E = 3.0 * 1.7, 1.7, 5.0, 4.0
+    G = np.array([1.0, -2.0, 0.5]) / c
+    v0 = np.array([0.3, -0.2, 0.1])
+    b = 4 * k * E / (3 * c * rho)
+    vinf = 3 * c * G / (4 * E)
+    Eg0 = 1.7 * 2.0 / (2.0 / 3.0) + 0.5 * rho * float(v0 @ v0)
+    errs = []
+    for dt in (0.02, 0.01):
+        g1, pend, _ = gas.gas_step(d, g, rad, dt)
+        g1, _ = gas.gas_correct(d, g1, pend, rad)
+        v_ex = vinf + (v0 - vinf) * math.exp(-b * dt)
+        intv = vinf * dt + (v0 - vinf) * (1 - math.exp(-b * dt)) / b
+        Eg_ex = Eg0 - k * float(G @ intv)
+        v1 = np.array([g1["vx"][0, 0, 0], g1["vy"][0, 0, 0], g1["vz"][0, 0, 0]])
+        Eg1 = g1["rho"][0, 0, 0] * g1["T"][0, 0, 0] / (2.0 / 3.0) + 0.5 * rho * float(v1 @ v1)
+        errs.append((np.max(np.abs(v1 - v_ex)), abs(Eg1 - Eg_ex)))
+        assert np.all(g1["rho"] == 1.7)
+    for q in range(2):
+        ratio = errs[0][q] / errs[1][q]
+        assert 6.0 < ratio < 10.0, (q, errs)
+
+
+def test_correction_integrates_a_linear_radiation_history_exactly():
+    # beta tau off, uniform: rho v gains dt k (G^n + G^{n+1}) / 2, the exact integral of a force that
+    # varies linearly in time; E_gas is unchanged
+    d, g, r0 = uniform_case(False, kpow=0)
+    r1 = dict(r0, Fx=np.full_like(r0["Fx"], 3.0), Fy=np.full_like(r0["Fy"], 1.0))
+    dt = 0.05
+    g1, pend, _ = gas.gas_step(d, g, r0, dt)
+    g2, _ = gas.gas_correct(d, g1, pend, r1)
+    M = 1.7 * np.array([g2["vx"][0, 0, 0], g2["vy"][0, 0, 0], g2["vz"][0, 0, 0]])
+    M0 = 1.7 * np.array([0.3, -0.2, 0.1])
+    want = M0 + dt * 3.0 * 0.5 * (np.array([1.0, -2.0, 0.5]) + np.array([3.0, 1.0, 0.5])) / 5.0
+    assert np.allclose(M, want, rtol=1e-14, atol=1e-15)
+    Eg0 = 1.7 * 2.0 * 1.5 + 0.5 * 1.7 * 0.14
+    Eg2 = 1.7 * g2["T"][0, 0, 0] * 1.5 + 0.5 * float(M @ M) / 1.7
+    assert Eg2 == pytest.approx(Eg0, rel=1e-14)
+
+
+def test_reflect_walls_keep_a_mirror_symmetric_state_symmetric():
+    n = 24
+    d = {"n": (n, 10, 1), "dx": (1.0 / n, 0.1, 1.0), "bc_lo": ["reflect", "periodic", "periodic"],
+         "bc_hi": ["reflect", "periodic", "periodic"], "gamma": 1.4, "mu_over_kB": 1.0, "c": 10.0, "kappa_F": 0.0,
+         "kappa_rho_pow": 0, "limiter": "mc", "beta_tau": False}
+    x = (np.arange(n) + 0.5) / n
+    y = (np.arange(10) + 0.5) / 10
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    rho = (1.0 + 0.5 * np.exp(-((X - 0.5) ** 2) / 0.01) * (1 + 0.3 * np.sin(2 * np.pi * Y)))[None]
+    vx = (0.2 * np.sin(2 * np.pi * (X - 0.5)))[None]  # odd about x = 1/2
+    g = run(d, state(rho, [vx, 0.0, 0.0], np.ones_like(rho)), 0.1)
+    assert np.max(np.abs(g["rho"] - g["rho"][:, :, ::-1])) < 1e-13
+    assert np.max(np.abs(g["vx"] + g["vx"][:, :, ::-1])) < 1e-13
+
+
+def test_swapping_x_and_y_swaps_the_result():
+    d = {"n": (12, 12, 1), "dx": (0.1, 0.1, 1.0), "bc_lo": ["outflow", "outflow", "periodic"],
+         "bc_hi": ["reflect", "reflect", "periodic"], "gamma": 1.4, "mu_over_kB": 1.0, "c": 10.0, "kappa_F": 1.5,
+         "kappa_rho_pow": 1, "limiter": "minmod", "beta_tau": True}
+    r = np.random.default_rng(7)
+    A = np.exp(r.normal(0, 0.3, (12, 12)))
+    rho = (A + A.T)[None]
+    T = np.ones_like(rho)
+    vx = r.normal(0, 0.2, (12, 12))
+    g0 = {"rho": rho, "vx": vx[None], "vy": vx.T[None].copy(), "vz": np.zeros_like(rho), "T": T}
+    E = (A * A.T)[None]
+    Fx = 0.2 * r.uniform(-1, 1, (12, 12))
+    rad = {"E": E, "Fx": Fx[None], "Fy": Fx.T[None].copy(), "Fz": np.zeros_like(rho)}
+    g, pend, _ = gas.gas_step(d, g0, rad, 0.02)
+    g, _ = gas.gas_correct(d, g, pend, rad)
+    assert np.max(np.abs(g["rho"][0] - g["rho"][0].T)) < 1e-13
+    assert np.max(np.abs(g["vx"][0] - g["vy"][0].T)) < 1e-13
+    assert np.max(np.abs(g["T"][0] - g["T"][0].T)) < 1e-13
