@@ -283,6 +283,34 @@ def time_rsla(torch, g, case, stream, hbm_peak, reps=5):
     return out
 
 
+def time_gas(torch, g, case, stream, hbm_peak, reps=3):
+    """The gas step (Section 3.1 step 3) and its source correction (step 6) on the same grid, after the
+    radiation legs: dt_gas = 0.1 min(dx) (a Courant number near 0.2 for this gas), one untimed step
+    (scratch allocation), then `reps` timed (step, correction) pairs with CUDA events on the library's
+    stream and the kernel timer.  Rate: interior cells advanced per second of (step + correction)."""
+    dx = min(case["desc"]["dx"][d] for d in range(3) if case["desc"]["n"][d] > 1)
+    dt = 0.1 * dx
+    cells = int(np.prod(case["fields"]["rho"].shape))
+    g.gas_step(dt)
+    g.gas_correct()
+    stream.synchronize()
+    g.kernel_times()  # discard
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for r in range(reps):
+        g.gas_step(dt)
+        g.gas_correct()
+        ev[r + 1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[-1]) / reps
+    kt = g.kernel_times()
+    st = g.get_stats(allow_nonfinite=True)
+    return {"value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_gas_step": ms, "dt_gas": dt,
+            "kernels": kt, "roofline": kernel_roofline(kt, hbm_peak, "measured"),
+            "gpu_launches": sum(v["launches"] for v in kt.values()) // reps,
+            "gas_energy_floors": st["gas_energy_floors"], "gas_nonfinite": st["gas_nonfinite"]}
+
+
 def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=True, launch_spec="auto",
               rsla_peak=None):
     """Device-resident run: autotune the launch configuration (untimed), warm up, then time `steps`
@@ -321,6 +349,10 @@ def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=Tr
     st = g.get_stats(allow_nonfinite=True)
     g.set_kernel_timing(False)
     rsla = time_rsla(torch, g, case, stream, rsla_peak) if rsla_peak else None
+    if rsla is not None:
+        g.set_kernel_timing(True)
+        rsla["gas_step"] = time_gas(torch, g, case, stream, rsla_peak)
+        g.set_kernel_timing(False)
     g.close()
     del dev
     return total_ms, per_step_ms, st, kt, launch, tuning, rsla
@@ -691,6 +723,7 @@ def main():
                 "e2e": e2e, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clocks,
                 "subcycle_roofline": subcycle_roofline, "alu_roofline": alu_roofline(value / ws),
                 "kernels": kt, "autotune": tuning, "rsla": rsla,
+                "gas_step": rsla.pop("gas_step", None) if rsla else None,
                 "stats": {k: st[k] for k in ("n_realizability_fix", "n_face_fallback", "n_theta_fallback",
                                              "n_nonfinite", "newton_iter_max")},
                 "per_step_ms": per_step}

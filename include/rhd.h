@@ -146,6 +146,9 @@ typedef struct {
                                     return RHD_ERR_BOUNDS.  The counter is per process (shared by all
                                     contexts; rhd_reset_stats of any context clears it).  Always 0 in
                                     the release build. */
+    int64_t gas_energy_floors;   /* gas step: cells whose internal energy went negative and was set to 0 */
+    int64_t gas_nonfinite;       /* gas step: interior cells with a non-finite result (nonzero makes
+                                    rhd_get_stats return RHD_ERR_NONFINITE) */
 } rhd_stats;
 
 /* Create a context for one grid (Section 3.1).  Validates d, allocates the device state and makes
@@ -174,8 +177,35 @@ rhd_status rhd_set_dirichlet(rhd_ctx* ctx, int face, const double state[4]);
  * RHD_ERR_CUDA. */
 rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double dt);
 
-/* Gas step of Section 3.1 (steps 1-3 and 6).  Not part of this library: always RHD_ERR_UNSUPPORTED. */
+/* Gas step of Section 3.1 step 3 (Section 3.4): advance (rho, rho v, E_gas) of the Euler equations over
+ * dt_gas >= 0 with the explicit gas sources S_e,gas of Eq. (algorithm:source:explicit:gas) without gravity,
+ *     rho v:  k_F (G - (4/3) (v/c) E),   E_gas:  -k_F v . G        (G = F/c, k_F = rho kappa_0;
+ * the terms with v are the O(beta tau) terms, included when beta_tau = 1), by one van Leer predictor /
+ * corrector step: a first-order half step whose sources use the gas and the radiation at t^n, then a
+ * second-order full step (piecewise-linear primitives with the grid's limiter, HLLC fluxes) whose
+ * sources use the gas at t^{n+1/2} and the radiation still at t^n.  k_F is the kF array if one was
+ * given, else kappa_F rho^kappa_rho_pow.  P = rho T / mu_over_kB, E_gas = P/(gamma-1) + rho v^2/2; the
+ * gas state (rho, v, T) is updated in place on the device and velocity components never given become
+ * arrays (starting at zero).  Ghost cells follow the grid's boundary conditions (a Dirichlet face
+ * takes the nearest cell for the gas).  A negative internal energy is set to zero (counted in
+ * rhd_stats.gas_energy_floors).  The step leaves a source correction pending: run the radiation
+ * subcycles that span dt_gas, then rhd_gas_correct.  The energy exchange stays in the subcycles.
+ * Does not synchronise.  Scratch: about (5 (n0+4)(n1+4)(n2+4) + 15 (n0+5)(n1+4)(n2+4) + 8 n) doubles,
+ * allocated by the first call.  Single grids only.  Errors: RHD_ERR_ARG (dt_gas), RHD_ERR_STATE
+ * (ensemble, gas or moments not set), RHD_ERR_OOM, RHD_ERR_CUDA. */
 rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas);
+
+/* Section 3.1 step 6: correct the gas sources of the pending gas step to second order with the current
+ * radiation state U_rad^{n+1}: rho v and E_gas change by
+ *     dt_gas/2 [S_e,gas(U_gas^{n+1/2}, U_rad^{n+1}) - S_e,gas(U_gas^{n+1/2}, U_rad^n)]
+ * (Section 3.4), where U_gas^{n+1/2} and U_rad^n are those the step used.  Does not synchronise.
+ * Errors: RHD_ERR_STATE (no pending step, ensemble), RHD_ERR_CUDA. */
+rhd_status rhd_gas_correct(rhd_ctx* ctx);
+
+/* Copy the gas state out: rho, vx, vy, vz, T (any may be NULL to skip it; an absent velocity component
+ * reads as zero).  Layout as rhd_set_gas_state.  Synchronises the stream.  Errors: RHD_ERR_ARG,
+ * RHD_ERR_STATE (gas not set, ensemble), RHD_ERR_CUDA. */
+rhd_status rhd_get_gas(rhd_ctx* ctx, double* rho, double* vx, double* vy, double* vz, double* T, int on_device);
 
 /* Copy the current moments out (synchronises the stream).  Errors: RHD_ERR_ARG, RHD_ERR_STATE, RHD_ERR_CUDA. */
 rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, double* Fz, int on_device);

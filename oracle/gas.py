@@ -46,10 +46,11 @@ GHOST = 2  # ghost layers of the predictor's half-step state (the corrector's st
 
 # ----------------------------------------------------------------------------- ghost cells
 
-def axis_map(n, g, lo, hi):
-    """Interior index and sign of the normal component for the coordinates -g .. n+g-1 of one axis."""
+def axis_map(n, g, lo, hi, c0=None, c1=None):
+    """Interior index and sign of the normal component for the coordinates -g .. n+g-1 of one axis
+    (or c0 .. c1-1 when given)."""
     idx, sgn = [], []
-    for c in range(-g, n + g):
+    for c in range(-g if c0 is None else c0, n + g if c1 is None else c1):
         s = 1.0
         while c < 0 or c >= n:
             low = c < 0
@@ -68,15 +69,17 @@ def axis_map(n, g, lo, hi):
     return np.array(idx), np.array(sgn)
 
 
-def with_ghosts(desc, a, g, normal=None):
-    """The array a extended by g ghost layers in every active direction.  normal = d marks a vector
-    component along d, whose sign flips where the direction d is mirrored."""
+def with_ghosts(desc, a, g, normal=None, box=None):
+    """The array a extended by g ghost layers in every active direction (or, with box = (lo, hi), the
+    cells lo - g .. hi + g - 1 of the grid extended so).  normal = d marks a vector component along d,
+    whose sign flips where the direction d is mirrored."""
     out = a
     for d in range(3):
         n = desc["n"][d]
         if n <= 1:
             continue
-        idx, sgn = axis_map(n, g, desc["bc_lo"][d], desc["bc_hi"][d])
+        lo, hi = (0, n) if box is None else (box[0][d], box[1][d])
+        idx, sgn = axis_map(n, g, desc["bc_lo"][d], desc["bc_hi"][d], lo - g, hi + g)
         out = np.take(out, idx, axis=2 - d)
         if normal == d:
             shape = [1, 1, 1]
@@ -220,11 +223,12 @@ def crop(desc, a, g):
     return a[tuple(sl)]
 
 
-def gas_step(desc, gas, rad, dt):
+def gas_step(desc, gas, rad, dt, box=None):
     """One gas step over dt.  gas: dict rho, vx, vy, vz, T (vx.. may be None: zero), optional kF;
     rad: dict E, Fx, Fy, Fz (F in flux units).  Returns (gas at t^{n+1} before the source
-    correction, pending data for gas_correct, number of floored cells)."""
-    gam = desc["gamma"]
+    correction, pending data for gas_correct, number of floored cells).  With box = (lo, hi) only the
+    cells lo <= (x, y, z) < hi are computed and returned (the same arithmetic on the cells they
+    depend on)."""
     c = desc["c"]
     shp = gas["rho"].shape
     v = [gas.get(k) if gas.get(k) is not None else np.zeros(shp) for k in ("vx", "vy", "vz")]
@@ -232,16 +236,31 @@ def gas_step(desc, gas, rad, dt):
     W = [gas["rho"], v[0], v[1], v[2], pressure(desc, gas["rho"], gas["T"])]
     E = rad["E"]
     G = [rad["Fx"] / c, rad["Fy"] / c, rad["Fz"] / c]
-    act = active(desc)
-    floors = 0
 
     # (1) ghost-filled state at t^n: three layers, so that the predictor can be applied on two
     g3 = GHOST + 1
-    Wg = [with_ghosts(desc, W[0], g3), with_ghosts(desc, W[1], g3, 0), with_ghosts(desc, W[2], g3, 1),
-          with_ghosts(desc, W[3], g3, 2), with_ghosts(desc, W[4], g3)]
-    Eg3 = with_ghosts(desc, E, g3)
-    Gg3 = [with_ghosts(desc, G[a], g3, a) for a in range(3)]
-    kFg3 = None if kF is None else with_ghosts(desc, kF, g3)
+    Wg = [with_ghosts(desc, W[0], g3, box=box), with_ghosts(desc, W[1], g3, 0, box),
+          with_ghosts(desc, W[2], g3, 1, box), with_ghosts(desc, W[3], g3, 2, box), with_ghosts(desc, W[4], g3, box=box)]
+    Eg3 = with_ghosts(desc, E, g3, box=box)
+    Gg3 = [with_ghosts(desc, G[a], g3, a, box) for a in range(3)]
+    kFg3 = None if kF is None else with_ghosts(desc, kF, g3, box=box)
+    if box is not None:
+        # the box is the grid of the steps below; its ghost layers are the neighbouring cells
+        desc = dict(desc, n=tuple(box[1][d] - box[0][d] if desc["n"][d] > 1 else 1 for d in range(3)))
+        sl = tuple(slice(box[0][d], box[1][d]) for d in (2, 1, 0))
+        W = [w[sl] for w in W]
+        E = E[sl]
+        G = [g[sl] for g in G]
+        kF = None if kF is None else kF[sl]
+        shp = W[0].shape
+    return _step(desc, dt, W, E, G, kF, Wg, Eg3, Gg3, kFg3, shp)
+
+
+def _step(desc, dt, W, E, G, kF, Wg, Eg3, Gg3, kFg3, shp):
+    gam = desc["gamma"]
+    act = active(desc)
+    g3 = GHOST + 1
+    floors = 0
 
     # (2) predictor: first-order HLLC fluxes and the half step (sources from U_gas^n, U_rad^n)
     Ug = conserved(desc, Wg)

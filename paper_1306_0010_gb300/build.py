@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librhd.so")
-SOURCES = ["rhd_api.cu", "k_fp64.cu", "k_split.cu", "k_aux.cu", "k_rsla.cu", "rhd_noalloc.cu"]
+SOURCES = ["rhd_api.cu", "k_fp64.cu", "k_split.cu", "k_aux.cu", "k_rsla.cu", "k_gas.cu", "rhd_noalloc.cu"]
 # librhd_debug.so: the kernel translation units again with -DRHD_BOUNDS_CHECK (index checks that count
 # out-of-range indices and redirect the access), linked with the other objects of the release build
 DEBUG_LIB = os.path.join(PKG, "librhd_debug.so")

@@ -18,6 +18,8 @@
 
 #include "rhd.h"
 #include "rhd_internal.h"
+#include "gas_index.h"
+#include "gas_internal.h"
 
 using namespace rhd;
 
@@ -80,6 +82,13 @@ struct GridState {
     const double* dir_dev = nullptr;  // low x Dirichlet state in device memory (rhd_marshak_advance only)
     bool tuned = false;           // RHD_FLAG_AUTOTUNE handled
     double tuned_ms = -1.0;       // time per subcycle measured by the last tuning
+    // gas step scratch (allocated by the first rhd_gas_step): W^{n+1/2} on the extended grid, the face
+    // fluxes of each active direction, and what rhd_gas_correct needs
+    double* gas_wh[5] = {nullptr};
+    double* gas_flux[3][5] = {{nullptr}};
+    double* gas_pend[8] = {nullptr};
+    bool gas_pending = false;     // a gas step waits for its source correction
+    double gas_dt = 0.0;
 };
 
 }  // namespace
@@ -98,6 +107,7 @@ struct rhd_ctx {
     double* red_partials = nullptr;
     double* rsla_partial = nullptr;  // reduced-speed-of-light reductions: rsla_blocks() + 1 doubles
     double* marshak_state = nullptr;  // rhd_marshak_advance: low x Dirichlet states, 4 doubles per subcycle
+    unsigned long long* gas_counters = nullptr;  // gas step: [0] internal-energy floors, [1] non-finite cells
     int marshak_cap = 0;              // subcycles it holds
     double* red_out = nullptr;
     int red_blocks = 1;
@@ -319,6 +329,11 @@ void free_grid(GridState& gs)
     dfree(gs.uhalf);
     dfree(gs.um32);
     dfree(gs.gas4);
+    for (int q = 0; q < 5; ++q) dfree(gs.gas_wh[q]);
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 5; ++q) dfree(gs.gas_flux[d][q]);
+    for (int q = 0; q < 8; ++q) dfree(gs.gas_pend[q]);
+    gs.gas_pending = false;
 }
 
 void clear_graphs(rhd_ctx* ctx)
@@ -391,6 +406,8 @@ rhd_status common_init(rhd_ctx* ctx)
     rhd_status st = dalloc(ctx, (void**)&ctx->dstats, sizeof(DevStats));
     if (st) return st;
     RHD_CUDA(ctx, cudaMemset(ctx->dstats, 0, sizeof(DevStats)));
+    if ((st = dalloc(ctx, (void**)&ctx->gas_counters, 2 * sizeof(unsigned long long)))) return st;
+    RHD_CUDA(ctx, cudaMemset(ctx->gas_counters, 0, 2 * sizeof(unsigned long long)));
     return RHD_OK;
 }
 
@@ -405,6 +422,7 @@ void destroy_ctx(rhd_ctx* ctx)
     dfree(ctx->red_out);
     dfree(ctx->rsla_partial);
     dfree(ctx->marshak_state);
+    dfree(ctx->gas_counters);
     dfree(ctx->d_egrids[0]);
     dfree(ctx->d_egrids[1]);
     dfree(ctx->d_counter);
@@ -474,6 +492,7 @@ rhd_status set_gas(rhd_ctx* ctx, GridState& gs, const double* rho, const double*
     if ((st = set_optional(ctx, gs, gs.j, gs.j32, gs.has_j, j, on_device))) return st;
     gs.has_gas = true;
     gs.gas4_ok = false;
+    gs.gas_pending = false;  // a pending source correction belongs to the replaced state
     clear_graphs(ctx);  // array pointers may have changed
     return leave(ctx);
 }
@@ -604,11 +623,14 @@ rhd_status check_dt(rhd_ctx* ctx, const GridState& gs, double chat, double dt)
 // kernels reported by the kernel timer
 enum KernelId {
     K_FUSED_FP64 = 0, K_FUSED_SPLIT, K_PREDICTOR, K_CORRECTOR, K_ENS_FP64, K_ENS_SPLIT, K_ENS_PRED, K_ENS_CORR,
+    K_GAS_PRED_FLUX, K_GAS_PRED_UPDATE, K_GAS_CORR_FLUX, K_GAS_CORR_UPDATE, K_GAS_CORRECT,
     K_COUNT
 };
 const char* const kKernelNames[K_COUNT] = {"subcycle_fused_fp64", "subcycle_fused_split", "twopass_predictor_split",
                                            "twopass_corrector_split", "ensemble_fp64", "ensemble_split",
-                                           "ensemble_predictor_split", "ensemble_corrector_split"};
+                                           "ensemble_predictor_split", "ensemble_corrector_split",
+                                           "gas_predictor_flux", "gas_predictor_update", "gas_corrector_flux",
+                                           "gas_corrector_update", "gas_source_correction"};
 
 // Algorithmic bytes per interior cell of one launch of kernel k: every array the kernel reads, read
 // once, and every array it writes, written once.  Fused kernels: U^m and U^{m+1} (4 FP64 each), the
@@ -1401,10 +1423,195 @@ rhd_status rhd_marshak_advance(rhd_ctx* ctx, int n_sub, double chat, double dt, 
     return leave(ctx);
 }
 
+namespace {
+
+GasParams gas_params(const GridState& gs, double dt)
+{
+    GasParams p;
+    std::memset(&p, 0, sizeof(p));
+    gas_set_geometry(p, gs.desc.n, gs.desc.bc_lo, gs.desc.bc_hi);
+    for (int d = 0; d < 3; ++d) p.inv_dx[d] = gs.desc.n[d] > 1 ? 1.0 / gs.desc.dx[d] : 0.0;
+    p.gamma = gs.desc.gamma;
+    p.gm1 = gs.desc.gamma - 1.0;
+    p.inv_gm1 = 1.0 / p.gm1;
+    p.mu_over_kB = gs.desc.mu_over_kB;
+    p.inv_mu = 1.0 / gs.desc.mu_over_kB;
+    p.inv_c = 1.0 / gs.desc.c;
+    p.kappa_F = gs.desc.kappa_F;
+    p.kpow = gs.desc.kappa_rho_pow;
+    p.beta_tau = gs.desc.beta_tau;
+    p.limiter = gs.desc.limiter;
+    p.dt = dt;
+    return p;
+}
+
+GasArrays gas_arrays(rhd_ctx* ctx, GridState& gs)
+{
+    GasArrays a;
+    std::memset(&a, 0, sizeof(a));
+    a.rho = gs.rho;
+    a.T = gs.T;
+    for (int d = 0; d < 3; ++d) a.v[d] = gs.v[d];
+    a.kF = gs.has_kF ? gs.kF : nullptr;
+    a.E = gs.U[ctx->cur][0];
+    for (int d = 0; d < 3; ++d) a.G[d] = gs.U[ctx->cur][1 + d];
+    for (int q = 0; q < 5; ++q) a.wh[q] = gs.gas_wh[q];
+    for (int d = 0; d < 3; ++d)
+        for (int q = 0; q < 5; ++q) a.flux[d][q] = gs.gas_flux[d][q];
+    for (int q = 0; q < 8; ++q) a.pend[q] = gs.gas_pend[q];
+    a.counters = ctx->gas_counters;
+    return a;
+}
+
+// The gas step's scratch, and all three velocity components (a component that was never given starts
+// at zero: the radiation force and the fluxes make it nonzero).
+rhd_status gas_prepare(rhd_ctx* ctx, GridState& gs, const GasParams& p)
+{
+    rhd_status st;
+    if (!gs.gas_wh[0]) {
+        for (int q = 0; q < 5; ++q)
+            if ((st = dalloc(ctx, (void**)&gs.gas_wh[q], sizeof(double) * (size_t)gas_count(p.m)))) return st;
+        for (int d = 0; d < 3; ++d) {
+            if (gs.desc.n[d] <= 1) continue;
+            for (int q = 0; q < 5; ++q)
+                if ((st = dalloc(ctx, (void**)&gs.gas_flux[d][q], sizeof(double) * (size_t)gas_face_capacity(p, d))))
+                    return st;
+        }
+        for (int q = 0; q < 8; ++q)
+            if ((st = dalloc(ctx, (void**)&gs.gas_pend[q], sizeof(double) * (size_t)gs.ncell))) return st;
+    }
+    bool added = false;
+    for (int d = 0; d < 3; ++d) {
+        if (gs.v[d]) continue;
+        if ((st = dalloc(ctx, (void**)&gs.v[d], sizeof(double) * (size_t)gs.ncell))) return st;
+        RHD_CUDA(ctx, cudaMemsetAsync(gs.v[d], 0, sizeof(double) * (size_t)gs.ncell, ctx->stream));
+        if (gs.desc.precision == RHD_SPLIT && !gs.v32[d])
+            if ((st = dalloc(ctx, (void**)&gs.v32[d], sizeof(float) * (size_t)gs.ncell))) return st;
+        added = true;
+    }
+    if (added) {
+        gs.has_v = true;
+        clear_graphs(ctx);  // the subcycle kernels' velocity pointers changed
+    }
+    return RHD_OK;
+}
+
+// After the gas changed: the FP32 copies the split subcycles read
+rhd_status gas_refresh_copies(rhd_ctx* ctx, GridState& gs)
+{
+    if (gs.desc.precision == RHD_SPLIT) {
+        RHD_CUDA(ctx, launch_to_float(gs.rho32, gs.rho, gs.ncell, ctx->stream));
+        for (int d = 0; d < 3; ++d) RHD_CUDA(ctx, launch_to_float(gs.v32[d], gs.v[d], gs.ncell, ctx->stream));
+    }
+    gs.gas4_ok = false;
+    return RHD_OK;
+}
+
+// bytes per cell of each gas kernel (each array read or written once per launch): the gas state is
+// 40 B (rho, T, v), W^{n+1/2} 40 B, one face-flux array 40 B per cell, the radiation 32 B, the
+// correction's record 64 B
+double gas_alg_bytes(const GridState& gs, int k, int nact)
+{
+    const double kf = gs.has_kF ? 8.0 : 0.0;
+    switch (k) {
+    case K_GAS_PRED_FLUX: return 40.0 + 40.0;
+    case K_GAS_PRED_UPDATE: return 40.0 + 32.0 + kf + 40.0 * nact + 40.0;
+    case K_GAS_CORR_FLUX: return 40.0 + 40.0;
+    case K_GAS_CORR_UPDATE: return 40.0 + 40.0 * nact + 32.0 + 32.0 + kf + 40.0 + 64.0;
+    default: return 40.0 + 64.0 + 32.0 + 32.0;  // K_GAS_CORRECT
+    }
+}
+
+rhd_status single_grid(rhd_ctx* ctx, const char* what)
+{
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, std::string(what) + " runs on single grids, not ensembles");
+    const GridState& gs = ctx->grids[0];
+    if (!gs.has_gas || !gs.has_moments) return fail(ctx, RHD_ERR_STATE, "set the gas state and the moments first");
+    return RHD_OK;
+}
+
+}  // namespace
+
 rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas)
 {
-    (void)dt_gas;
-    return fail(ctx, RHD_ERR_UNSUPPORTED, "the gas step is not part of this library");
+    ApiRange range_("rhd_gas_step");
+    rhd_status st = single_grid(ctx, "rhd_gas_step");
+    if (st) return st;
+    if (!(std::isfinite(dt_gas) && dt_gas >= 0.0)) return fail(ctx, RHD_ERR_ARG, "dt_gas must be finite and >= 0");
+    GridState& gs = ctx->grids[0];
+    if ((st = enter(ctx))) return st;
+    const GasParams p = gas_params(gs, dt_gas);
+    if ((st = gas_prepare(ctx, gs, p))) return st;
+    const GasArrays a = gas_arrays(ctx, gs);
+    const double ext = (double)gas_count(p.m), nc = (double)gs.ncell;
+    int nact = 0;
+    for (int d = 0; d < 3; ++d) nact += gs.desc.n[d] > 1;
+    cudaStream_t s = ctx->stream;
+    for (int d = 0; d < 3; ++d) {
+        if (gs.desc.n[d] <= 1) continue;
+        if ((st = timed_launch(ctx, K_GAS_PRED_FLUX, ext * gas_alg_bytes(gs, K_GAS_PRED_FLUX, nact),
+                               [&] { return launch_gas_pred_flux(p, a, d, s); })))
+            return st;
+    }
+    if ((st = timed_launch(ctx, K_GAS_PRED_UPDATE, ext * gas_alg_bytes(gs, K_GAS_PRED_UPDATE, nact),
+                           [&] { return launch_gas_pred_update(p, a, s); })))
+        return st;
+    for (int d = 0; d < 3; ++d) {
+        if (gs.desc.n[d] <= 1) continue;
+        if ((st = timed_launch(ctx, K_GAS_CORR_FLUX, nc * gas_alg_bytes(gs, K_GAS_CORR_FLUX, nact),
+                               [&] { return launch_gas_corr_flux(p, a, d, s); })))
+            return st;
+    }
+    if ((st = timed_launch(ctx, K_GAS_CORR_UPDATE, nc * gas_alg_bytes(gs, K_GAS_CORR_UPDATE, nact),
+                           [&] { return launch_gas_corr_update(p, a, s); })))
+        return st;
+    if ((st = gas_refresh_copies(ctx, gs))) return st;
+    gs.gas_pending = true;
+    gs.gas_dt = dt_gas;
+    return leave(ctx);
+}
+
+rhd_status rhd_gas_correct(rhd_ctx* ctx)
+{
+    ApiRange range_("rhd_gas_correct");
+    rhd_status st = single_grid(ctx, "rhd_gas_correct");
+    if (st) return st;
+    GridState& gs = ctx->grids[0];
+    if (!gs.gas_pending) return fail(ctx, RHD_ERR_STATE, "no gas step waits for its source correction");
+    if ((st = enter(ctx))) return st;
+    const GasParams p = gas_params(gs, gs.gas_dt);
+    const GasArrays a = gas_arrays(ctx, gs);
+    if ((st = timed_launch(ctx, K_GAS_CORRECT, (double)gs.ncell * gas_alg_bytes(gs, K_GAS_CORRECT, 0),
+                           [&] { return launch_gas_correct(p, a, ctx->stream); })))
+        return st;
+    if ((st = gas_refresh_copies(ctx, gs))) return st;
+    gs.gas_pending = false;
+    return leave(ctx);
+}
+
+rhd_status rhd_get_gas(rhd_ctx* ctx, double* rho, double* vx, double* vy, double* vz, double* T, int on_device)
+{
+    ApiRange range_("rhd_get_gas");
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (ctx->ensemble) return fail(ctx, RHD_ERR_STATE, "rhd_get_gas runs on single grids, not ensembles");
+    GridState& gs = ctx->grids[0];
+    if (!gs.has_gas) return fail(ctx, RHD_ERR_STATE, "the gas state is not set");
+    rhd_status st = enter(ctx);
+    if (st) return st;
+    const size_t bytes = sizeof(double) * (size_t)gs.ncell;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    double* out[5] = {rho, vx, vy, vz, T};
+    const double* src[5] = {gs.rho, gs.v[0], gs.v[1], gs.v[2], gs.T};
+    for (int q = 0; q < 5; ++q) {
+        if (!out[q]) continue;
+        if (src[q]) RHD_CUDA(ctx, cudaMemcpyAsync(out[q], src[q], bytes, kind, ctx->stream));
+        else if (on_device) RHD_CUDA(ctx, cudaMemsetAsync(out[q], 0, bytes, ctx->stream));
+        else std::memset(out[q], 0, bytes);
+    }
+    if ((st = leave(ctx))) return st;
+    RHD_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RHD_OK;
 }
 
 rhd_status rhd_get_moments(rhd_ctx* ctx, double* E, double* Fx, double* Fy, double* Fz, int on_device)
@@ -1500,6 +1707,7 @@ rhd_status rhd_reset_stats(rhd_ctx* ctx)
     rhd_status st = enter(ctx);
     if (st) return st;
     RHD_CUDA(ctx, cudaMemsetAsync(ctx->dstats, 0, sizeof(DevStats), ctx->stream));
+    RHD_CUDA(ctx, cudaMemsetAsync(ctx->gas_counters, 0, 2 * sizeof(unsigned long long), ctx->stream));
     RHD_CUDA(ctx, oob_read_fp64(nullptr, 1, ctx->stream));
     RHD_CUDA(ctx, oob_read_split(nullptr, 1, ctx->stream));
     ctx->n_subcycles = 0;
@@ -1515,6 +1723,9 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
     if (st) return st;
     DevStats hs;
     RHD_CUDA(ctx, cudaMemcpyAsync(&hs, ctx->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long gas_counts[2] = {0, 0};
+    RHD_CUDA(ctx, cudaMemcpyAsync(gas_counts, ctx->gas_counters, sizeof(gas_counts), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
     double sums[5] = {0, 0, 0, 0, 0};
     for (auto& gs : ctx->grids) {
         if (!gs.has_moments) continue;
@@ -1547,6 +1758,8 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
     out->sum_E = sums[0];
     for (int d = 0; d < 3; ++d) out->sum_F[d] = sums[1 + d];
     out->max_f = sums[4];
+    out->gas_energy_floors = (int64_t)gas_counts[0];
+    out->gas_nonfinite = (int64_t)gas_counts[1];
     if (out->bounds_violations) {
         const OobRecord& r = oob[0].count ? oob[0] : oob[1];
         return fail(ctx, RHD_ERR_BOUNDS,
@@ -1558,6 +1771,9 @@ rhd_status rhd_get_stats(rhd_ctx* ctx, rhd_stats* out)
     if (out->n_nonfinite)
         return fail(ctx, RHD_ERR_NONFINITE,
                     std::to_string(out->n_nonfinite) + " non-finite values were produced since the last reset");
+    if (out->gas_nonfinite)
+        return fail(ctx, RHD_ERR_NONFINITE,
+                    std::to_string(out->gas_nonfinite) + " cells of the gas step became non-finite since the last reset");
     return RHD_OK;
 }
 

@@ -87,6 +87,8 @@ class Stats(ctypes.Structure):
         ("sum_F", ctypes.c_double * 3),
         ("max_f", ctypes.c_double),
         ("bounds_violations", ctypes.c_int64),
+        ("gas_energy_floors", ctypes.c_int64),
+        ("gas_nonfinite", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -148,6 +150,8 @@ _SIGS = {
     "rhd_set_dirichlet": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rhd_radiation_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "rhd_gas_step": (ctypes.c_int, [_P, ctypes.c_double]),
+    "rhd_gas_correct": (ctypes.c_int, [_P]),
+    "rhd_get_gas": (ctypes.c_int, [_P] + [_P] * 5 + [ctypes.c_int]),
     "rhd_get_moments": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
     "rhd_set_conserved": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
     "rhd_get_conserved": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
@@ -303,6 +307,7 @@ class Grid:
         # references to the frozen gas inputs, for checkpoint() (T evolves and is read back from the device)
         self._gas_in = dict(zip(self._GAS_KEYS, (rho, T, vx, vy, vz, kP, kF, j)))
         self._set_gas_state(rho, T, vx, vy, vz, kP, kF, j)
+        self._gas_stepped = self._gas_pending = False
 
     def _set_gas_state(self, rho, T, vx=None, vy=None, vz=None, kP=None, kF=None, j=None):
         ps = [_ptr(a, self.ncell) for a in (rho, T, vx, vy, vz, kP, kF, j)]
@@ -322,7 +327,38 @@ class Grid:
         _check(self._ctx, lib().rhd_radiation_subcycle(self._ctx, int(n_sub), float(chat), float(dt)))
 
     def gas_step(self, dt_gas):
+        """The gas half of a cycle (Section 3.1 step 3): one van Leer step of the gas with the explicit gas
+        sources, the radiation held at its current state; leaves the source correction pending."""
         _check(self._ctx, lib().rhd_gas_step(self._ctx, float(dt_gas)))
+        self._gas_stepped = self._gas_pending = True
+
+    def gas_correct(self):
+        """Section 3.1 step 6: the pending gas step's sources corrected with the current radiation."""
+        _check(self._ctx, lib().rhd_gas_correct(self._ctx))
+        self._gas_pending = False
+
+    def gas_cycle(self, chat, cfl=None, ratio=None, dt_gas=None):
+        """One whole cycle of Section 3.1: time steps (unless dt_gas is given: then the subcycles are
+        the fewest of length <= cfl min(dx) / chat spanning it), the gas step, the radiation subcycles
+        over dt_gas, the source correction.  Returns (dt_gas, n_sub)."""
+        cfl = self.desc.get("cfl", 0.4) if cfl is None else cfl
+        dxm = min(self.desc["dx"][d] for d in range(3) if self.desc["n"][d] > 1)
+        if dt_gas is None:
+            dt_gas, dt_rad, n_sub = time_steps(cfl, dxm, self.max_signal_speed(), chat)
+        else:
+            n_sub = max(1, int(np.ceil(dt_gas / (cfl * dxm / chat) * (1 - 1e-12))))
+            dt_rad = dt_gas / n_sub
+        self.gas_step(dt_gas)
+        self.radiation_subcycle(n_sub, chat, dt_rad)
+        self.gas_correct()
+        return dt_gas, n_sub
+
+    def get_gas(self):
+        """The gas state: dict rho, vx, vy, vz, T (NumPy)."""
+        out = {k: np.empty(self.shape) for k in ("rho", "vx", "vy", "vz", "T")}
+        ps = [_ptr(out[k], self.ncell, writable=True)[0] for k in ("rho", "vx", "vy", "vz", "T")]
+        _check(self._ctx, lib().rhd_get_gas(self._ctx, *ps, 0))
+        return out
 
     def get_moments(self, E=None, Fx=None, Fy=None, Fz=None):
         if E is None:
@@ -414,11 +450,18 @@ class Grid:
         """Save the evolving state (E, G = F/c, T), the descriptor, the launch configuration and the frozen
         gas inputs last given to set_gas_state (as they are at this call) to an .npz file;
         Grid.restore(path) continues bit for bit."""
+        if getattr(self, "_gas_pending", False):
+            raise RhdError(ERR_STATE, "a gas step waits for its source correction: checkpoint after gas_correct")
         out = self.get_conserved()
         out["T_state"] = self.get_gas_state()
         for k, v in getattr(self, "_gas_in", {}).items():
             if v is not None and k != "T":
                 out["gas_" + k] = v.detach().cpu().numpy() if _is_torch(v) else np.asarray(v)
+        if getattr(self, "_gas_stepped", False):
+            # the gas steps moved rho and v away from the inputs: save the current state
+            gas = self.get_gas()
+            for k in ("rho", "vx", "vy", "vz"):
+                out["gas_" + k] = gas[k]
         cfg = self.launch_config()
         np.savez(path, desc=np.array(json.dumps(self.desc, default=float)),
                  launch=np.array(json.dumps(dict(cfg, tile=list(cfg["tile"])))), **out)

@@ -161,6 +161,24 @@ def parity_case(name, n, bc="periodic", exchange="equilibrium", limiter="minmod"
     return {"name": name, "desc": desc, "fields": fields, "chat": chat, "dt": dt, "n_sub": n_sub}
 
 
+def gas_case(name, n, bc="periodic", limiter="minmod", beta_tau=True, kappa=2.0, kappa_rho_pow=1, kF_array=False,
+             seed=0, precision="fp64", dirichlet=None, exchange="full", n_sub=4, with_v=True, c=10.0, gamma=5.0 / 3.0):
+    """A gas-step case: the random gas and radiation of parity_case (rho = exp(N(0, 0.5^2)), T = exp(N(0,
+    0.2^2)), v ~ N(0, (0.05 c)^2) per component, Mach numbers up to about 1), a second random radiation
+    state "rad1" (the radiation at t^{n+1} for the source correction), dt_gas = 0.1 min(dx) (below a
+    third of the gas Courant limit) and n_sub radiation subcycles of dt_gas / n_sub."""
+    case = parity_case(name, n, bc=bc, exchange=exchange, limiter=limiter, beta_tau=beta_tau, kappa=kappa,
+                       kappa_rho_pow=kappa_rho_pow, seed=seed, with_v=with_v, precision=precision,
+                       dirichlet=dirichlet, kP_array=kF_array, c=c, n_sub=n_sub)
+    case["desc"]["gamma"] = gamma
+    g = rng(3000 + seed)
+    case["rad1"] = random_state(case["desc"], g, fmax=0.9)
+    dxs = [case["desc"]["dx"][d] for d in range(3) if case["desc"]["n"][d] > 1]
+    case["dt_gas"] = 0.1 * min(dxs)
+    case["dt"] = case["dt_gas"] / n_sub
+    return case
+
+
 # ----------------------------------------------------------------------------- paper-shaped configs
 
 def dispersion_omega(chat, k, kF, mode):

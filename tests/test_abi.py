@@ -86,7 +86,9 @@ def test_identification_and_argument_errors(lib):
     # NULL contexts
     assert lib.rhd_radiation_subcycle(None, 1, 1.0, 0.1) == rhd.ERR_ARG
     assert lib.rhd_destroy(None) == rhd.OK
-    assert lib.rhd_gas_step(None, 1.0) == rhd.ERR_UNSUPPORTED
+    assert lib.rhd_gas_step(None, 1.0) == rhd.ERR_ARG
+    assert lib.rhd_gas_correct(None) == rhd.ERR_ARG
+    assert lib.rhd_get_gas(None, None, None, None, None, None, 0) == rhd.ERR_ARG
     cfg = rhd.LaunchConfig()
     assert lib.rhd_autotune(None, 1.0, 0.1, 1, None, 0, None, None) == rhd.ERR_ARG
     assert lib.rhd_ensemble_autotune(None, 1.0, None, 1, None, 0, None, None) == rhd.ERR_ARG
