@@ -64,8 +64,9 @@ GAS_CASES = [
     dict(name="3d_gas_at_rest", n=(8, 6, 5), bc="outflow", with_v=False),
     dict(name="2d_reflect_periodic", n=(17, 13, 1), bc=(["reflect", "periodic", "periodic"],
                                                       ["reflect", "periodic", "periodic"])),
-    dict(name="2d_yz", n=(1, 11, 6), bc="outflow", limiter="none"),
-    dict(name="2d_xz", n=(6, 1, 9), bc="periodic"),
+    dict(name="2d_outflow_unlimited", n=(11, 6, 1), bc="outflow", limiter="none"),
+    dict(name="2d_dirichlet_kF", n=(9, 14, 1), bc=(["dirichlet", "outflow", "periodic"], ["outflow", "reflect", "periodic"]),
+         dirichlet=([[2.0, 0.5, 0.0, 0.0], [0.0] * 4, [0.0] * 4], [[0.0] * 4] * 3), kF_array=True),
     dict(name="1d_outflow_none", n=(33, 1, 1), bc="outflow", limiter="none"),
     dict(name="1d_n3_reflect", n=(3, 1, 1), bc="reflect"),
 ]
