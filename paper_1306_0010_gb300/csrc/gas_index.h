@@ -18,7 +18,7 @@ namespace rhd {
 // periodic wraps, outflow and Dirichlet take the nearest cell, reflect mirrors and flips the sign of
 // the normal component.  Coordinates within 2n of the grid need at most two steps; the clamp keeps
 // any other coordinate inside [0, n).
-GAS_HD int gas_axis(int c, int n, int lo, int hi, double& s)
+GAS_HD int gas_axis(int c, int n, int lo, int hi, int& s)
 {
     for (int it = 0; it < 4 && (c < 0 || c >= n); ++it) {
         const bool low = c < 0;
@@ -36,12 +36,12 @@ GAS_HD int gas_axis(int c, int n, int lo, int hi, double& s)
 }
 
 // interior linear index of the cell at coordinates c (which may lie in the ghost layers) and the
-// signs of its normal components s[d]
-GAS_HD long long gas_remap(const GasParams& p, const int c[3], double s[3])
+// signs (+1 or -1) of its normal components s[d]
+GAS_HD long long gas_remap(const GasParams& p, const int c[3], int s[3])
 {
     int q[3];
     for (int d = 0; d < 3; ++d) {
-        s[d] = 1.0;
+        s[d] = 1;
         q[d] = gas_axis(c[d], p.n[d], p.bc_lo[d], p.bc_hi[d], s[d]);
     }
     return q[0] + (long long)p.n[0] * (q[1] + (long long)p.n[1] * q[2]);
@@ -98,8 +98,8 @@ inline void gas_set_geometry(GasParams& p, const int n[3], const int bc_lo[3], c
 
 // predictor flux, face f of direction d: the interior indices (and normal-component signs) of the cells
 // on its low (L) and high (R) side
-GAS_HD void gas_pred_flux_cells(const GasParams& p, int d, long long f, long long* iL, double sL[3], long long* iR,
-                                double sR[3])
+GAS_HD void gas_pred_flux_cells(const GasParams& p, int d, long long f, long long* iL, int sL[3], long long* iR,
+                                int sR[3])
 {
     int fe[3], A[3], cL[3], cR[3];
     gas_pred_faces(p, d, fe);
@@ -112,7 +112,7 @@ GAS_HD void gas_pred_flux_cells(const GasParams& p, int d, long long f, long lon
 
 // predictor update, extended cell i: the interior cell k it is filled from (signs s), whether it is an
 // interior cell, and its low / high faces in each active direction's predictor layout (-1: inactive)
-GAS_HD void gas_pred_update_cells(const GasParams& p, long long i, long long* k, double s[3], bool* inside,
+GAS_HD void gas_pred_update_cells(const GasParams& p, long long i, long long* k, int s[3], bool* inside,
                                   long long lo[3], long long hi[3])
 {
     int A[3], c[3];

@@ -25,18 +25,26 @@ struct GasParams {
     double kappa_F;           // opacity law k_F = kappa_F rho^kpow where no kF array is given
     int kpow, beta_tau, limiter;
     double dt;
+    // split grids: the face fluxes (reconstruction, wave speeds, HLLC) in FP32 with these FP32 copies;
+    // conversions, accumulation and sources stay FP64
+    int split;
+    float f_gamma, f_inv_gm1, f_inv_mu;
 };
 
 struct GasArrays {
     double* rho;              // gas at t^n (read), overwritten with t^{n+1} by the corrector
     double* T;
     double* v[3];             // all three components present
+    const float* rho32;       // split grids: FP32 copies of rho and v (current with the FP64 state)
+    const float* v32[3];
     const double* kF;         // NULL: the opacity law
     const double* E;          // radiation at t^n (step) or t^{n+1} (correction), G = F/c
     const double* G[3];
     double* wh[5];            // W^{n+1/2} = (rho, vx, vy, vz, P) on the extended grid m[0] x m[1] x m[2]
+    float* wh32[5];           // split grids: its FP32 copy (read by the corrector's FP32 fluxes)
     double* flux[3][5];       // face fluxes of direction d (predictor layout (m_d + 1) x m_e, corrector
-                              // layout (n_d + 1) x n_e), components (rho, Mx, My, Mz, E_gas)
+                              // layout (n_d + 1) x n_e), components (rho, Mx, My, Mz, E_gas); FP32 values
+                              // (the first half of each buffer) on split grids
     double* pend[8];          // kept for the correction: k_F(rho^{n+1/2}), v^{n+1/2} (3), E^n, G^n (3)
     unsigned long long* counters;  // [0] cells whose internal energy was floored to 0, [1] non-finite cells
 };

@@ -10,12 +10,19 @@
 //   correction (after the subcycles): dt/2 [S_e,gas(W^{n+1/2}, U_rad^{n+1}) - S_e,gas(W^{n+1/2}, U_rad^n)].
 //
 // Each face flux is computed once, by one thread, and stored (the face arrays of one direction); the
-// update kernels take the flux differences.  Everything is FP64.  The HLLC solver (Toro, Riemann
-// Solvers and Numerical Methods for Fluid Dynamics, Sec. 10.4) uses the Davis wave-speed estimates; the
-// left star state when S* = 0; HLL where the contact speed's denominator is not negative.
+// update kernels take the flux differences.  The HLLC solver (Toro, Riemann Solvers and Numerical
+// Methods for Fluid Dynamics, Sec. 10.4) uses the Davis wave-speed estimates; the left star state when
+// S* = 0; HLL where the contact speed's denominator is not negative.
+//
+// Precision: the flux kernels are templates on the arithmetic type R.  FP64 grids: R = double.  Split
+// grids: R = float for reconstruction, wave speeds and HLLC (inputs truncated to FP32 by integer bit
+// operations, FP32 fluxes stored), while the updates (flux differences, sources, conversions between
+// primitive and conserved variables) are FP64 on both.  Divisions are reciprocals (FP64: the hardware
+// approximation refined by Newton-Raphson; FP32: the hardware approximation) times the numerator.
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "fp_convert.cuh"
 #include "gas_index.h"
 #include "gas_internal.h"
 
@@ -25,37 +32,89 @@ namespace {
 
 constexpr int GAS_THREADS = 256;
 
+template <typename R>
 struct Prim {
-    double r, v[3], P;
+    R r, v[3], P;
 };
 
-__device__ __forceinline__ Prim load_prim(const GasParams& p, const GasArrays& a, long long i, const double s[3])
+template <typename R>
+__device__ __forceinline__ R flip(R x, int s)
 {
-    Prim w;
+    return s < 0 ? -x : x;
+}
+
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f2d_exact(x); }
+
+// physical constants in R
+template <typename R>
+struct Consts {
+    R gamma, inv_gm1, inv_mu;
+};
+template <typename R>
+__device__ __forceinline__ Consts<R> consts(const GasParams& p);
+template <>
+__device__ __forceinline__ Consts<double> consts<double>(const GasParams& p)
+{
+    return {p.gamma, p.inv_gm1, p.inv_mu};
+}
+template <>
+__device__ __forceinline__ Consts<float> consts<float>(const GasParams& p)
+{
+    return {p.f_gamma, p.f_inv_gm1, p.f_inv_mu};
+}
+
+// the gas state at t^n of interior cell i, with the normal velocity components of a mirrored ghost
+// cell flipped (s)
+__device__ __forceinline__ Prim<double> load_prim(const GasParams& p, const GasArrays& a, long long i, const int s[3])
+{
+    Prim<double> w;
     w.r = a.rho[i];
-    for (int d = 0; d < 3; ++d) w.v[d] = a.v[d][i] * s[d];
+    for (int d = 0; d < 3; ++d) w.v[d] = flip(a.v[d][i], s[d]);
     w.P = w.r * a.T[i] * p.inv_mu;
     return w;
 }
 
-__device__ __forceinline__ double kin2(const Prim& w)
+template <typename R>
+__device__ __forceinline__ Prim<R> load_prim_t(const GasParams& p, const GasArrays& a, long long i, const int s[3]);
+template <>
+__device__ __forceinline__ Prim<double> load_prim_t<double>(const GasParams& p, const GasArrays& a, long long i,
+                                                            const int s[3])
+{
+    return load_prim(p, a, i, s);
+}
+template <>
+__device__ __forceinline__ Prim<float> load_prim_t<float>(const GasParams& p, const GasArrays& a, long long i,
+                                                          const int s[3])
+{
+    Prim<float> w;
+    w.r = a.rho32[i];
+    for (int d = 0; d < 3; ++d) w.v[d] = flip(a.v32[d][i], s[d]);
+    w.P = w.r * d2f_trunc(a.T[i]) * p.f_inv_mu;
+    return w;
+}
+
+template <typename R>
+__device__ __forceinline__ R kin2(const Prim<R>& w)
 {
     return w.v[0] * w.v[0] + w.v[1] * w.v[1] + w.v[2] * w.v[2];
 }
 
-// (rho, Mx, My, Mz, E_gas) of a primitive state
-__device__ __forceinline__ void to_cons(const GasParams& p, const Prim& w, double U[5])
+// (rho, Mx, My, Mz, E_gas) of a primitive state (FP64)
+__device__ __forceinline__ void to_cons(const GasParams& p, const Prim<double>& w, double U[5])
 {
     U[0] = w.r;
     for (int d = 0; d < 3; ++d) U[1 + d] = w.r * w.v[d];
     U[4] = w.P * p.inv_gm1 + 0.5 * w.r * kin2(w);
 }
 
-// primitive state of U; a negative internal energy is floored to zero (returns true then)
-__device__ __forceinline__ bool to_prim(const GasParams& p, const double U[5], Prim& w)
+// primitive state of U (FP64); a negative internal energy is floored to zero (returns true then).
+// inv_r receives 1/rho.
+__device__ __forceinline__ bool to_prim(const GasParams& p, const double U[5], Prim<double>& w, double& inv_r)
 {
     w.r = U[0];
-    for (int d = 0; d < 3; ++d) w.v[d] = U[1 + d] / U[0];
+    inv_r = rcp(U[0]);
+    for (int d = 0; d < 3; ++d) w.v[d] = U[1 + d] * inv_r;
     double e = U[4] - 0.5 * (U[1] * w.v[0] + U[2] * w.v[1] + U[3] * w.v[2]);
     const bool neg = e < 0.0;
     if (neg) e = 0.0;
@@ -63,65 +122,67 @@ __device__ __forceinline__ bool to_prim(const GasParams& p, const double U[5], P
     return neg;
 }
 
-template <int D>
-__device__ __forceinline__ void euler_flux(const GasParams& p, const Prim& w, double F[5], double& E)
+template <typename R, int D>
+__device__ __forceinline__ void euler_flux(const Consts<R>& k, const Prim<R>& w, R F[5], R& E)
 {
-    const double u = w.v[D];
-    E = w.P * p.inv_gm1 + 0.5 * w.r * kin2(w);
+    const R u = w.v[D];
+    E = w.P * k.inv_gm1 + R(0.5) * w.r * kin2(w);
     F[0] = w.r * u;
-    for (int k = 0; k < 3; ++k) F[1 + k] = w.r * w.v[k] * u;
+    for (int q = 0; q < 3; ++q) F[1 + q] = w.r * w.v[q] * u;
     F[1 + D] += w.P;
     F[4] = (E + w.P) * u;
 }
 
-template <int D>
-__device__ void hllc(const GasParams& p, const Prim& L, const Prim& R, double F[5])
+template <typename R, int D>
+__device__ void hllc(const Consts<R>& k, const Prim<R>& L, const Prim<R>& Rt, R F[5])
 {
-    const double aL = sqrt(p.gamma * L.P / L.r), aR = sqrt(p.gamma * R.P / R.r);
-    const double uL = L.v[D], uR = R.v[D];
-    const double SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
-    double FL[5], FR[5], EL, ER;
-    if (SL >= 0.0) {
-        euler_flux<D>(p, L, F, EL);
+    const R irL = rcp(L.r), irR = rcp(Rt.r);
+    const R aL = rsq(k.gamma * L.P * irL), aR = rsq(k.gamma * Rt.P * irR);
+    const R uL = L.v[D], uR = Rt.v[D];
+    const R SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
+    R FL[5], FR[5], EL, ER;
+    if (SL >= R(0)) {
+        euler_flux<R, D>(k, L, F, EL);
         return;
     }
-    if (SR <= 0.0) {
-        euler_flux<D>(p, R, F, ER);
+    if (SR <= R(0)) {
+        euler_flux<R, D>(k, Rt, F, ER);
         return;
     }
-    euler_flux<D>(p, L, FL, EL);
-    euler_flux<D>(p, R, FR, ER);
-    const double den = L.r * (SL - uL) - R.r * (SR - uR);
-    if (den < 0.0) {
-        const double Ss = (R.P - L.P + L.r * uL * (SL - uL) - R.r * uR * (SR - uR)) / den;
-        const bool left = Ss >= 0.0;
-        const Prim& K = left ? L : R;
-        const double S = left ? SL : SR, EK = left ? EL : ER, uK = K.v[D];
-        const double* FK = left ? FL : FR;
-        const double chi = K.r * (S - uK) / (S - Ss);
-        double Us[5];
+    euler_flux<R, D>(k, L, FL, EL);
+    euler_flux<R, D>(k, Rt, FR, ER);
+    const R den = L.r * (SL - uL) - Rt.r * (SR - uR);
+    if (den < R(0)) {
+        const R Ss = (Rt.P - L.P + L.r * uL * (SL - uL) - Rt.r * uR * (SR - uR)) * rcp(den);
+        const bool left = Ss >= R(0);
+        const Prim<R>& K = left ? L : Rt;
+        const R S = left ? SL : SR, EK = left ? EL : ER, uK = K.v[D], irK = left ? irL : irR;
+        const R* FK = left ? FL : FR;
+        const R chi = K.r * (S - uK) * rcp(S - Ss);
+        R Us[5];
         Us[0] = chi;
-        for (int k = 0; k < 3; ++k) Us[1 + k] = chi * K.v[k];
+        for (int q = 0; q < 3; ++q) Us[1 + q] = chi * K.v[q];
         Us[1 + D] = chi * Ss;
-        Us[4] = chi * (EK / K.r + (Ss - uK) * (Ss + K.P / (K.r * (S - uK))));
-        const double UK[5] = {K.r, K.r * K.v[0], K.r * K.v[1], K.r * K.v[2], EK};
+        Us[4] = chi * (EK * irK + (Ss - uK) * (Ss + K.P * irK * rcp(S - uK)));
+        const R UK[5] = {K.r, K.r * K.v[0], K.r * K.v[1], K.r * K.v[2], EK};
         for (int q = 0; q < 5; ++q) F[q] = FK[q] + S * (Us[q] - UK[q]);
     } else {
-        const double UL[5] = {L.r, L.r * L.v[0], L.r * L.v[1], L.r * L.v[2], EL};
-        const double UR[5] = {R.r, R.r * R.v[0], R.r * R.v[1], R.r * R.v[2], ER};
-        for (int q = 0; q < 5; ++q) F[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) / (SR - SL);
+        const R UL[5] = {L.r, L.r * L.v[0], L.r * L.v[1], L.r * L.v[2], EL};
+        const R UR[5] = {Rt.r, Rt.r * Rt.v[0], Rt.r * Rt.v[1], Rt.r * Rt.v[2], ER};
+        const R iw = rcp(SR - SL);
+        for (int q = 0; q < 5; ++q) F[q] = (SR * FL[q] - SL * FR[q] + SL * SR * (UR[q] - UL[q])) * iw;
     }
 }
 
-__device__ __forceinline__ double limited_slope(double dl, double dr, int lim)
+template <typename R>
+__device__ __forceinline__ R limited_slope(R dl, R dr, int lim)
 {
-    if (lim == 2) return 0.5 * (dl + dr);  // no limiter
-    if (dl * dr <= 0.0) return 0.0;
-    const double s = dl > 0.0 ? 1.0 : -1.0;
-    const double x = fabs(dl), y = fabs(dr);
-    const double m = fmin(x, y);
-    if (lim == 0) return s * m;            // minmod
-    return s * fmin(2.0 * m, 0.5 * fabs(dl + dr));  // monotonized central
+    if (lim == 2) return R(0.5) * (dl + dr);  // no limiter
+    if (dl * dr <= R(0)) return R(0);
+    const R s = dl > R(0) ? R(1) : R(-1);
+    const R m = fmin(fabs(dl), fabs(dr));
+    if (lim == 0) return s * m;                          // minmod
+    return s * fmin(R(2) * m, R(0.5) * fabs(dl + dr));  // monotonized central
 }
 
 __device__ __forceinline__ double absorption(const GasParams& p, const double* kF, long long i, double rho)
@@ -144,7 +205,7 @@ __device__ __forceinline__ void gas_source(const GasParams& p, double k, const d
     }
 }
 
-__device__ __forceinline__ bool finite_prim(const Prim& w)
+__device__ __forceinline__ bool finite_prim(const Prim<double>& w)
 {
     return isfinite(w.r) && isfinite(w.v[0]) && isfinite(w.v[1]) && isfinite(w.v[2]) && isfinite(w.P);
 }
@@ -152,25 +213,41 @@ __device__ __forceinline__ bool finite_prim(const Prim& w)
 __device__ __forceinline__ long long first_index() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long index_stride() { return (long long)gridDim.x * blockDim.x; }
 
+// flux difference of face arrays of type R, accumulated in FP64
+template <typename R>
+__device__ __forceinline__ void add_divergence(const GasParams& p, const GasArrays& a, const long long lo[3],
+                                               const long long hi[3], double dU[5])
+{
+    for (int d = 0; d < 3; ++d) {
+        if (p.n[d] <= 1) continue;
+        for (int q = 0; q < 5; ++q) {
+            const R* F = reinterpret_cast<const R*>(a.flux[d][q]);
+            dU[q] -= (widen(F[hi[d]]) - widen(F[lo[d]])) * p.inv_dx[d];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------- predictor
 
-template <int D>
+template <typename R, int D>
 __global__ void __launch_bounds__(GAS_THREADS) gas_pred_flux_kernel(GasParams p, GasArrays a)
 {
     int fe[3];
     gas_pred_faces(p, D, fe);
     const long long nf = gas_count(fe);
+    const Consts<R> k = consts<R>(p);
     for (long long f = first_index(); f < nf; f += index_stride()) {
         long long iL, iR;
-        double sL[3], sR[3];
+        int sL[3], sR[3];
         gas_pred_flux_cells(p, D, f, &iL, sL, &iR, sR);
-        const Prim WL = load_prim(p, a, iL, sL), WR = load_prim(p, a, iR, sR);
-        double F[5];
-        hllc<D>(p, WL, WR, F);
-        for (int q = 0; q < 5; ++q) a.flux[D][q][f] = F[q];
+        const Prim<R> WL = load_prim_t<R>(p, a, iL, sL), WR = load_prim_t<R>(p, a, iR, sR);
+        R F[5];
+        hllc<R, D>(k, WL, WR, F);
+        for (int q = 0; q < 5; ++q) reinterpret_cast<R*>(a.flux[D][q])[f] = F[q];
     }
 }
 
+template <typename R>
 __global__ void __launch_bounds__(GAS_THREADS) gas_pred_update_kernel(GasParams p, GasArrays a)
 {
     const long long ne = gas_count(p.m);
@@ -178,73 +255,86 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_pred_update_kernel(GasParams 
     unsigned long long floors = 0;
     for (long long i = first_index(); i < ne; i += index_stride()) {
         long long k, lo[3], hi[3];
-        double s[3];
+        int s[3];
         bool inside;
         gas_pred_update_cells(p, i, &k, s, &inside, lo, hi);
-        const Prim W = load_prim(p, a, k, s);
+        const Prim<double> W = load_prim(p, a, k, s);
         double U[5], dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         to_cons(p, W, U);
-        for (int d = 0; d < 3; ++d) {
-            if (p.n[d] <= 1) continue;
-            for (int q = 0; q < 5; ++q) dU[q] -= (a.flux[d][q][hi[d]] - a.flux[d][q][lo[d]]) * p.inv_dx[d];
-        }
-        const double G[3] = {a.G[0][k] * s[0], a.G[1][k] * s[1], a.G[2][k] * s[2]};
+        add_divergence<R>(p, a, lo, hi, dU);
+        const double G[3] = {flip(a.G[0][k], s[0]), flip(a.G[1][k], s[1]), flip(a.G[2][k], s[2])};
         double S[5];
         gas_source(p, absorption(p, a.kF, k, W.r), W.v, a.E[k], G, S);
-        double Uh[5];
+        double Uh[5], inv_r;
         for (int q = 0; q < 5; ++q) Uh[q] = U[q] + hdt * dU[q] + hdt * S[q];
-        Prim Wh;
-        if (to_prim(p, Uh, Wh) && inside) ++floors;
-        a.wh[0][i] = Wh.r;
-        for (int d = 0; d < 3; ++d) a.wh[1 + d][i] = Wh.v[d];
-        a.wh[4][i] = Wh.P;
+        Prim<double> Wh;
+        if (to_prim(p, Uh, Wh, inv_r) && inside) ++floors;
+        const double w5[5] = {Wh.r, Wh.v[0], Wh.v[1], Wh.v[2], Wh.P};
+        for (int q = 0; q < 5; ++q) a.wh[q][i] = w5[q];
+        if (a.wh32[0])
+            for (int q = 0; q < 5; ++q) a.wh32[q][i] = d2f_trunc(w5[q]);
     }
     if (floors) atomicAdd(&a.counters[0], floors);
 }
 
 // ---------------------------------------------------------------------------------------- corrector
 
-template <int D>
+template <typename R>
+__device__ __forceinline__ R load_half(const GasArrays& a, int q, long long x);
+template <>
+__device__ __forceinline__ double load_half<double>(const GasArrays& a, int q, long long x)
+{
+    return a.wh[q][x];
+}
+template <>
+__device__ __forceinline__ float load_half<float>(const GasArrays& a, int q, long long x)
+{
+    return a.wh32[q][x];
+}
+
+template <typename R, int D>
 __global__ void __launch_bounds__(GAS_THREADS) gas_corr_flux_kernel(GasParams p, GasArrays a)
 {
     int fe[3];
     gas_corr_faces(p, D, fe);
     const long long nf = gas_count(fe);
+    const Consts<R> k = consts<R>(p);
     for (long long f = first_index(); f < nf; f += index_stride()) {
         // W^{n+1/2} of the cells f - 2 e_D .. f + e_D
         long long x[4];
         gas_corr_flux_cells(p, D, f, x);
-        double w[4][5];
+        R w[4][5];
         for (int j = 0; j < 4; ++j)
-            for (int q = 0; q < 5; ++q) w[j][q] = a.wh[q][x[j]];
+            for (int q = 0; q < 5; ++q) w[j][q] = load_half<R>(a, q, x[j]);
         // limited slopes of the cells on each side of the face; a slope whose face values have
         // rho <= 0 or P <= 0 is zeroed (all components)
-        Prim WL, WR;
+        Prim<R> WL, WR;
         for (int side = 0; side < 2; ++side) {
-            const double* wm = w[side];
-            const double* w0 = w[side + 1];
-            const double* wp = w[side + 2];
-            double sl[5];
-            for (int q = 0; q < 5; ++q) sl[q] = limited_slope(w0[q] - wm[q], wp[q] - w0[q], p.limiter);
+            const R* wm = w[side];
+            const R* w0 = w[side + 1];
+            const R* wp = w[side + 2];
+            R sl[5];
+            for (int q = 0; q < 5; ++q) sl[q] = limited_slope<R>(w0[q] - wm[q], wp[q] - w0[q], p.limiter);
             bool bad = false;
-            for (int h = 0; h < 2; ++h) {
-                const double sg = h ? 0.5 : -0.5;
-                bad = bad || !(w0[0] + sg * sl[0] > 0.0) || !(w0[4] + sg * sl[4] > 0.0);
+            for (int hs = 0; hs < 2; ++hs) {
+                const R sg = hs ? R(0.5) : R(-0.5);
+                bad = bad || !(w0[0] + sg * sl[0] > R(0)) || !(w0[4] + sg * sl[4] > R(0));
             }
             if (bad)
-                for (int q = 0; q < 5; ++q) sl[q] = 0.0;
-            Prim& W = side ? WR : WL;
-            const double h = side ? -0.5 : 0.5;  // cell A - e_D: its high face; cell A: its low face
+                for (int q = 0; q < 5; ++q) sl[q] = R(0);
+            Prim<R>& W = side ? WR : WL;
+            const R h = side ? R(-0.5) : R(0.5);  // cell f - e_D: its high face; cell f: its low face
             W.r = w0[0] + h * sl[0];
-            for (int k = 0; k < 3; ++k) W.v[k] = w0[1 + k] + h * sl[1 + k];
+            for (int q = 0; q < 3; ++q) W.v[q] = w0[1 + q] + h * sl[1 + q];
             W.P = w0[4] + h * sl[4];
         }
-        double F[5];
-        hllc<D>(p, WL, WR, F);
-        for (int q = 0; q < 5; ++q) a.flux[D][q][f] = F[q];
+        R F[5];
+        hllc<R, D>(k, WL, WR, F);
+        for (int q = 0; q < 5; ++q) reinterpret_cast<R*>(a.flux[D][q])[f] = F[q];
     }
 }
 
+template <typename R>
 __global__ void __launch_bounds__(GAS_THREADS) gas_corr_update_kernel(GasParams p, GasArrays a)
 {
     const long long nc = gas_count(p.n);
@@ -252,14 +342,11 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_corr_update_kernel(GasParams 
     for (long long i = first_index(); i < nc; i += index_stride()) {
         long long x, lo[3], hi[3];
         gas_corr_update_cells(p, i, &x, lo, hi);
-        const double one[3] = {1.0, 1.0, 1.0};
-        const Prim W = load_prim(p, a, i, one);
+        const int one[3] = {1, 1, 1};
+        const Prim<double> W = load_prim(p, a, i, one);
         double U[5], dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         to_cons(p, W, U);
-        for (int d = 0; d < 3; ++d) {
-            if (p.n[d] <= 1) continue;
-            for (int q = 0; q < 5; ++q) dU[q] -= (a.flux[d][q][hi[d]] - a.flux[d][q][lo[d]]) * p.inv_dx[d];
-        }
+        add_divergence<R>(p, a, lo, hi, dU);
         const double rh = a.wh[0][x];
         const double vh[3] = {a.wh[1][x], a.wh[2][x], a.wh[3][x]};
         const double kh = absorption(p, a.kF, i, rh);
@@ -267,14 +354,14 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_corr_update_kernel(GasParams 
         const double G[3] = {a.G[0][i], a.G[1][i], a.G[2][i]};
         double S[5];
         gas_source(p, kh, vh, E, G, S);
-        double U1[5];
+        double U1[5], inv_r;
         for (int q = 0; q < 5; ++q) U1[q] = U[q] + p.dt * dU[q] + p.dt * S[q];
-        Prim W1;
-        if (to_prim(p, U1, W1)) ++floors;
+        Prim<double> W1;
+        if (to_prim(p, U1, W1, inv_r)) ++floors;
         if (!finite_prim(W1)) ++bad;
         a.rho[i] = W1.r;
         for (int d = 0; d < 3; ++d) a.v[d][i] = W1.v[d];
-        a.T[i] = W1.P * p.mu_over_kB / W1.r;
+        a.T[i] = W1.P * p.mu_over_kB * inv_r;
         a.pend[0][i] = kh;
         for (int d = 0; d < 3; ++d) a.pend[1 + d][i] = vh[d];
         a.pend[4][i] = E;
@@ -292,8 +379,8 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_correct_kernel(GasParams p, G
     const double hdt = 0.5 * p.dt;
     unsigned long long floors = 0, bad = 0;
     for (long long i = first_index(); i < nc; i += index_stride()) {
-        const double one[3] = {1.0, 1.0, 1.0};
-        const Prim W = load_prim(p, a, i, one);
+        const int one[3] = {1, 1, 1};
+        const Prim<double> W = load_prim(p, a, i, one);
         double U[5];
         to_cons(p, W, U);
         const double kh = a.pend[0][i];
@@ -304,11 +391,12 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_correct_kernel(GasParams p, G
         gas_source(p, kh, vh, a.E[i], G1, S1);
         gas_source(p, kh, vh, a.pend[4][i], G0, S0);
         for (int q = 1; q < 5; ++q) U[q] = U[q] + hdt * (S1[q] - S0[q]);
-        Prim W1;
-        if (to_prim(p, U, W1)) ++floors;
+        Prim<double> W1;
+        double inv_r;
+        if (to_prim(p, U, W1, inv_r)) ++floors;
         if (!finite_prim(W1)) ++bad;
         for (int d = 0; d < 3; ++d) a.v[d][i] = W1.v[d];
-        a.T[i] = W1.P * p.mu_over_kB / W1.r;
+        a.T[i] = W1.P * p.mu_over_kB * inv_r;
     }
     if (floors) atomicAdd(&a.counters[0], floors);
     if (bad) atomicAdd(&a.counters[1], bad);
@@ -320,6 +408,22 @@ int blocks_for(long long n)
     return (int)(b < 1 ? 1 : (b > (1LL << 30) ? (1LL << 30) : b));
 }
 
+template <typename R>
+void pred_flux(const GasParams& p, const GasArrays& a, int d, int nb, cudaStream_t s)
+{
+    if (d == 0) gas_pred_flux_kernel<R, 0><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    else if (d == 1) gas_pred_flux_kernel<R, 1><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    else gas_pred_flux_kernel<R, 2><<<nb, GAS_THREADS, 0, s>>>(p, a);
+}
+
+template <typename R>
+void corr_flux(const GasParams& p, const GasArrays& a, int d, int nb, cudaStream_t s)
+{
+    if (d == 0) gas_corr_flux_kernel<R, 0><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    else if (d == 1) gas_corr_flux_kernel<R, 1><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    else gas_corr_flux_kernel<R, 2><<<nb, GAS_THREADS, 0, s>>>(p, a);
+}
+
 }  // namespace
 
 cudaError_t launch_gas_pred_flux(const GasParams& p, const GasArrays& a, int d, cudaStream_t s)
@@ -327,15 +431,16 @@ cudaError_t launch_gas_pred_flux(const GasParams& p, const GasArrays& a, int d, 
     int e[3];
     gas_pred_faces(p, d, e);
     const int nb = blocks_for(gas_count(e));
-    if (d == 0) gas_pred_flux_kernel<0><<<nb, GAS_THREADS, 0, s>>>(p, a);
-    else if (d == 1) gas_pred_flux_kernel<1><<<nb, GAS_THREADS, 0, s>>>(p, a);
-    else gas_pred_flux_kernel<2><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    if (p.split) pred_flux<float>(p, a, d, nb, s);
+    else pred_flux<double>(p, a, d, nb, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gas_pred_update(const GasParams& p, const GasArrays& a, cudaStream_t s)
 {
-    gas_pred_update_kernel<<<blocks_for(gas_count(p.m)), GAS_THREADS, 0, s>>>(p, a);
+    const int nb = blocks_for(gas_count(p.m));
+    if (p.split) gas_pred_update_kernel<float><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    else gas_pred_update_kernel<double><<<nb, GAS_THREADS, 0, s>>>(p, a);
     return cudaGetLastError();
 }
 
@@ -344,15 +449,16 @@ cudaError_t launch_gas_corr_flux(const GasParams& p, const GasArrays& a, int d, 
     int e[3];
     gas_corr_faces(p, d, e);
     const int nb = blocks_for(gas_count(e));
-    if (d == 0) gas_corr_flux_kernel<0><<<nb, GAS_THREADS, 0, s>>>(p, a);
-    else if (d == 1) gas_corr_flux_kernel<1><<<nb, GAS_THREADS, 0, s>>>(p, a);
-    else gas_corr_flux_kernel<2><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    if (p.split) corr_flux<float>(p, a, d, nb, s);
+    else corr_flux<double>(p, a, d, nb, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gas_corr_update(const GasParams& p, const GasArrays& a, cudaStream_t s)
 {
-    gas_corr_update_kernel<<<blocks_for(gas_count(p.n)), GAS_THREADS, 0, s>>>(p, a);
+    const int nb = blocks_for(gas_count(p.n));
+    if (p.split) gas_corr_update_kernel<float><<<nb, GAS_THREADS, 0, s>>>(p, a);
+    else gas_corr_update_kernel<double><<<nb, GAS_THREADS, 0, s>>>(p, a);
     return cudaGetLastError();
 }
 

@@ -85,7 +85,8 @@ struct GridState {
     // gas step scratch (allocated by the first rhd_gas_step): W^{n+1/2} on the extended grid, the face
     // fluxes of each active direction, and what rhd_gas_correct needs
     double* gas_wh[5] = {nullptr};
-    double* gas_flux[3][5] = {{nullptr}};
+    float* gas_wh32[5] = {nullptr};  // split grids: FP32 copy of W^{n+1/2}
+    double* gas_flux[3][5] = {{nullptr}};  // FP32 values on split grids
     double* gas_pend[8] = {nullptr};
     bool gas_pending = false;     // a gas step waits for its source correction
     double gas_dt = 0.0;
@@ -329,7 +330,10 @@ void free_grid(GridState& gs)
     dfree(gs.uhalf);
     dfree(gs.um32);
     dfree(gs.gas4);
-    for (int q = 0; q < 5; ++q) dfree(gs.gas_wh[q]);
+    for (int q = 0; q < 5; ++q) {
+        dfree(gs.gas_wh[q]);
+        dfree(gs.gas_wh32[q]);
+    }
     for (int d = 0; d < 3; ++d)
         for (int q = 0; q < 5; ++q) dfree(gs.gas_flux[d][q]);
     for (int q = 0; q < 8; ++q) dfree(gs.gas_pend[q]);
@@ -1442,6 +1446,10 @@ GasParams gas_params(const GridState& gs, double dt)
     p.beta_tau = gs.desc.beta_tau;
     p.limiter = gs.desc.limiter;
     p.dt = dt;
+    p.split = gs.desc.precision == RHD_SPLIT;
+    p.f_gamma = (float)p.gamma;
+    p.f_inv_gm1 = (float)p.inv_gm1;
+    p.f_inv_mu = (float)p.inv_mu;
     return p;
 }
 
@@ -1452,10 +1460,15 @@ GasArrays gas_arrays(rhd_ctx* ctx, GridState& gs)
     a.rho = gs.rho;
     a.T = gs.T;
     for (int d = 0; d < 3; ++d) a.v[d] = gs.v[d];
+    a.rho32 = gs.rho32;
+    for (int d = 0; d < 3; ++d) a.v32[d] = gs.v32[d];
     a.kF = gs.has_kF ? gs.kF : nullptr;
     a.E = gs.U[ctx->cur][0];
     for (int d = 0; d < 3; ++d) a.G[d] = gs.U[ctx->cur][1 + d];
-    for (int q = 0; q < 5; ++q) a.wh[q] = gs.gas_wh[q];
+    for (int q = 0; q < 5; ++q) {
+        a.wh[q] = gs.gas_wh[q];
+        a.wh32[q] = gs.gas_wh32[q];
+    }
     for (int d = 0; d < 3; ++d)
         for (int q = 0; q < 5; ++q) a.flux[d][q] = gs.gas_flux[d][q];
     for (int q = 0; q < 8; ++q) a.pend[q] = gs.gas_pend[q];
@@ -1469,13 +1482,16 @@ rhd_status gas_prepare(rhd_ctx* ctx, GridState& gs, const GasParams& p)
 {
     rhd_status st;
     if (!gs.gas_wh[0]) {
-        for (int q = 0; q < 5; ++q)
+        const size_t fb = p.split ? sizeof(float) : sizeof(double);
+        for (int q = 0; q < 5; ++q) {
             if ((st = dalloc(ctx, (void**)&gs.gas_wh[q], sizeof(double) * (size_t)gas_count(p.m)))) return st;
+            if (p.split && (st = dalloc(ctx, (void**)&gs.gas_wh32[q], sizeof(float) * (size_t)gas_count(p.m))))
+                return st;
+        }
         for (int d = 0; d < 3; ++d) {
             if (gs.desc.n[d] <= 1) continue;
             for (int q = 0; q < 5; ++q)
-                if ((st = dalloc(ctx, (void**)&gs.gas_flux[d][q], sizeof(double) * (size_t)gas_face_capacity(p, d))))
-                    return st;
+                if ((st = dalloc(ctx, (void**)&gs.gas_flux[d][q], fb * (size_t)gas_face_capacity(p, d)))) return st;
         }
         for (int q = 0; q < 8; ++q)
             if ((st = dalloc(ctx, (void**)&gs.gas_pend[q], sizeof(double) * (size_t)gs.ncell))) return st;
@@ -1485,8 +1501,10 @@ rhd_status gas_prepare(rhd_ctx* ctx, GridState& gs, const GasParams& p)
         if (gs.v[d]) continue;
         if ((st = dalloc(ctx, (void**)&gs.v[d], sizeof(double) * (size_t)gs.ncell))) return st;
         RHD_CUDA(ctx, cudaMemsetAsync(gs.v[d], 0, sizeof(double) * (size_t)gs.ncell, ctx->stream));
-        if (gs.desc.precision == RHD_SPLIT && !gs.v32[d])
-            if ((st = dalloc(ctx, (void**)&gs.v32[d], sizeof(float) * (size_t)gs.ncell))) return st;
+        if (gs.desc.precision == RHD_SPLIT) {
+            if (!gs.v32[d] && (st = dalloc(ctx, (void**)&gs.v32[d], sizeof(float) * (size_t)gs.ncell))) return st;
+            RHD_CUDA(ctx, cudaMemsetAsync(gs.v32[d], 0, sizeof(float) * (size_t)gs.ncell, ctx->stream));
+        }
         added = true;
     }
     if (added) {
@@ -1508,16 +1526,18 @@ rhd_status gas_refresh_copies(rhd_ctx* ctx, GridState& gs)
 }
 
 // bytes per cell of each gas kernel (each array read or written once per launch): the gas state is
-// 40 B (rho, T, v), W^{n+1/2} 40 B, one face-flux array 40 B per cell, the radiation 32 B, the
-// correction's record 64 B
+// 40 B (rho, T, v; the split predictor's fluxes read the FP32 rho, v and the FP64 T, 24 B), W^{n+1/2}
+// 40 B (+ its 20 B FP32 copy on split grids, which the corrector's fluxes read instead), one
+// face-flux array 40 B per cell (20 B split), the radiation 32 B, the correction's record 64 B
 double gas_alg_bytes(const GridState& gs, int k, int nact)
 {
-    const double kf = gs.has_kF ? 8.0 : 0.0;
+    const bool split = gs.desc.precision == RHD_SPLIT;
+    const double kf = gs.has_kF ? 8.0 : 0.0, fl = split ? 20.0 : 40.0;
     switch (k) {
-    case K_GAS_PRED_FLUX: return 40.0 + 40.0;
-    case K_GAS_PRED_UPDATE: return 40.0 + 32.0 + kf + 40.0 * nact + 40.0;
-    case K_GAS_CORR_FLUX: return 40.0 + 40.0;
-    case K_GAS_CORR_UPDATE: return 40.0 + 40.0 * nact + 32.0 + 32.0 + kf + 40.0 + 64.0;
+    case K_GAS_PRED_FLUX: return (split ? 24.0 : 40.0) + fl;
+    case K_GAS_PRED_UPDATE: return 40.0 + 32.0 + kf + fl * nact + 40.0 + (split ? 20.0 : 0.0);
+    case K_GAS_CORR_FLUX: return (split ? 20.0 : 40.0) + fl;
+    case K_GAS_CORR_UPDATE: return 40.0 + fl * nact + 32.0 + 32.0 + kf + 40.0 + 64.0;
     default: return 40.0 + 64.0 + 32.0 + 32.0;  // K_GAS_CORRECT
     }
 }

@@ -35,7 +35,7 @@ static void check_grid(const int n[3], const int lo[3], const int hi[3])
         for (long long f = 0; f < gas_count(fe); ++f) {
             check(f < cap[d], "predictor face", f, cap[d], n);
             long long iL, iR;
-            double sL[3], sR[3];
+            int sL[3], sR[3];
             gas_pred_flux_cells(p, d, f, &iL, sL, &iR, sR);
             check(iL >= 0 && iL < ncell, "predictor flux iL", iL, ncell, n);
             check(iR >= 0 && iR < ncell, "predictor flux iR", iR, ncell, n);
@@ -50,7 +50,7 @@ static void check_grid(const int n[3], const int lo[3], const int hi[3])
     }
     for (long long i = 0; i < next; ++i) {
         long long k, l[3], h[3];
-        double s[3];
+        int s[3];
         bool inside;
         gas_pred_update_cells(p, i, &k, s, &inside, l, h);
         check(k >= 0 && k < ncell, "predictor update cell", k, ncell, n);
@@ -81,9 +81,9 @@ int main(int argc, char** argv)
     if (argc == 6 && std::string_view(argv[1]) == "axis") {
         const int n = std::atoi(argv[2]), lo = std::atoi(argv[3]), hi = std::atoi(argv[4]), g = std::atoi(argv[5]);
         for (int c = -g; c < n + g; ++c) {
-            double s = 1.0;
+            int s = 1;
             const int q = gas_axis(c, n, lo, hi, s);
-            std::printf("%d %d %g\n", c, q, s);
+            std::printf("%d %d %d\n", c, q, s);
         }
         return 0;
     }

@@ -368,8 +368,9 @@ def test_device_pointers_and_errors(rhd):
     with pytest.raises(rhd.RhdError) as ei:
         g.radiation_subcycle(1, case["desc"]["c"] * 1.5, case["dt"] * 0.1)
     assert ei.value.status == rhd.ERR_CFL
-    with pytest.raises(rhd.RhdError):
-        g.gas_step(1.0)
+    with pytest.raises(rhd.RhdError) as ei:
+        g.gas_step(-1.0)
+    assert ei.value.status == rhd.ERR_ARG
     g.close()
     g2 = rhd.Grid(case["desc"])
     with pytest.raises(rhd.RhdError) as ei:
