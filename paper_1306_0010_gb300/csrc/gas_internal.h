@@ -28,7 +28,7 @@ struct GasParams {
     // split grids: the face fluxes (reconstruction, wave speeds, HLLC) in FP32 with these FP32 copies;
     // conversions, accumulation and sources stay FP64
     int split;
-    float f_gamma, f_inv_gm1, f_inv_mu;
+    float f_gamma, f_inv_gm1, f_inv_mu, f_inv_dx[3];
 };
 
 struct GasArrays {

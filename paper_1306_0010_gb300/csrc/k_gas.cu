@@ -16,8 +16,8 @@
 //
 // Precision: the flux kernels are templates on the arithmetic type R.  FP64 grids: R = double.  Split
 // grids: R = float for reconstruction, wave speeds and HLLC (inputs truncated to FP32 by integer bit
-// operations, FP32 fluxes stored), while the updates (flux differences, sources, conversions between
-// primitive and conserved variables) are FP64 on both.  Divisions are reciprocals (FP64: the hardware
+// operations, FP32 fluxes stored) and for the flux differences, while the accumulation, the sources and
+// the conversions between primitive and conserved variables are FP64 on both.  Divisions are reciprocals (FP64: the hardware
 // approximation refined by Newton-Raphson; FP32: the hardware approximation) times the numerator.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -42,9 +42,6 @@ __device__ __forceinline__ R flip(R x, int s)
 {
     return s < 0 ? -x : x;
 }
-
-__device__ __forceinline__ double widen(double x) { return x; }
-__device__ __forceinline__ double widen(float x) { return f2d_exact(x); }
 
 // physical constants in R
 template <typename R>
@@ -213,18 +210,34 @@ __device__ __forceinline__ bool finite_prim(const Prim<double>& w)
 __device__ __forceinline__ long long first_index() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long index_stride() { return (long long)gridDim.x * blockDim.x; }
 
-// flux difference of face arrays of type R, accumulated in FP64
+// minus the divergence of the stored face fluxes: FP64 fluxes in FP64; FP32 fluxes (split grids) in
+// FP32, then widened (their differences carry far less error than the FP32 fluxes themselves)
 template <typename R>
-__device__ __forceinline__ void add_divergence(const GasParams& p, const GasArrays& a, const long long lo[3],
-                                               const long long hi[3], double dU[5])
+__device__ __forceinline__ void flux_divergence(const GasParams& p, const GasArrays& a, const long long lo[3],
+                                                const long long hi[3], double dU[5]);
+template <>
+__device__ __forceinline__ void flux_divergence<double>(const GasParams& p, const GasArrays& a, const long long lo[3],
+                                                        const long long hi[3], double dU[5])
 {
+    for (int q = 0; q < 5; ++q) dU[q] = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (p.n[d] <= 1) continue;
+        for (int q = 0; q < 5; ++q) dU[q] -= (a.flux[d][q][hi[d]] - a.flux[d][q][lo[d]]) * p.inv_dx[d];
+    }
+}
+template <>
+__device__ __forceinline__ void flux_divergence<float>(const GasParams& p, const GasArrays& a, const long long lo[3],
+                                                       const long long hi[3], double dU[5])
+{
+    float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     for (int d = 0; d < 3; ++d) {
         if (p.n[d] <= 1) continue;
         for (int q = 0; q < 5; ++q) {
-            const R* F = reinterpret_cast<const R*>(a.flux[d][q]);
-            dU[q] -= (widen(F[hi[d]]) - widen(F[lo[d]])) * p.inv_dx[d];
+            const float* F = reinterpret_cast<const float*>(a.flux[d][q]);
+            acc[q] -= (F[hi[d]] - F[lo[d]]) * p.f_inv_dx[d];
         }
     }
+    for (int q = 0; q < 5; ++q) dU[q] = f2d_exact(acc[q]);
 }
 
 // ---------------------------------------------------------------------------------------- predictor
@@ -259,9 +272,9 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_pred_update_kernel(GasParams 
         bool inside;
         gas_pred_update_cells(p, i, &k, s, &inside, lo, hi);
         const Prim<double> W = load_prim(p, a, k, s);
-        double U[5], dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        double U[5], dU[5];
         to_cons(p, W, U);
-        add_divergence<R>(p, a, lo, hi, dU);
+        flux_divergence<R>(p, a, lo, hi, dU);
         const double G[3] = {flip(a.G[0][k], s[0]), flip(a.G[1][k], s[1]), flip(a.G[2][k], s[2])};
         double S[5];
         gas_source(p, absorption(p, a.kF, k, W.r), W.v, a.E[k], G, S);
@@ -344,9 +357,9 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_corr_update_kernel(GasParams 
         gas_corr_update_cells(p, i, &x, lo, hi);
         const int one[3] = {1, 1, 1};
         const Prim<double> W = load_prim(p, a, i, one);
-        double U[5], dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        double U[5], dU[5];
         to_cons(p, W, U);
-        add_divergence<R>(p, a, lo, hi, dU);
+        flux_divergence<R>(p, a, lo, hi, dU);
         const double rh = a.wh[0][x];
         const double vh[3] = {a.wh[1][x], a.wh[2][x], a.wh[3][x]};
         const double kh = absorption(p, a.kF, i, rh);
@@ -383,14 +396,14 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_correct_kernel(GasParams p, G
         const Prim<double> W = load_prim(p, a, i, one);
         double U[5];
         to_cons(p, W, U);
+        // S_e,gas is linear in the radiation state: S(W^{n+1/2}, U_rad^{n+1}) - S(W^{n+1/2}, U_rad^n) is S of
+        // the radiation's change
         const double kh = a.pend[0][i];
         const double vh[3] = {a.pend[1][i], a.pend[2][i], a.pend[3][i]};
-        const double G1[3] = {a.G[0][i], a.G[1][i], a.G[2][i]};
-        const double G0[3] = {a.pend[5][i], a.pend[6][i], a.pend[7][i]};
-        double S1[5], S0[5];
-        gas_source(p, kh, vh, a.E[i], G1, S1);
-        gas_source(p, kh, vh, a.pend[4][i], G0, S0);
-        for (int q = 1; q < 5; ++q) U[q] = U[q] + hdt * (S1[q] - S0[q]);
+        const double dG[3] = {a.G[0][i] - a.pend[5][i], a.G[1][i] - a.pend[6][i], a.G[2][i] - a.pend[7][i]};
+        double dS[5];
+        gas_source(p, kh, vh, a.E[i] - a.pend[4][i], dG, dS);
+        for (int q = 1; q < 5; ++q) U[q] = U[q] + hdt * dS[q];
         Prim<double> W1;
         double inv_r;
         if (to_prim(p, U, W1, inv_r)) ++floors;

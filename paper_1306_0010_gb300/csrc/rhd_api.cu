@@ -1450,6 +1450,7 @@ GasParams gas_params(const GridState& gs, double dt)
     p.f_gamma = (float)p.gamma;
     p.f_inv_gm1 = (float)p.inv_gm1;
     p.f_inv_mu = (float)p.inv_mu;
+    for (int d = 0; d < 3; ++d) p.f_inv_dx[d] = (float)p.inv_dx[d];
     return p;
 }
 
