@@ -128,7 +128,7 @@ def mode_state(N, P0, C, Ch, tau, gamma=5.0 / 3.0, amplitude=1e-6, mode=None):
     x = x / x[0] * amplitude
     X = (np.arange(N) + 0.5) / N
     ph = np.exp(2j * math.pi * X)
-    f = lambda q: (x[q] * ph).real.reshape(1, 1, N)
+    f = lambda q: np.ascontiguousarray((x[q] * ph).real).reshape(1, 1, N)
     return {"rho": 1.0 + f(0), "vx": f(1), "T": 1.0 + f(2), "E": P0 + f(3), "Fx": C * f(4)}, Z
 
 
