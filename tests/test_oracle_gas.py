@@ -341,3 +341,72 @@ def test_swapping_x_and_y_swaps_the_result():
     assert np.max(np.abs(g["rho"][0] - g["rho"][0].T)) < 1e-13
     assert np.max(np.abs(g["vx"][0] - g["vy"][0].T)) < 1e-13
     assert np.max(np.abs(g["T"][0] - g["T"][0].T)) < 1e-13
+
+
+# ----------------------------------------------------------------------------- the Riemann solver
+
+def random_states(seed, n=2000, mach=3.0):
+    r = np.random.default_rng(seed)
+    W = [np.exp(r.normal(0, 1, n))] + [r.normal(0, mach, n) for _ in range(3)] + [np.exp(r.normal(0, 1, n))]
+    return W
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hllc_is_consistent_with_the_physical_flux(d):
+    # F(W, W) = F(W): identical states on both sides of a face
+    W = random_states(11 + d)
+    F = gas.hllc(W, W, d, 1.4)
+    Fx, _ = gas.euler_flux(W, d, 1.4)
+    for q in range(5):
+        assert np.allclose(F[q], Fx[q], rtol=1e-12, atol=1e-12 * np.max(np.abs(Fx[q])))
+
+
+def test_hllc_upwinds_supersonic_flow():
+    # every wave moves right (u - a > 0 on both sides): the flux is the left state's; left-moving: the right's
+    r = np.random.default_rng(5)
+    n = 500
+    L = [np.exp(r.normal(0, 0.3, n)), 5.0 + r.uniform(0, 1, n), r.normal(0, 1, n), r.normal(0, 1, n),
+         np.exp(r.normal(0, 0.3, n))]
+    R = [np.exp(r.normal(0, 0.3, n)), 5.0 + r.uniform(0, 1, n), r.normal(0, 1, n), r.normal(0, 1, n),
+         np.exp(r.normal(0, 0.3, n))]
+    F = gas.hllc(L, R, 0, 1.4)
+    FL, _ = gas.euler_flux(L, 0, 1.4)
+    for q in range(5):
+        assert np.array_equal(F[q], FL[q])
+    Lm = [L[0], -L[1], L[2], L[3], L[4]]
+    Rm = [R[0], -R[1], R[2], R[3], R[4]]
+    F = gas.hllc(Lm, Rm, 0, 1.4)
+    FR, _ = gas.euler_flux(Rm, 0, 1.4)
+    for q in range(5):
+        assert np.array_equal(F[q], FR[q])
+
+
+def test_hllc_resolves_an_isolated_moving_contact_exactly():
+    # equal pressure and normal velocity u, any density and tangential velocities: the exact Godunov flux
+    # is the upwind side's physical flux (the contact moves at u), which HLLC reproduces
+    r = np.random.default_rng(8)
+    n = 400
+    u = r.normal(0, 0.5, n)
+    P = np.exp(r.normal(0, 0.3, n))
+    L = [np.exp(r.normal(0, 1, n)), u, r.normal(0, 1, n), r.normal(0, 1, n), P]
+    R = [np.exp(r.normal(0, 1, n)), u, r.normal(0, 1, n), r.normal(0, 1, n), P]
+    F = gas.hllc(L, R, 0, 1.4)
+    FL, _ = gas.euler_flux(L, 0, 1.4)
+    FR, _ = gas.euler_flux(R, 0, 1.4)
+    for q in range(5):
+        want = np.where(u >= 0, FL[q], FR[q])
+        assert np.allclose(F[q], want, rtol=1e-12, atol=1e-12 * np.max(np.abs(want)))
+
+
+def test_hllc_mirror_symmetry():
+    # reflecting the problem (swap sides, negate normal velocities) negates the mass, tangential momentum
+    # and energy fluxes and keeps the normal momentum flux
+    L = random_states(21, n=300)
+    R = random_states(22, n=300)
+    F = gas.hllc(L, R, 1, 1.4)
+    Lm = [R[0], R[1], -R[2], R[3], R[4]]
+    Rm = [L[0], L[1], -L[2], L[3], L[4]]
+    Fm = gas.hllc(Lm, Rm, 1, 1.4)
+    sign = [-1, -1, 1, -1, -1]
+    for q in range(5):
+        assert np.allclose(Fm[q], sign[q] * F[q], rtol=1e-10, atol=1e-10 * np.max(np.abs(F[q])))
