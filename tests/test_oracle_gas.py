@@ -410,3 +410,31 @@ def test_hllc_mirror_symmetry():
     sign = [-1, -1, 1, -1, -1]
     for q in range(5):
         assert np.allclose(Fm[q], sign[q] * F[q], rtol=1e-10, atol=1e-10 * np.max(np.abs(F[q])))
+
+
+def test_reflecting_walls_pass_no_mass():
+    # gas streaming into a reflecting wall: the mirrored ghost state (normal velocity negated) makes the
+    # wall's mass and energy fluxes vanish, so the totals stay exact while the gas piles up at the wall
+    n = 32
+    d = desc1(n, bc="reflect")
+    x = (np.arange(n) + 0.5) / n
+    rho = (1.0 + 0.3 * np.sin(2 * np.pi * x)).reshape(1, 1, n)
+    g0 = state(rho, [0.5, 0.2, 0.0], np.ones_like(rho))
+    t0 = totals(d, g0)
+    g = run(d, g0, 0.1)
+    t1 = totals(d, g)
+    assert abs(t1[0] - t0[0]) <= 1e-13 * t0[0]
+    assert abs(t1[4] - t0[4]) <= 1e-13 * t0[4]
+    assert abs(t1[2] - t0[2]) <= 1e-13 * abs(t0[2])  # tangential momentum passes no wall either
+    assert g["rho"][0, 0, -1] > rho[0, 0, -1] + 0.1   # the stream piles up at the high wall
+
+
+def test_negative_internal_energy_is_set_to_zero_and_flagged():
+    d = {"gamma": 1.4}
+    U = [np.array([1.0, 2.0]), np.array([3.0, 0.5]), np.array([0.0, 0.0]), np.array([0.0, 0.0]),
+         np.array([4.0, 1.0])]  # cell 0: E_gas = 4 < rho v^2 / 2 = 4.5
+    W, neg = gas.primitive(d, U)
+    assert list(neg) == [True, False]
+    assert W[4][0] == 0.0
+    assert W[4][1] == pytest.approx(0.4 * (1.0 - 0.5 * 0.5 * 0.25))
+
