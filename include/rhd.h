@@ -17,6 +17,11 @@
  *   frozen gas state.  The flux-limiting condition |F| <= cE (Eq. m1:fluxlimit) is re-imposed after
  *   each stage.
  *
+ * Around the subcycles (Section 3.1 steps 1-3 and 6): the time steps (rhd_max_signal_speed,
+ * rhd_max_optical_depth, rhd_suggest_chat, rhd_time_steps), the gas step (rhd_gas_step: the Euler
+ * equations with the explicit gas sources, one van Leer step with HLLC fluxes) and its second-order
+ * source correction after the subcycles (rhd_gas_correct).
+ *
  * Conventions
  *   - Every array is dense FP64 over the interior cells only, x fastest: idx = i + nx*(j + ny*k).
  *     A direction with n = 1 is inactive (1D: ny = nz = 1; 2D: nz = 1).  Active directions need
@@ -41,7 +46,7 @@
 extern "C" {
 #endif
 
-#define RHD_ABI_VERSION 1
+#define RHD_ABI_VERSION 2  /* 2: rhd_stats gained the gas-step counters; the gas-step entry points */
 
 typedef struct rhd_ctx rhd_ctx; /* opaque, library-owned */
 

@@ -60,7 +60,7 @@ def test_struct_layout_matches_header(tmp_path):
 def test_identification_and_argument_errors(lib):
     from paper_1306_0010_gb300 import rhd, workloads as wl
 
-    assert lib.rhd_abi_version() == 1
+    assert lib.rhd_abi_version() == 2
     assert lib.rhd_built_arch() == 103
     # NULL out pointer
     desc = rhd.desc_struct(wl.base_desc((8, 8, 8), (0.1, 0.1, 0.1)))
