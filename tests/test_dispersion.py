@@ -121,3 +121,21 @@ def test_oracle_propagates_the_acoustic_mode_at_the_predicted_speed_and_damping(
     assert errs[0][0] < 1e-3 and errs[0][1] < 0.12, errs
     assert errs[1][0] < 5e-4 and errs[1][1] < 0.05, errs
     assert errs[1][0] < errs[0][0] and errs[1][1] < errs[0][1], errs
+
+
+def test_rsla_criterion_keeps_the_acoustic_mode():
+    """Gas-dominated case (P_0 = 1e-3, C = 1e4): while Chat >= tau (the static-diffusion criterion,
+    Eq. rsla:staticdiffreq, at rest) the acoustic mode with the reduced speed stays within a few per
+    cent of the mode with chat = c; well beyond it (tau = 10 Chat) its speed and damping change where the
+    energy exchange still matters (Chat = 10, 100: tau ~ P_0 C).  The paper notes the criterion is
+    sufficient, not necessary: at Chat = 1000, tau = 10^4 >> P_0 C the mode is adiabatic either way."""
+    P0, C = 1e-3, 1e4
+    for Ch in (10.0, 100.0, 1000.0):
+        for tau in np.logspace(-2, math.log10(Ch), 12):
+            Za, _ = dsp.acoustic_mode(P0, C, Ch, tau)
+            Zc, _ = dsp.acoustic_mode(P0, C, C, tau)
+            assert abs(Za - Zc) <= 0.06 * abs(Zc), (Ch, tau, Za, Zc)
+    for Ch in (10.0, 100.0):
+        Za, _ = dsp.acoustic_mode(P0, C, Ch, 10 * Ch)
+        Zc, _ = dsp.acoustic_mode(P0, C, C, 10 * Ch)
+        assert abs(Za.real - Zc.real) > 0.05 * Zc.real and abs(Za.imag) < 0.7 * abs(Zc.imag), (Ch, Za, Zc)
