@@ -139,3 +139,15 @@ def test_rsla_criterion_keeps_the_acoustic_mode():
         Za, _ = dsp.acoustic_mode(P0, C, Ch, 10 * Ch)
         Zc, _ = dsp.acoustic_mode(P0, C, C, 10 * Ch)
         assert abs(Za.real - Zc.real) > 0.05 * Zc.real and abs(Za.imag) < 0.7 * abs(Zc.imag), (Ch, Za, Zc)
+
+
+def test_oracle_acoustic_speed_in_the_radiation_dominated_case_is_the_reduced_one():
+    """P_0 = 10, C = 1e4, Chat = 10, tau = 10: with chat = c the acoustic mode would travel at
+    a_0* = 2.31 a_0; with the reduced speed the dispersion relation gives 0.775 a_0 (radiation pressure no
+    longer supports the wave), and the oracle's coupled cycles travel at that speed.  The mode's own
+    damping (1e-3) is below the scheme's at 32 cells, whose error is first order in the cell size (the
+    gas / radiation splitting of Sec. 3.1 is formally first order)."""
+    Z, Zm = oracle_wave(32, 10.0, 1e4, 10.0, 10.0)
+    assert abs(Zm.real - Z.real) <= 3e-4 * Z.real, (Z, Zm)
+    assert abs(Zm.real - dsp.radiation_acoustic_speed(10.0)) > 1.0
+    assert -0.02 < Zm.imag < 0.0
