@@ -179,6 +179,41 @@ def gas_case(name, n, bc="periodic", limiter="minmod", beta_tau=True, kappa=2.0,
     return case
 
 
+def radpulse_case(N=512, v=3e6, shift=None, beta_tau=True):
+    """The advected radiation pulse (Section 4.3.2) in cgs units: rho_0 = 25 g cm^-3, T_0 = 1.1e7 K,
+    w = 20 cm, mu = m_H, kappa_0 = 0.4 cm^2 g^-1, gamma = 5/3, periodic x / w in [-21.25, 21.25] on N cells;
+    T / T_0 = 1 + exp(-x^2 / (2 w^2)) about x = -shift (default: v t_end = 2 w for a moving run, 0 at rest),
+    rho from pressure equilibrium (Eq. radpulse:rho), E = a_R T^4, F the quasi-steady flux
+    -c dE/dx / (3 rho kappa_0) + (4/3) v E (reading), uniform velocity v; chat = 100 a_0; M1 closure, MC
+    limiter, FULL exchange, theta = 1.  Also returns t_end = 2 w / 3e6 cm s^-1."""
+    kB, mH, aR, c = 1.380649e-16, 1.6726e-24, 7.5657e-15, 2.99792458e10
+    rho0, T0, w, kap, gam = 25.0, 1.1e7, 20.0, 0.4, 5.0 / 3.0
+    t_end = 2.0 * w / 3e6
+    if shift is None:
+        shift = v * t_end
+    mu = mH / kB
+    a0 = math.sqrt(gam * T0 / mu)
+    P0 = aR * T0 ** 4 / (rho0 * a0 ** 2)
+    L = 42.5 * w
+    dx = L / N
+    x = -0.5 * L + (np.arange(N) + 0.5) * dx
+    xs = (x + shift + 0.5 * L) % L - 0.5 * L
+    T = T0 * (1.0 + np.exp(-xs ** 2 / (2 * w * w)))
+    rho = rho0 * (T0 / T + gam * P0 / 3.0 * (T0 / T - (T / T0) ** 3))
+    E = aR * T ** 4
+    dEdx = (np.roll(E, -1) - np.roll(E, 1)) / (2 * dx)
+    F = -c / (3 * rho * kap) * dEdx + (4.0 / 3.0) * v * E
+    desc = base_desc((N, 1, 1), (dx, 1.0, 1.0), bc="periodic", c=c, a_rad=aR, gamma=gam, mu_over_kB=mu,
+                     exchange="full", beta_tau=beta_tau, limiter="mc", kappa_P=kap, kappa_F=kap, kappa_rho_pow=1,
+                     theta_F=1.0, theta_E=1.0, E_floor=1e-30, cfl=0.4)
+    sh = (1, 1, N)
+    z = np.zeros(sh)
+    fields = {"E": E.reshape(sh), "Fx": F.reshape(sh), "Fy": z, "Fz": z.copy(), "T": T.reshape(sh),
+              "rho": rho.reshape(sh), "vx": np.full(sh, float(v)), "vy": z.copy(), "vz": z.copy(), "kP": None,
+              "kF": None, "j": None}
+    return {"name": f"radpulse{N}", "desc": desc, "fields": fields, "chat": 100.0 * a0, "t_end": t_end, "P0": P0}
+
+
 # ----------------------------------------------------------------------------- paper-shaped configs
 
 def dispersion_omega(chat, k, kF, mode):
