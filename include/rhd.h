@@ -195,8 +195,10 @@ rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double d
  * takes the nearest cell for the gas).  A negative internal energy is set to zero (counted in
  * rhd_stats.gas_energy_floors).  The step leaves a source correction pending: run the radiation
  * subcycles that span dt_gas, then rhd_gas_correct.  The energy exchange stays in the subcycles.
- * Does not synchronise.  Scratch: about (5 (n0+4)(n1+4)(n2+4) + 15 (n0+5)(n1+4)(n2+4) + 8 n) doubles,
- * allocated by the first call.  Single grids only.  Errors: RHD_ERR_ARG (dt_gas), RHD_ERR_STATE
+ * RHD_SPLIT grids compute the face fluxes (reconstruction, wave speeds, HLLC) and their differences in
+ * FP32 and the rest in FP64.  Does not synchronise.  Scratch, allocated by the first call, for n cells
+ * and m = (n0+4)(n1+4)(n2+4) (2D / 1D: no padding in inactive directions): 5 m + 8 n doubles, and 15 m
+ * face values (doubles; floats plus 5 m more floats on RHD_SPLIT grids).  Single grids only.  Errors: RHD_ERR_ARG (dt_gas), RHD_ERR_STATE
  * (ensemble, gas or moments not set), RHD_ERR_OOM, RHD_ERR_CUDA. */
 rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas);
 
