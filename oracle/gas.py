@@ -344,3 +344,38 @@ def gas_correct(desc, gas, pending, rad):
     W1, neg = primitive(desc, U)
     out = {"rho": W1[0], "vx": W1[1], "vy": W1[2], "vz": W1[3], "T": temperature(desc, W1[0], W1[4])}
     return out, int(np.count_nonzero(neg))
+
+
+# ----------------------------------------------------------------------------- step 2 (option)
+
+def gas_exchange(desc, gas, rad, dt, chat):
+    """Section 3.1 step 2 for the option that integrates the stiff exchange S_i (Eq.
+    algorithm:source:implicit) once per gas step: the implicit gas-radiation energy exchange over dt =
+    Delta t_gas in every cell (the quartic theta scheme of Eqs. source:energyupdate - source:polynomial,
+    the radiation oracle's cell routine), on E floored at E_floor, followed by |F| <= cE (the order of
+    the per-subcycle exchange).  k_P is the kP array or kappa_P rho^p.  Returns (gas with the new T,
+    radiation with the new E and F, number of theta = 1 fallbacks)."""
+    from . import oracle as orc
+
+    c = desc["c"]
+    E = np.array(rad["E"], dtype=np.float64, copy=True)
+    F = [np.array(rad[k], dtype=np.float64, copy=True) for k in ("Fx", "Fy", "Fz")]
+    T = np.array(gas["T"], dtype=np.float64, copy=True)
+    rho = gas["rho"]
+    kP = gas.get("kP")
+    if kP is None:
+        p = int(desc["kappa_rho_pow"])
+        kap = desc["kappa_P"]
+        kP = kap * np.ones_like(rho) if p == 0 else (kap * rho if p == 1 else (kap * rho) * rho)
+    fallbacks = 0
+    for i in np.ndindex(E.shape):
+        Ei = max(float(E[i]), desc["E_floor"])
+        Ei, Ti, fb = orc.exchange_full(desc, chat, dt, float(rho[i]), float(kP[i]), Ei, float(T[i]))
+        E[i], T[i] = Ei, Ti
+        fallbacks += fb
+        g2 = (F[0][i] / c) ** 2 + (F[1][i] / c) ** 2 + (F[2][i] / c) ** 2
+        if g2 > Ei * Ei:
+            s = Ei / np.sqrt(g2)
+            for a in range(3):
+                F[a][i] *= s
+    return dict(gas, T=T), {"E": E, "Fx": F[0], "Fy": F[1], "Fz": F[2]}, fallbacks
