@@ -88,8 +88,16 @@ typedef enum { RHD_EX_FULL = 0, RHD_EX_ABSORB = 1, RHD_EX_EQUILIBRIUM = 2, RHD_E
 typedef enum { RHD_LIM_MINMOD = 0, RHD_LIM_MC = 1, RHD_LIM_NONE = 2 } rhd_limiter;
 typedef enum { RHD_CLOSURE_M1 = 0, RHD_CLOSURE_P1 = 1 } rhd_closure;     /* P1: T = I/3 (Section 2.3) */
 typedef enum { RHD_SPEEDS_M1 = 0, RHD_SPEEDS_FIXED = 1 } rhd_speeds;     /* FIXED: -+chat/sqrt(3) */
-/* FP64: every step in FP64.  SPLIT: reconstruction, closure, wave speeds and HLL fluxes in FP32;
- * the conserved-variable accumulation, the source terms and the energy exchange in FP64. */
+/* FP64: every step in FP64.
+ * SPLIT: reconstruction, closure, wave speeds, HLL fluxes, the flux divergence and the explicit O(beta
+ * tau) and emissivity sources in FP32, giving an FP32 increment of each cell's state; the predictor's
+ * half-step state U^{m+1/2} is FP32.  The state (E, G and T) is FP64 and accumulates that increment in
+ * FP64.  The corrector's stiff sources (the theta updates of F and E and the FULL energy exchange) act
+ * on the FP64 state at FP64 accuracy: double-float arithmetic (about 48 bits) seeded by an FP32 Newton
+ * iteration, their results added to the FP64 state in FP64; their error is a few 2^-48 of the state
+ * and does not grow with the ratio of gas to radiation energy.  The gas inputs enter as FP32 copies
+ * (rho, v, kP, kF, j; the opacity law is evaluated at the FP32 density).  E_floor must be at least the
+ * smallest normal FP32 number (1.2e-38) on SPLIT grids. */
 typedef enum { RHD_FP64 = 0, RHD_SPLIT = 1 } rhd_precision;
 /* RHD_FLAG_NO_GRAPH: issue the n_sub launches one by one instead of replaying a captured CUDA graph. */
 #define RHD_FLAG_NO_GRAPH 1
@@ -114,7 +122,8 @@ typedef struct {
     double gamma;               /* adiabatic index, e = P/(gamma-1) */
     double mu_over_kB;          /* mean particle mass over k_B: P = rho T / mu_over_kB */
     double theta_F, theta_E;    /* theta of the F absorption and of the E exchange, in (0, 1] */
-    double E_floor;             /* E is kept >= E_floor > 0 */
+    double E_floor;             /* E is kept >= E_floor; a normal number: >= DBL_MIN, and >= FLT_MIN on SPLIT grids
+                                   (RHD_ERR_ARG otherwise) */
     double cfl;                 /* Courant number K0 of Eq. (algorithm:radtimestep), (0, 1] */
     int exchange;               /* rhd_exchange */
     int beta_tau;               /* 1: include the O(beta tau) source terms (Section 3.4 code switch) */

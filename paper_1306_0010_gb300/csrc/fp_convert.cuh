@@ -61,4 +61,15 @@ __device__ __forceinline__ float rcp(float x)
     return r;
 }
 
+// Explicitly rounded arithmetic: never contracted into FMAs or reassociated by the compiler, so every
+// inlined copy of an expression written with these rounds the same way.  Quantities that two tiles (or a
+// tile's own cells and its halo) compute separately use them, so that both copies get the same bits
+// (a face flux shared by two tiles, a uniform state that must stay uniform).
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 }  // namespace rhd

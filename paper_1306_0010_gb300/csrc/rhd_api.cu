@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -201,6 +202,11 @@ rhd_status validate_desc(rhd_ctx* ctx, const rhd_grid_desc* d)
     if (!(d->theta_F > 0 && d->theta_F <= 1) || !(d->theta_E > 0 && d->theta_E <= 1))
         return fail(ctx, RHD_ERR_ARG, "theta must lie in (0, 1]");
     if (!finite_pos(d->E_floor)) return fail(ctx, RHD_ERR_ARG, "E_floor must be positive");
+    // the kernels' reciprocals flush subnormal inputs: E >= E_floor must be a normal number of the
+    // arithmetic that divides by it (FP64; FP32 on split grids)
+    if (d->E_floor < DBL_MIN) return fail(ctx, RHD_ERR_ARG, "E_floor must be at least the smallest normal FP64 number");
+    if (d->precision == RHD_SPLIT && d->E_floor < (double)FLT_MIN)
+        return fail(ctx, RHD_ERR_ARG, "E_floor must be at least the smallest normal FP32 number (1.2e-38) on split grids");
     if (!(d->cfl > 0 && d->cfl <= 1)) return fail(ctx, RHD_ERR_ARG, "cfl must lie in (0, 1]");
     if (d->exchange < 0 || d->exchange > 4) return fail(ctx, RHD_ERR_ARG, "unknown exchange mode");
     if (d->exchange == RHD_EX_LINEAR && !finite_pos(d->linear_eps))

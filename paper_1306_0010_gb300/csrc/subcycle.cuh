@@ -26,6 +26,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
 #include "fp_convert.cuh"
 #include "rhd_internal.h"
 
@@ -125,8 +126,7 @@ __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R 
 {
     ClosureScalars<R> k;
     R invE = rcp(E);
-    R g2 = gx * gx + gy * gy + gz * gz;
-    R f2 = g2 * (invE * invE);
+    R f2 = xmul(xfma(gz, gz, xfma(gy, gy, xmul(gx, gx))), xmul(invE, invE));
     R invEb = invE;
     if (f2 > R(1)) {
         // |G| > E (a state outside the realizable set, e.g. an input U^m): the closure is that of
@@ -134,51 +134,53 @@ __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R 
         // b G G^T = E n n^T with b = 1/(E f^2).  Face states of the corrector have passed the
         // realizability test and never take this branch beyond its rounding allowance.
         const R q = rcp(rsq(f2));
-        invE = invE * q;
-        invEb = invE * q;
+        invE = xmul(invE, q);
+        invEb = xmul(invE, q);
         f2 = R(1);
     }
     k.invE = invE;
-    k.s = rsq(R(4) - R(3) * f2);
-    k.inv2ps = rcp(R(2) + k.s);
-    k.cs = chat * rcp(k.s);
+    k.s = rsq(xfma(R(-3), f2, R(4)));
+    k.inv2ps = rcp(xadd(R(2), k.s));
+    k.cs = xmul(chat, rcp(k.s));
     if (p1) {
-        k.a = E * R(1.0 / 3.0);
+        k.a = xmul(E, R(1.0 / 3.0));
         k.b = R(0);
     } else {
-        k.a = (k.s - R(1)) * E * R(1.0 / 3.0);
-        k.b = R(3) * k.inv2ps * invEb;
+        k.a = xmul(xmul(xadd(k.s, R(-1)), E), R(1.0 / 3.0));
+        k.b = xmul(xmul(R(3), k.inv2ps), invEb);
     }
     return k;
 }
 
 // lambda_1, lambda_3 in a direction with flux component gd (Eq. hyperbolic:evals13 rewritten with
-// mu f = gd/E and 2 mu^2 (2 - f^2 - s) = (2/3) mu^2 (s-1)(s-2)).
+// mu f = gd/E and 2 mu^2 (2 - f^2 - s) = (2/3) mu^2 (s-1)(s-2)).  The closure and the wave speeds use
+// explicitly rounded operations (xmul / xadd / xfma): a tile evaluates them for its own cells and for
+// its halo cells, which are other tiles' own cells, and both must get the same bits.
 template <typename R>
 __device__ __forceinline__ void wave_speeds(const ClosureScalars<R>& k, R gd, R chat, int fixed, R& l1, R& l3)
 {
     if (fixed) {
-        l3 = chat * R(0.57735026918962576451);
+        l3 = xmul(chat, R(0.57735026918962576451));
         l1 = -l3;
         return;
     }
-    R fd = gd * k.invE;
-    R rad = R(2.0 / 3.0) * (k.s - R(1)) * (k.s - R(3) * fd * fd * k.inv2ps);
+    const R fd = xmul(gd, k.invE);
+    R rad = xmul(xmul(R(2.0 / 3.0), xadd(k.s, R(-1))), xfma(-xmul(xmul(R(3), fd), fd), k.inv2ps, k.s));
     rad = rmax(rad, R(0));
-    R sr = rsq(rad);
-    l1 = (fd - sr) * k.cs;
-    l3 = (fd + sr) * k.cs;
+    const R sr = rsq(rad);
+    l1 = xmul(xadd(fd, -sr), k.cs);
+    l3 = xmul(xadd(fd, sr), k.cs);
 }
 
 // Flux chat * (G_d, P_dx, P_dy, P_dz) of a state in direction D.
 template <int D, typename R>
 __device__ __forceinline__ void dir_flux(const ClosureScalars<R>& k, const R U[4], R chat, R F[4])
 {
-    R gd = U[1 + D];
-    F[0] = chat * gd;
-    F[1] = chat * ((D == 0 ? k.a : R(0)) + k.b * gd * U[1]);
-    F[2] = chat * ((D == 1 ? k.a : R(0)) + k.b * gd * U[2]);
-    F[3] = chat * ((D == 2 ? k.a : R(0)) + k.b * gd * U[3]);
+    const R gd = U[1 + D], bg = xmul(k.b, gd);
+    F[0] = xmul(chat, gd);
+    F[1] = xmul(chat, xfma(bg, U[1], D == 0 ? k.a : R(0)));
+    F[2] = xmul(chat, xfma(bg, U[2], D == 1 ? k.a : R(0)));
+    F[3] = xmul(chat, xfma(bg, U[3], D == 2 ? k.a : R(0)));
 }
 
 // Eq. (hyperbolic:hllflux2); S_R^+ = S_L^- = 0 gives the average (same reading as the oracle).
@@ -188,15 +190,16 @@ __device__ __forceinline__ void hll(const R UL[4], const R UR[4], const R FL[4],
 {
     R SR = rmax(l3L, l3R), SL = rmin(l1L, l1R);
     R SRp = rmax(SR, R(0)), SLm = rmin(SL, R(0));
-    R den = SRp - SLm;
+    R den = xadd(SRp, -SLm);
     if (den > R(0)) {
         R inv = rcp(den);
-        R pr = SRp * SLm;
+        R pr = xmul(SRp, SLm);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[q] = (SRp * FL[q] - SLm * FR[q] + pr * (UR[q] - UL[q])) * inv;
+        for (int q = 0; q < 4; ++q)
+            out[q] = xmul(xfma(pr, xadd(UR[q], -UL[q]), xfma(SRp, FL[q], xmul(-SLm, FR[q]))), inv);
     } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[q] = R(0.5) * (FL[q] + FR[q]);
+        for (int q = 0; q < 4; ++q) out[q] = xmul(R(0.5), xadd(FL[q], FR[q]));
     }
 }
 
@@ -215,8 +218,8 @@ __device__ __forceinline__ R limited(R dl, R dr, int lim)
 template <typename R>
 __device__ __forceinline__ bool face_unrealizable(R E, R gx, R gy, R gz)
 {
-    R g2 = gx * gx + gy * gy + gz * gz;
-    return !(E > R(0)) || (g2 > (R(1) + Tol<R>::face) * (E * E));
+    const R g2 = xfma(gz, gz, xfma(gy, gy, xmul(gx, gx)));
+    return !(E > R(0)) || (g2 > xmul(R(1) + Tol<R>::face, xmul(E, E)));
 }
 
 // Face states of one cell in direction D for the corrector: the limited slope of U^{m+1/2} from
@@ -717,6 +720,201 @@ struct Counters {
     unsigned fix, face, theta, newton_fb, nonfinite, iter_max, timeout;
 };
 
+// ------------------------------------------------------------------------------------------------
+// Stiff sources of a split-path cell (a8, a9) at FP64 accuracy.  Reconstruction, closure, fluxes and
+// the explicit O(beta tau) and emissivity sources give an FP32 increment d of the cell; the stiff
+// sources then act on the FP64 state U0 + d (U0 the state at t^m) exactly as in the FP64 path, with the
+// FP32 copies of the gas inputs as their inputs (the density exact; an absorption coefficient is the
+// FP32 copy of its array, or the opacity law evaluated at that density).  The FP64 pipe of this part
+// runs at a small fraction of the FP32 rate and with a long latency, so the arithmetic is double-float
+// on the FP32 pipe (dfloat.cuh: about 48 bits, a few 2^-48 relative per operation), and FP64
+// operations are spent only on splitting the FP64 state into double-floats and adding the results back
+// to it (about ten per cell in FULL mode):
+//   - theta updates of G (Eq. source:stiff:radmomentum:soln) and of E in ABSORB (Eq.
+//     source:stiff:radenergy:soln): x = chat k dt and the factor (1 - (1 - theta) x)/(1 + theta x) in
+//     double-float, then (U0 + d) f as one FP64 FMA per component; FROZEN_T's a_R T^4 term likewise;
+//   - the FULL exchange (Eqs. source:energyupdate - source:polynomial): the paper's quartic written
+//     for the temperature change t = T^{n+1} - T^n (t = q delta with delta = e^{n+1} - e^n and
+//     q = (gamma - 1) mu/(k_B rho)) and multiplied by x = chat kP dt > 0,
+//       R(t) = sigma (1 + theta x) t + x (a_R [theta (T + t)^4 + (1 - theta) T^4] - E) = 0,
+//     sigma = (chat/c)/q, after which E^{n+1} = E - sigma t (Eq. source:eradupdate: E - (chat/c) delta).
+//     The FP32 Newton iteration on delta (exchange_delta_fp32) gives the seed t0 = q delta, within a
+//     few 2^-24 T of the root; R(t0) is evaluated in double-float (its two terms cancel near the root)
+//     and one step with Halley's second-order term, t = t0 - c - (R''/2R') c^2 with c = R/R', follows,
+//     R' and R'' in FP32: the step's error is of order c^3/T^2 plus the FP32 relative error of R' times
+//     c, a few 2^-48 T in all, and the E error (sigma times that) a few 2^-48 max(E, a_R T^4),
+//     independent of the ratio of gas to radiation energy.  E^{n+1} and T^{n+1} are the FP64 state plus
+//     double-float increments.  A cell whose seed or step is not finite, or whose step exceeds 2^-20 T
+//     (a seed the FP32 iteration got wrong, e.g. in units that leave its range), is solved instead by
+//     FP64 Newton steps from the seed (R is convex and increasing in t for T + t >= 0, so the iterates
+//     decrease monotonically after the first; the first iterate that does not decrease is the answer).
+// The theta fallback (c0 > 0, Section 3.4) is decided by the FP32 iteration.  E is floored at E_floor
+// before the exchange, as in the FP64 path.
+// ------------------------------------------------------------------------------------------------
+struct SplitStiffConsts {
+    dfl cdt;         // chat dt (absorption-coefficient arrays)
+    dfl KP, KF;      // chat dt kappa_P, chat dt kappa_F (the opacity law's factor)
+    dfl aR, thF, omF, thE, omE;  // a_R, theta, 1 - theta
+    dfl sig1;        // (chat/c) / ((gamma - 1) mu/k_B): sigma = sig1 rho
+    dfl Efl;         // E_floor
+    double chat, dt, sig1d;
+};
+
+__device__ __forceinline__ SplitStiffConsts split_stiff_consts(const GridParams& g, double chat, double dt)
+{
+    SplitStiffConsts k;
+    const double cdt = chat * dt;
+    k.cdt = dconst(cdt);
+    k.KP = dconst(cdt * g.kappa_P);
+    k.KF = dconst(cdt * g.kappa_F);
+    k.sig1d = chat * g.inv_c / g.gm1_mu;
+    k.sig1 = dconst(k.sig1d);
+    k.Efl = dconst(g.E_floor);
+    k.aR = dconst(g.a_rad);
+    k.thF = dconst(g.theta_F);
+    k.omF = dconst(1.0 - g.theta_F);
+    k.thE = dconst(g.theta_E);
+    k.omE = dconst(1.0 - g.theta_E);
+    k.chat = chat;
+    k.dt = dt;
+    return k;
+}
+
+// chat dt k of a split-path cell: k the FP32 copy of its array, or the opacity law K rho^p with
+// K = chat dt kappa
+__device__ __forceinline__ dfl split_x(const SplitStiffConsts& k, const float* karr, float kv, dfl K, int p, float rho)
+{
+    if (karr) return dmul(k.cdt, kv);
+    return p == 0 ? K : (p == 1 ? dmul(K, rho) : dmul(dmul(K, rho), rho));
+}
+__device__ __forceinline__ bool is_one(dfl t) { return t.hi == 1.0f && t.lo == 0.0f; }
+// (1 - (1 - theta) x)/(1 + theta x)
+__device__ __forceinline__ dfl theta_factor(dfl x, dfl th, dfl om)
+{
+    if (is_one(th)) return drcp(dadd(x, 1.0f));
+    return dmul(dadd(dneg(dmul(om, x)), 1.0f), drcp(dadd(dmul(th, x), 1.0f)));
+}
+// (U0 + d) f in FP64 for a double-float factor f: U0 (f_hi + f_lo) + d f_hi (d is an FP32 quantity, so
+// its product is rounded in FP32); f_hi + f_lo is exact in FP64
+__device__ __forceinline__ double scale_state(double U0, float d, double f64, float fhi)
+{
+    return fma(U0, f64, f2d_exact(__fmul_rn(d, fhi)));
+}
+
+// U0: the FP64 state at t^m; d: the FP32 increment (transport and explicit sources over dt); T: the gas
+// temperature (read for FROZEN_T, read and updated for FULL and LINEAR).  Writes Un = U^{m+1} before
+// realizability.
+__device__ __forceinline__ void split_stiff(const GridParams& g, const GridArrays& a, const SplitStiffConsts& k,
+                                            float chat, float dt, const GasCell<float>& gc, const double U0[4],
+                                            const float d[4], double& T, double Un[4], Counters& cnt)
+{
+    const float rho = gc.rho32;
+    {
+        const dfl fF = theta_factor(split_x(k, a.kF32, gc.kF, k.KF, g.kpow, rho), k.thF, k.omF);
+        const double f64 = df2d(fF);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) Un[q] = scale_state(U0[q], d[q], f64, fF.hi);
+    }
+    const int ex = g.exchange;
+    if (ex == EX_EQUILIBRIUM) {
+        Un[0] = U0[0] + f2d_exact(d[0]);
+        return;
+    }
+    if (ex == EX_LINEAR) {
+        double E = U0[0] + f2d_exact(d[0]);
+        const double kP = a.kP32 ? f2d_exact(gc.kP) : kappa_law(g.kappa_P, g.kpow, f2d_exact(rho));
+        exchange_linear_fp64(g, k.chat, k.dt, kP, E, T);
+        Un[0] = E;
+        return;
+    }
+    const dfl xP = split_x(k, a.kP32, gc.kP, k.KP, g.kpow, rho);
+    if (ex == EX_ABSORB) {
+        const dfl fE = theta_factor(xP, k.thE, k.omE);
+        Un[0] = scale_state(U0[0], d[0], df2d(fE), fE.hi);
+        return;
+    }
+    if (ex == EX_FROZEN_T) {
+        // (E (1 - (1 - theta) x) + x a_R T^4)/(1 + theta x) = (U0 + d) fE + x a_R T^4 / (1 + theta x)
+        const dfl rD = drcp(dadd(dmul(k.thE, xP), 1.0f));
+        const dfl fE = dmul(dadd(dneg(dmul(k.omE, xP)), 1.0f), rD);
+        const dfl W = dmul(dmul(xP, dmul(k.aR, dsqr(dsqr(d2df(T))))), rD);
+        const dfl Z = dadd(W, __fmaf_rn(d2f_rn(U0[0]), fE.lo, __fmul_rn(d[0], fE.hi)));
+        Un[0] = fma(U0[0], f2d_exact(fE.hi), f2d_exact(Z.hi)) + f2d_exact(Z.lo);
+        return;
+    }
+    // FULL.  E_in = U0 + d, floored (transport is not positivity preserving)
+    dfl Ein = dadd(d2df(U0[0]), d[0]);
+    const bool floored = Ein.hi < k.Efl.hi || (Ein.hi == k.Efl.hi && Ein.lo < k.Efl.lo);
+    if (floored) Ein = k.Efl;
+    const dfl Td = d2df(T);
+    ExchangeOut o;
+    float qv;
+    const float del = exchange_delta_fp32(g, chat, dt, rho, gc.kP, Ein.hi, Td.hi, o, qv);
+    const float t0 = qv * del;
+    const bool thone = o.theta_fb || is_one(k.thE);
+    const dfl th = o.theta_fb ? dfl{1.0f, 0.0f} : k.thE;
+    const dfl sig = dmul(k.sig1, rho);
+    const dfl sD = dmul(sig, dadd(thone ? xP : dmul(th, xP), 1.0f));  // sigma (1 + theta x)
+    // R(t0) in double-float
+    const dfl T1 = dadd(Td, t0);
+    const dfl T1s = dsqr(T1);
+    dfl M = dsqr(T1s);
+    if (!thone) M = dadd_same(dmul(th, M), dmul(k.omE, dsqr(dsqr(Td))));
+    const dfl R = dadd(dmul(sD, t0), dmul(xP, dadd(dmul(k.aR, M), dneg(Ein))));
+    // the step with Halley's term: R' = sigma (1 + theta x) + 4 theta x a_R T1^3, R''/2R' = 6 theta x a_R T1^2 / R'
+    const float T1h = T1.hi;
+    const float q4 = 4.0f * th.hi * xP.hi * k.aR.hi * T1h * T1h;
+    const float Rp = __fmaf_rn(q4, T1h, sD.hi);
+    const float iRp = rcp(Rp);
+    const float ch = R.hi * iRp;
+    const float cl = __fmaf_rn(1.5f * q4 * iRp * ch, ch, (__fmaf_rn(-ch, Rp, R.hi) + R.lo) * iRp);
+    dfl t = two_sum(t0, -ch);
+    t = fast_two_sum(t.hi, t.lo - cl);
+    o.iters += 1;
+    const bool ok = isfinite(t.hi) && isfinite(t.lo) && isfinite(sD.hi) && fabsf(ch) <= 9.5367431640625e-7f * fabsf(T1h);
+    if (ok) {
+        const dfl sigt = dmul(sig, t);
+        const dfl inc = floored ? dneg(sigt) : dadd(dneg(sigt), d[0]);
+        Un[0] = ((floored ? g.E_floor : U0[0]) + f2d_exact(inc.hi)) + f2d_exact(inc.lo);
+        T = (T + f2d_exact(t.hi)) + f2d_exact(t.lo);
+    } else {
+        // FP64 Newton steps from the seed (or from t = 0 if the seed is not finite)
+        const double E = floored ? g.E_floor : U0[0] + f2d_exact(d[0]);
+        const double rhod = f2d_exact(rho);
+        const double kPd = a.kP32 ? f2d_exact(gc.kP) : kappa_law(g.kappa_P, g.kpow, rhod);
+        const double xPd = k.chat * k.dt * kPd, thd = o.theta_fb ? 1.0 : g.theta_E, sigd = k.sig1d * rhod;
+        const double sDd = sigd * fma(thd, xPd, 1.0);
+        double ts = isfinite(t0) ? f2d_exact(t0) : 0.0;
+        bool settled = false;
+#pragma unroll 1
+        for (int s = 0; s < 64; ++s) {
+            const double T1d = T + ts, T1sd = T1d * T1d;
+            double Md = T1sd * T1sd;
+            if (thd != 1.0) {
+                const double T2 = T * T, T4 = T2 * T2;
+                Md = fma(thd, Md - T4, T4);
+            }
+            const double Rv = fma(sDd, ts, xPd * fma(g.a_rad, Md, -E));
+            const double tn = ts - Rv / fma(4.0 * thd * xPd * g.a_rad * T1sd, T1d, sDd);
+            if (s > 0 && !(tn < ts)) {
+                settled = true;
+                o.iters += s;
+                break;
+            }
+            ts = tn;
+        }
+        if (!settled) {
+            o.newton_fb = 1;
+            o.iters += 64;
+        }
+        Un[0] = fma(-sigd, ts, E);
+        T = T + ts;
+    }
+    cnt.theta += o.theta_fb;
+    cnt.newton_fb += o.newton_fb;
+    cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
+}
+
 template <typename R>
 __device__ __forceinline__ void store20(R* base, int stride, int idx, const R v[20])
 {
@@ -763,6 +961,7 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
     const R chat = (R)chat_d;
     const R dt = (R)dt_d;
     const R hdt = R(0.5) * dt;
+    const SplitStiffConsts sk = split_stiff_consts(g, chat_d, dt_d);
     const R idx = (R)g.inv_dx[0], idy = (R)g.inv_dx[1], idz = (R)g.inv_dx[2];
     const int p1 = g.closure == 1, fixed = g.speeds == 1, lim = g.limiter;
     const R E_floor = sizeof(R) == 8 ? (R)g.E_floor : (R)g.f_E_floor;
@@ -1186,59 +1385,17 @@ __device__ __forceinline__ void subcycle_tile(const GridParams& g, const GridArr
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) Un[qq] = U[qq];
                 } else {
-                    // FP32 increment relative to the FP64 state
-                    float u0f[4];
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) u0f[qq] = d2f_trunc(U0[qq]);
+                    // FP32 increment relative to the FP64 state; the stiff sources in FP64
                     float d[4];
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) d[qq] = -dt * div[qq] + dt * S[qq];
-                    const float thF = g.f_theta_F, thE = g.f_theta_E;
-                    float xF = (float)chat * (float)gc.kF * (float)dt;
-                    float wF = xF * rcp(1.0f + thF * xF);
-#pragma unroll
-                    for (int qq = 1; qq < 4; ++qq) d[qq] -= (u0f[qq] + d[qq]) * wF;
-                    if (g.exchange == EX_ABSORB) {
-                        float xP = (float)chat * (float)gc.kP * (float)dt;
-                        d[0] -= (u0f[0] + d[0]) * (xP * rcp(1.0f + thE * xP));
-                    } else if (g.exchange == EX_FROZEN_T) {
-                        float xP = (float)chat * (float)gc.kP * (float)dt;
-                        float Tf = d2f_trunc(gc.T);
-                        float aT4 = g.f_a_rad * (Tf * Tf) * (Tf * Tf);
-                        d[0] += xP * (aT4 - (u0f[0] + d[0])) * rcp(1.0f + thE * xP);
-                    }
-                    double Etr = U0[0] + f2d_exact(d[0]);
-                    if (full) {
-                        // exchange on E >= E_floor; its change is applied to the FP64 energy
-                        float Ef = u0f[0] + d[0];
-                        if (!(Ef > 2.0f * g.f_E_floor)) {
-                            if (Etr < g.E_floor) Etr = g.E_floor;
-                            Ef = d2f_trunc(Etr);
-                        }
-                        ExchangeOut o;
-                        float qv;
-                        float del = exchange_delta_fp32(g, (float)chat, (float)dt, gc.rho32, (float)gc.kP, Ef,
-                                                        d2f_trunc(gc.T), o, qv);
-                        Etr = Etr - f2d_exact(((float)chat * g.f_inv_c) * del);
-                        d[0] = Ef - ((float)chat * g.f_inv_c) * del - u0f[0];
-                        Tn = gc.T + f2d_exact(qv * del);
-                        cnt.theta += o.theta_fb;
-                        cnt.newton_fb += o.newton_fb;
-                        cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
-                    } else if (linear) {
-                        // the linear exchange in FP64 on the FP64 energy and temperature
-                        exchange_linear_fp64(g, chat_d, dt_d, (double)gc.kP, Etr, Tn);
-                        d[0] = d2f_trunc(Etr) - u0f[0];
-                    }
-                    Un[0] = Etr;
-#pragma unroll
-                    for (int qq = 1; qq < 4; ++qq) Un[qq] = U0[qq] + f2d_exact(d[qq]);
+                    split_stiff(g, a, sk, (float)chat, (float)dt, gc, U0, d, Tn, Un, cnt);
                     // realizability: cheap FP32 screen, exact FP64 test only near the limit
-                    float ef = u0f[0] + d[0];
+                    const float ef = d2f_trunc(Un[0]);
                     float g2f = 0.f;
 #pragma unroll
                     for (int qq = 1; qq < 4; ++qq) {
-                        float gq = u0f[qq] + d[qq];
+                        const float gq = d2f_trunc(Un[qq]);
                         g2f += gq * gq;
                     }
                     if (!(ef > g.f_E_floor * 1.001f) || g2f > 0.9999f * ef * ef) cnt.fix += realize(Un, g.E_floor);

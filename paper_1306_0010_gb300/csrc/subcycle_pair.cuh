@@ -110,9 +110,9 @@ template <int D>
 __device__ __forceinline__ float4 flux_ab(float4 U, float a, float b)
 {
     const float gd = D == 0 ? U.y : (D == 1 ? U.z : U.w);
-    const float bg = b * gd;
-    return make_float4(gd, D == 0 ? fmaf(bg, U.y, a) : bg * U.y, D == 1 ? fmaf(bg, U.z, a) : bg * U.z,
-                       D == 2 ? fmaf(bg, U.w, a) : bg * U.w);
+    const float bg = xmul(b, gd);
+    return make_float4(gd, D == 0 ? xfma(bg, U.y, a) : xmul(bg, U.y), D == 1 ? xfma(bg, U.z, a) : xmul(bg, U.z),
+                       D == 2 ? xfma(bg, U.w, a) : xmul(bg, U.w));
 }
 
 // minmod(a, b): the one of a, b nearer zero if they have the same sign, else 0, as three min / max:
@@ -136,8 +136,8 @@ __device__ __forceinline__ float limited_f(float dl, float dr, int lim)
 // E <= 0 or |G|^2 > (1 + tol) E^2, without short-circuit branches (same test as face_unrealizable)
 __device__ __forceinline__ int unrealizable_f(float4 U)
 {
-    const float g2 = U.y * U.y + U.z * U.z + U.w * U.w;
-    return (int)(!(U.x > 0.0f)) | (int)(g2 > (1.0f + Tol<float>::face) * (U.x * U.x));
+    const float g2 = xfma(U.w, U.w, xfma(U.z, U.z, xmul(U.y, U.y)));
+    return (int)(!(U.x > 0.0f)) | (int)(g2 > xmul(1.0f + Tol<float>::face, xmul(U.x, U.x)));
 }
 
 // Face-state record of one cell in direction D (see face_states): minus state, its flux, plus state,
@@ -221,11 +221,11 @@ __device__ __forceinline__ float4 hll4(float4 UL, float4 UR, float4 FL, float4 F
     const float SRp = fmaxf(fmaxf(l3L, l3R), 0.f), SLm = fminf(fminf(l1L, l1R), 0.f);
     const float den = SRp - SLm;
     if (den > 0.f) {
-        const float a = SRp * chat, b = -SLm * chat, c = SRp * SLm, iv = rcp(den);
-        return make_float4(fmaf(c, UR.x - UL.x, fmaf(b, FR.x, a * FL.x)) * iv,
-                           fmaf(c, UR.y - UL.y, fmaf(b, FR.y, a * FL.y)) * iv,
-                           fmaf(c, UR.z - UL.z, fmaf(b, FR.z, a * FL.z)) * iv,
-                           fmaf(c, UR.w - UL.w, fmaf(b, FR.w, a * FL.w)) * iv);
+        const float a = xmul(SRp, chat), b = xmul(-SLm, chat), c = xmul(SRp, SLm), iv = rcp(den);
+        return make_float4(xmul(xfma(c, xadd(UR.x, -UL.x), xfma(b, FR.x, xmul(a, FL.x))), iv),
+                           xmul(xfma(c, xadd(UR.y, -UL.y), xfma(b, FR.y, xmul(a, FL.y))), iv),
+                           xmul(xfma(c, xadd(UR.z, -UL.z), xfma(b, FR.z, xmul(a, FL.z))), iv),
+                           xmul(xfma(c, xadd(UR.w, -UL.w), xfma(b, FR.w, xmul(a, FL.w))), iv));
     }
     const float h = 0.5f * chat;
     return make_float4((FL.x + FR.x) * h, (FL.y + FR.y) * h, (FL.z + FR.z) * h, (FL.w + FR.w) * h);

@@ -252,10 +252,11 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
         float l1x, l3x, l1y, l3y;
         wave_speeds(k, U.y, chat, fixed, l1x, l3x);
         wave_speeds(k, U.z, chat, fixed, l1y, l3y);
-        const float bx = k.b * U.y;
-        const float Pxy = bx * U.z, Pxz = bx * U.w, Pyz = k.b * U.z * U.w;
-        CX[i] = make_float4(k.a + bx * U.y, Pxy, Pxz, l1x);
-        CY[i] = make_float4(Pxy, k.a + k.b * U.z * U.z, Pyz, l1y);
+        // explicitly rounded: own and halo cells (other tiles' own cells) must get the same bits
+        const float bx = xmul(k.b, U.y), bz = xmul(k.b, U.z);
+        const float Pxy = xmul(bx, U.z), Pxz = xmul(bx, U.w), Pyz = xmul(bz, U.w);
+        CX[i] = make_float4(xfma(bx, U.y, k.a), Pxy, Pxz, l1x);
+        CY[i] = make_float4(Pxy, xfma(bz, U.z, k.a), Pyz, l1y);
         L3[i] = make_float2(l3x, l3y);
     };
     const float4* Um = Um0;  // the current plane's buffer
@@ -310,7 +311,8 @@ __device__ __forceinline__ void predictor_tile(const GridParams& g, const GridAr
             float l1z, l3z;
             wave_speeds(k, U.w, chat, fixed, l1z, l3z);
             nU = U;
-            nP = make_float4(k.b * U.y * U.w, k.b * U.z * U.w, k.a + k.b * U.w * U.w, l1z);
+            const float bw = xmul(k.b, U.w);
+            nP = make_float4(xmul(bw, U.y), xmul(bw, U.z), xfma(bw, U.w, k.a), l1z);
             nl3 = l3z;
         }
         if (has_h) {
@@ -423,7 +425,8 @@ struct GeoCorr {
 // and mbar are then required, and sm must be 128-byte aligned); otherwise by per-thread cp.async.
 template <int TX, int TY, bool TMA = false, int LIMK = -1>
 __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridArrays& a, const float4* uh,
-                                               float chat, float dt, int x0, int y0, int z0, int z1, float4* sm,
+                                               float chat, float dt, double chat_d, double dt_d, int x0, int y0,
+                                               int z0, int z1, float4* sm,
                                                Counters& cnt, const CUtensorMap* map = nullptr,
                                                uint64_t* mbar = nullptr)
 {
@@ -437,6 +440,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     double* oD = reinterpret_cast<double*>(sm + G::END4) + t;                       // oD[q NT]: E, Gx, Gy, Gz, T
     float4* oG = reinterpret_cast<float4*>(reinterpret_cast<double*>(sm + G::END4) + G::OD * G::NT) + t;  // gas
     const float idx = g.f_inv_dx[0], idy = g.f_inv_dx[1], idz = g.f_inv_dx[2];
+    const SplitStiffConsts sk = split_stiff_consts(g, chat_d, dt_d);
     // LIMK >= 0: the limiter is a compile-time constant (only its code is generated); -1: g.limiter
     const int p1 = g.closure == 1, fixed = g.speeds == 1, lim = LIMK >= 0 ? LIMK : g.limiter;
     const bool needT = g.exchange == EX_FULL || g.exchange == EX_FROZEN_T;
@@ -687,53 +691,18 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             const bool full = g.exchange == EX_FULL;
             float S[4];
             explicit_sources(g, gc, Uhk, chat, S);
-            float u0f[4], d[4];
+            float d[4];
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                u0f[qq] = d2f_trunc(U0[qq]);
-                d[qq] = -dt * div[qq] + dt * S[qq];
+            for (int qq = 0; qq < 4; ++qq) d[qq] = -dt * div[qq] + dt * S[qq];
+            double Un[4];
+            split_stiff(g, a, sk, chat, dt, gc, U0, d, Tn, Un, cnt);
+            // realizability: the FP32 mirror screens, the FP64 test runs only near the limit
+            float4 m = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
+            if (!(m.x > g.f_E_floor * 1.001f) || m.y * m.y + m.z * m.z + m.w * m.w > 0.9999f * m.x * m.x) {
+                const int fx = realize(Un, g.E_floor);
+                cnt.fix += fx;
+                m = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
             }
-            const float thF = g.f_theta_F, thE = g.f_theta_E;
-            const float xF = chat * gc.kF * dt;
-            const float wF = xF * rcp(1.0f + thF * xF);
-#pragma unroll
-            for (int qq = 1; qq < 4; ++qq) d[qq] -= (u0f[qq] + d[qq]) * wF;
-            if (g.exchange == EX_ABSORB) {
-                const float xP = chat * gc.kP * dt;
-                d[0] -= (u0f[0] + d[0]) * (xP * rcp(1.0f + thE * xP));
-            } else if (g.exchange == EX_FROZEN_T) {
-                const float xP = chat * gc.kP * dt;
-                const float Tf = d2f_trunc(Tn);
-                const float aT4 = g.f_a_rad * (Tf * Tf) * (Tf * Tf);
-                d[0] += xP * (aT4 - (u0f[0] + d[0])) * rcp(1.0f + thE * xP);
-            }
-            double Etr = U0[0] + f2d_exact(d[0]);
-            if (full) {
-                float Ef = u0f[0] + d[0];
-                if (!(Ef > 2.0f * g.f_E_floor)) {
-                    if (Etr < g.E_floor) Etr = g.E_floor;
-                    Ef = d2f_trunc(Etr);
-                }
-                ExchangeOut o;
-                float qv;
-                const float del = exchange_delta_fp32(g, chat, dt, gc.rho32, gc.kP, Ef, d2f_trunc(Tn), o, qv);
-                const float dE = (chat * g.f_inv_c) * del;
-                Etr = Etr - f2d_exact(dE);
-                d[0] = Ef - dE - u0f[0];
-                Tn = Tn + f2d_exact(qv * del);
-                cnt.theta += o.theta_fb;
-                cnt.newton_fb += o.newton_fb;
-                cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
-            }
-            double Un[4] = {Etr, U0[1] + f2d_exact(d[1]), U0[2] + f2d_exact(d[2]), U0[3] + f2d_exact(d[3])};
-            const float ef = u0f[0] + d[0];
-            float g2f = 0.f;
-#pragma unroll
-            for (int qq = 1; qq < 4; ++qq) {
-                const float gq = u0f[qq] + d[qq];
-                g2f += gq * gq;
-            }
-            if (!(ef > g.f_E_floor * 1.001f) || g2f > 0.9999f * ef * ef) cnt.fix += realize(Un, g.E_floor);
             const bool bad = !(finite_d(Un[0]) && finite_d(Un[1]) && finite_d(Un[2]) && finite_d(Un[3]) &&
                                (!full || finite_d(Tn)));
             cnt.nonfinite += bad;
@@ -742,7 +711,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
             a.Go[1][lo] = Un[2];
             a.Go[2][lo] = Un[3];
             // the FP32 mirror of U^{m+1} for the next subcycle's predictor
-            a.um32[lo] = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
+            a.um32[lo] = m;
             if (full) a.T[lo] = Tn;
         }
         cfl = cfh;
@@ -789,7 +758,8 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(
     // TMA destinations need 128-byte alignment: the launch adds 128 bytes of slack
     float4* sm = reinterpret_cast<float4*>(smem_raw);
     if constexpr (TMA) sm = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    corrector_tile<TX, TY, TMA, LIMK>(P.g, P.a, P.uhalf, P.f_chat, P.f_dt, x0, y0, z0, z1, sm, cnt, &P.uh_map, mbar);
+    corrector_tile<TX, TY, TMA, LIMK>(P.g, P.a, P.uhalf, P.f_chat, P.f_dt, P.chat, P.dt, x0, y0, z0, z1, sm, cnt,
+                                      &P.uh_map, mbar);
     add_counter(&P.stats->n_fix, cnt.fix);
     add_counter(&P.stats->n_face, cnt.face);
     add_counter(&P.stats->n_theta, cnt.theta);
@@ -867,7 +837,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_ens_ker
         const int txy = (int)(local % nxy), tz = (int)(local / nxy);
         const int x0 = (txy % eg.tiles_x) * TX, y0 = (txy / eg.tiles_x) * TY;
         const int z0 = tz * P.z_chunk, z1 = min(z0 + P.z_chunk, eg.g.n[2]);
-        corrector_tile<TX, TY, false, LIMK>(eg.g, eg.a, eg.uhalf, P.f_chat, eg.f_dt, x0, y0, z0, z1,
+        corrector_tile<TX, TY, false, LIMK>(eg.g, eg.a, eg.uhalf, P.f_chat, eg.f_dt, P.chat, eg.dt, x0, y0, z0, z1,
                                reinterpret_cast<float4*>(smem_raw), cnt);
         __syncthreads();
     }

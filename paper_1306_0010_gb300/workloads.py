@@ -161,6 +161,48 @@ def parity_case(name, n, bc="periodic", exchange="equilibrium", limiter="minmod"
     return {"name": name, "desc": desc, "fields": fields, "chat": chat, "dt": dt, "n_sub": n_sub}
 
 
+def stiff_case(name, n, uniform=False, exchange="full", K=2.0e4, x_abs=20.0, rho0=1000.0, T0=1.5, theta=1.0,
+               c=10.0, chat=1.0, n_sub=10, seed=0, bc="periodic", fmax=0.5, precision="split"):
+    """Stiff exchange with the gas energy far above the radiation's: hot dense gas against a weak
+    radiation field.  K = e / ((c/chat) E) sets E from the gas (e = rho T / ((gamma - 1) mu/k_B)), and
+    the opacity law k = kappa rho (kappa_P = kappa_F) gives chat k dt = x_abs at rho0.  The density is
+    rounded to FP32 (so the split path's FP32 copy of it is exact) and v = 0, j = 0 (no explicit
+    source).  uniform: every cell holds the same state, so the transport of every subcycle cancels
+    exactly and only the stiff sources act; otherwise rho = rho0 exp(N(0, 0.3^2)), T = T0 exp(N(0,
+    0.1^2)), E = E_K U(0.5, 1.5) and F = c E f n with f ~ U(0, fmax), n uniform on the sphere (active
+    directions only)."""
+    g = rng(5000 + seed)
+    n = tuple(n)
+    dx = tuple(1.0 / max(v, 1) for v in n)
+    desc = base_desc(n, dx, bc=bc, c=c, exchange=exchange, kappa_rho_pow=1, theta_F=theta, theta_E=theta,
+                     E_floor=1e-12, precision=precision)
+    dt = cfl_dt(desc, chat)
+    kappa = float(np.float32(x_abs / (chat * rho0 * dt)))
+    desc["kappa_P"] = desc["kappa_F"] = kappa
+    shp = _shape(desc)
+    gm1_mu = (desc["gamma"] - 1.0) * desc["mu_over_kB"]
+    if uniform:
+        rho = np.full(shp, float(np.float32(rho0)))
+        T = np.full(shp, T0)
+        E = np.full(shp, rho0 * T0 / gm1_mu / (K * c / chat))
+        f = np.full(shp, 0.5 * fmax)
+        dirs = [np.full(shp, v) for v in (0.48, -0.6, 0.64)]
+    else:
+        rho = (rho0 * np.exp(g.normal(0.0, 0.3, size=shp))).astype(np.float32).astype(np.float64)
+        T = T0 * np.exp(g.normal(0.0, 0.1, size=shp))
+        E = rho0 * T0 / gm1_mu / (K * c / chat) * g.uniform(0.5, 1.5, size=shp)
+        f = g.uniform(0.0, fmax, size=shp)
+        dirs = list(random_directions(g, shp))
+    act = [n[d] > 1 for d in range(3)]
+    comps = [dirs[d] if act[d] else np.zeros(shp) for d in range(3)]
+    norm = np.sqrt(sum(cc ** 2 for cc in comps))
+    norm = np.where(norm > 0, norm, 1.0)
+    fields = {"E": E, "T": T, "rho": rho, "vx": None, "vy": None, "vz": None, "kP": None, "kF": None, "j": None}
+    for d, k in enumerate(("Fx", "Fy", "Fz")):
+        fields[k] = c * E * f * comps[d] / norm
+    return {"name": name, "desc": desc, "fields": fields, "chat": chat, "dt": dt, "n_sub": n_sub}
+
+
 def gas_case(name, n, bc="periodic", limiter="minmod", beta_tau=True, kappa=2.0, kappa_rho_pow=1, kF_array=False,
              seed=0, precision="fp64", dirichlet=None, exchange="full", n_sub=4, with_v=True, c=10.0, gamma=5.0 / 3.0):
     """A gas-step case: the random gas and radiation of parity_case (rho = exp(N(0, 0.5^2)), T = exp(N(0,

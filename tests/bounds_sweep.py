@@ -13,6 +13,7 @@ sys.path.insert(0, ROOT)
 
 from oracle import oracle as orc  # noqa: E402
 from paper_1306_0010_gb300 import rhd, workloads as wl  # noqa: E402
+from split_bounds import split_bound  # noqa: E402
 
 D = {"dirichlet": ([[1.2, 0.3, 0.0, 0.0], [0.9, 0.0, 0.2, 0.0], [1.1, 0.0, 0.0, 0.4]],
                    [[0.8, -0.2, 0.0, 0.0], [1.0, 0.0, 0.0, 0.0], [0.7, 0.0, 0.0, -0.1]])}
@@ -74,7 +75,8 @@ def main():
         ref, _ = orc.subcycles(case)
         print(json.dumps({"case": i, "n": n, "precision": precision, "launch": launch and launch["variant"],
                           "status": status, "bounds_violations": None if st is None else st["bounds_violations"],
-                          "message": msg, "error": errors(out, ref, case["desc"])}), flush=True)
+                          "message": msg, "error": errors(out, ref, case["desc"]),
+                          "bound": split_bound(case, case["n_sub"])}), flush=True)
     # an ensemble of tiny grids (persistent kernels, work queue)
     cases = [wl.parity_case("bounds_ens", n, bc="outflow", exchange="full", n_sub=2, seed=120 + k, precision="split")
              for k, n in enumerate([(5, 3, 3), (9, 4, 3), (33, 9, 5)])]
@@ -93,7 +95,7 @@ def main():
     ens.close()
     print(json.dumps({"case": "ensemble", "precision": "split", "status": status,
                       "bounds_violations": None if st is None else st["bounds_violations"], "message": msg,
-                      "error": err}), flush=True)
+                      "error": err, "bound": min(split_bound(c, 2) for c in cases)}), flush=True)
 
 
 if __name__ == "__main__":

@@ -9,10 +9,11 @@ import pytest
 from oracle import oracle as orc
 from paper_1306_0010_gb300 import workloads as wl
 
+from split_bounds import split_bound
+
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
-SPLIT_TOL = 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -91,7 +92,7 @@ def test_every_split_candidate_within_bound(rhd):
         assert g.get_stats()["n_nonfinite"] == 0
         g.close()
         e = errors(out, ref, case["desc"])
-        assert max(e.values()) <= SPLIT_TOL, (cfg, e)
+        assert max(e.values()) <= split_bound(case, case["n_sub"]), (cfg, e)
 
 
 def test_fp64_tuned_parity(rhd):
@@ -121,7 +122,7 @@ def test_flag_autotune_on_first_call_and_reuse(rhd):
     c1 = g1.launch_config()
     assert c1["ms_per_subcycle"] >= 0
     e = errors(snapshot(g1), ref, case["desc"])
-    assert max(e.values()) <= SPLIT_TOL, e
+    assert max(e.values()) <= split_bound(case, case["n_sub"]), e
     g1.close()
     g2 = rhd.Grid(desc)  # same shape and mode: the first context's choice is reused
     g2.load_case(case)
@@ -129,7 +130,7 @@ def test_flag_autotune_on_first_call_and_reuse(rhd):
     c2 = g2.launch_config()
     assert c2 == c1
     e = errors(snapshot(g2), ref, case["desc"])
-    assert max(e.values()) <= SPLIT_TOL, e
+    assert max(e.values()) <= split_bound(case, case["n_sub"]), e
     g2.close()
 
 
@@ -179,7 +180,7 @@ def test_ensemble_split_autotune_variants(rhd):
         out = ens.get_moments(i)
         out["T"] = ens.get_gas_state(i)
         ref, _ = orc.subcycles(c, n_sub=2)
-        assert max(errors(out, ref, c["desc"]).values()) <= SPLIT_TOL, i
+        assert max(errors(out, ref, c["desc"]).values()) <= split_bound(c, 2), i
     ens.close()
 
 

@@ -14,7 +14,6 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 FP64_TOL = 1e-12
-SPLIT_TOL = 2e-5
 
 
 def test_debug_build_finds_no_out_of_range_index():
@@ -33,5 +32,5 @@ def test_debug_build_finds_no_out_of_range_index():
     assert len(results) >= 14
     for res in results:
         assert res["status"] == 0 and res["bounds_violations"] == 0, res
-        tol = FP64_TOL if res["precision"] == "fp64" else SPLIT_TOL
+        tol = FP64_TOL if res["precision"] == "fp64" else res["bound"]  # split: split_bounds.split_bound
         assert res["error"] <= tol, res

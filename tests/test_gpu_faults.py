@@ -6,9 +6,10 @@ import pytest
 from oracle import oracle as orc
 from paper_1306_0010_gb300 import workloads as wl
 
+from split_bounds import split_bound
+
 pytestmark = pytest.mark.gpu
 
-SPLIT_TOL = 2e-5
 FP64_TOL = 1e-12
 
 
@@ -65,7 +66,7 @@ def test_superluminal_input_is_rescaled(rhd, precision):
     out = g.get_moments()
     g.close()
     assert st["n_realizability_fix"] > 0 and st_ref["n_realizability_fix"] > 0 and st["n_nonfinite"] == 0
-    tol = SPLIT_TOL if precision == "split" else FP64_TOL
+    tol = split_bound(case, 1) if precision == "split" else FP64_TOL
     sE = float(np.max(np.abs(ref["E"])))
     assert float(np.max(np.abs(out["E"] - ref["E"]))) <= tol * sE
     for k in ("Fx", "Fy", "Fz"):
@@ -120,4 +121,16 @@ def test_state_required_before_stepping(rhd):
     with pytest.raises(rhd.RhdError) as ei:
         g.get_moments()
     assert ei.value.status == rhd.ERR_STATE
+    g.close()
+
+
+def test_subnormal_energy_floor_rejected(rhd):
+    """E_floor must be a normal number of the arithmetic that divides by E: FP64 everywhere, FP32 on
+    split grids (whose closure takes FP32 reciprocals of E); a subnormal floor is an argument error."""
+    case = wl.parity_case("floor", (8, 6, 5), bc="periodic", n_sub=1, seed=3, precision="split")
+    for precision, floor in (("split", 1e-39), ("fp64", 1e-310)):
+        with pytest.raises(rhd.RhdError) as ei:
+            rhd.Grid(dict(case["desc"], precision=precision, E_floor=floor))
+        assert ei.value.status == rhd.ERR_ARG
+    g = rhd.Grid(dict(case["desc"], precision="split", E_floor=2e-38))  # normal in FP32: accepted
     g.close()

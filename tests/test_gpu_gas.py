@@ -27,7 +27,6 @@ pytestmark = pytest.mark.gpu
 
 GAS_TOL = 1e-11
 SPLIT_GAS_TOL = 1e-4
-SPLIT_TOL = 2e-5  # the split radiation path's bound (test_gpu_parity)
 
 
 @pytest.fixture(scope="module")

@@ -2,17 +2,17 @@
 
 For each case the normwise L1 and L-infinity errors of E, F (scaled by max|E| and c max|E|) and T
 (scaled by max|T|) are computed against the oracle on the same inputs, printed (run with -s to see
-them), and held to the split path's bound of 2e-5 in L-infinity.  Sizes are reduced so the oracle
-finishes in seconds; the recipes are those of the configurations."""
+them) beside the split path's bound derived in split_bounds.py, and held to that bound in L-infinity.
+Sizes are reduced so the oracle finishes in seconds; the recipes are those of the configurations."""
 import numpy as np
 import pytest
 
 from oracle import oracle as orc
 from paper_1306_0010_gb300 import workloads as wl
 
-pytestmark = pytest.mark.gpu
+from split_bounds import split_bound
 
-SPLIT_TOL = 2e-5
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -63,8 +63,9 @@ def test_split_error_report(rhd, name, make, n_sub):
     out = run(rhd, case, n_sub)
     ref, _ = orc.subcycles(case, n_sub=n_sub)
     res = norms(out, ref, case["desc"])
-    print(f"\n{name}: " + ", ".join(f"{k} L1 {l1:.2e} Linf {li:.2e}" for k, (l1, li) in res.items()))
-    assert max(li for _, li in res.values()) <= SPLIT_TOL, res
+    bound = split_bound(case, n_sub)
+    print(f"\n{name}: bound {bound:.2e}; " + ", ".join(f"{k} L1 {l1:.2e} Linf {li:.2e}" for k, (l1, li) in res.items()))
+    assert max(li for _, li in res.values()) <= bound, res
 
 
 def test_split_error_report_ensemble(rhd):
@@ -74,6 +75,7 @@ def test_split_error_report_ensemble(rhd):
         ens.load_case(i, c)
     ens.subcycle(20, 1.0, [c["dt"] for c in cases])
     worst = 0.0
+    bound = min(split_bound(c, 20) for c in cases)
     for i, c in enumerate(cases):
         out = ens.get_moments(i)
         out["T"] = ens.get_gas_state(i)
@@ -83,4 +85,4 @@ def test_split_error_report_ensemble(rhd):
               ", ".join(f"{k} L1 {l1:.2e} Linf {li:.2e}" for k, (l1, li) in res.items()))
         worst = max(worst, max(li for _, li in res.values()))
     ens.close()
-    assert worst <= SPLIT_TOL
+    assert worst <= bound, (worst, bound)
