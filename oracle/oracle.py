@@ -78,6 +78,8 @@ def lib():
         L.orc_hll.argtypes = [dp, dp, _c_int, _c_double, _c_int, _c_int, dp]
         L.orc_theta_factor.restype = _c_double
         L.orc_theta_factor.argtypes = [_c_double, _c_double]
+        L.orc_limited_slope.restype = _c_double
+        L.orc_limited_slope.argtypes = [_c_double, _c_double, _c_int]
         L.orc_quartic_root.restype = _c_double
         L.orc_quartic_root.argtypes = [_c_double, _c_double, _c_double]
         L.orc_exchange_full.restype = _c_int
@@ -175,6 +177,11 @@ def hll(UL, UR, d, chat, closure="m1", speeds="m1"):
 
 def theta_factor(theta, x):
     return lib().orc_theta_factor(float(theta), float(x))
+
+
+def limited_slope(dl, dr, limiter):
+    """The oracle's limited slope of a cell from its left / right differences (minmod, mc, none)."""
+    return lib().orc_limited_slope(float(dl), float(dr), LIMITER[limiter])
 
 
 def quartic_root(c4, c1, c0):

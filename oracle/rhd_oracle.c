@@ -459,7 +459,9 @@ static int face_unrealizable(const double U[4])
     return !(U[0] > 0.0) || (g2 > (1.0 + 1e-12) * (U[0] * U[0]));
 }
 
-static double limited_slope(double dl, double dr, int lim)
+/* Limited slope of a cell from its left and right differences (reading r4: componentwise on (E, G);
+ * minmod, monotonized central, or the unlimited central difference). */
+double orc_limited_slope(double dl, double dr, int lim)
 {
     if (lim == ORC_LIM_NONE) return 0.5 * (dl + dr);
     if (dl * dr <= 0.0) return 0.0;
@@ -550,7 +552,7 @@ static void run_block(work_t* w, double* Eo, double* Gxo, double* Gyo, double* G
                     long cr = bidx(b, i + e[d][0], jy + e[d][1], k + e[d][2]);
                     double s[4], Um_[4], Up_[4];
                     for (q = 0; q < 4; ++q) {
-                        s[q] = limited_slope(w->Uh[q][c] - w->Uh[q][cl], w->Uh[q][cr] - w->Uh[q][c],
+                        s[q] = orc_limited_slope(w->Uh[q][c] - w->Uh[q][cl], w->Uh[q][cr] - w->Uh[q][c],
                                              p->limiter);
                         Um_[q] = w->Uh[q][c] - 0.5 * s[q];
                         Up_[q] = w->Uh[q][c] + 0.5 * s[q];

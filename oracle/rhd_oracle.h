@@ -71,6 +71,9 @@ void orc_hll(const double UL[4], const double UR[4], int d, double chat, int clo
 /* theta-scheme factor [1 - (1-theta) x] / [1 + theta x], Eqs. (source:stiff:radmomentum:soln),
  * (source:stiff:radenergy:soln). */
 double orc_theta_factor(double theta, double x);
+/* Limited slope from the left and right differences dl = U_i - U_{i-1}, dr = U_{i+1} - U_i: lim =
+ * ORC_LIM_MINMOD, ORC_LIM_MC (monotonized central) or ORC_LIM_NONE ((dl + dr)/2). */
+double orc_limited_slope(double dl, double dr, int lim);
 
 /* Root in [0, b] of c4 x^4 + c1 x + c0 (c0 <= 0) by bisection to adjacent doubles,
  * b = min(|c0/c1|, |c0/c4|^(1/4)), Section 3.4. */

@@ -438,3 +438,24 @@ def test_negative_internal_energy_is_set_to_zero_and_flagged():
     assert W[4][0] == 0.0
     assert W[4][1] == pytest.approx(0.4 * (1.0 - 0.5 * 0.5 * 0.25))
 
+
+
+@pytest.mark.parametrize("kpow", [1, 2])
+def test_corrector_sources_take_the_opacity_at_the_half_step_density(kpow):
+    """The corrector's sources S_e,gas are evaluated at the half-step state (Section 3.4: second order
+    from U^{n+1/2}), so their absorption coefficient is k_F(rho^{n+1/2}), which the step also hands to the
+    source correction.  For a contact advected at a uniform v > 0 with uniform pressure and no radiation,
+    the predictor's HLLC flux is the upwind physical flux (the exact Godunov flux of a pure contact), so
+    rho^{n+1/2}_i = rho_i - (v dt / (2 dx)) (rho_i - rho_{i-1}) exactly; k_F at rho^n differs from it by
+    the upwind difference, about 0.1 of the density contrast here."""
+    n, v, dt, kap = 48, 0.7, 0.01, 2.0
+    d = desc1(n, bc="periodic", kappa_F=kap, kappa_rho_pow=kpow)
+    x = (np.arange(n) + 0.5) / n
+    rho = np.exp(0.5 * np.sin(2 * math.pi * x)).reshape(1, 1, n)
+    g = state(rho, (v, 0.0, 0.0), np.ones_like(rho))
+    _, pend, _ = gas.gas_step(d, g, zero_rad(rho.shape), dt)
+    rho_half = rho - (v * dt / (2.0 / n)) * (rho - np.roll(rho, 1, axis=2))
+    want = kap * rho_half ** kpow
+    assert np.max(np.abs(pend["kF"] - want) / want) < 1e-13
+    # the same at rho^n would be off by the upwind term
+    assert np.max(np.abs(kap * rho ** kpow - want) / want) > 1e-2
