@@ -345,17 +345,19 @@ rhd_status rhd_get_kernel_times(rhd_ctx* ctx, rhd_kernel_time* out, int capacity
  * until the process exits: 32 MiB for the working state, so grids of at most RHD_NOALLOC_MAX_CELLS
  * cells (larger grids return RHD_ERR_ARG).  It calls no cudaMalloc, cudaFree or allocating routine.
  *   d         grid descriptor; precision must be RHD_FP64; d->cuda_stream is the stream used (NULL:
- *             legacy default stream); the call returns without synchronising unless stats != NULL
+ *             legacy default stream); the call synchronises that stream before it returns (it reads
+ *             the call's event counters back, so that non-finite results are always reported)
  *   dirichlet 6 x 4 values (E, Fx, Fy, Fz) for faces 2*dir + side, or NULL (zeros)
  *   E..Fz     input moments; rho, T required; vx, vy, vz, kP, kF, j may be NULL (as in
  *             rhd_set_gas_state)
  *   *_out     output moments and gas temperature (may equal the inputs: the inputs are read first)
- *   stats     NULL, or counters of this call (sums are not computed; synchronises the stream)
+ *   stats     NULL, or counters of this call (sums are not computed)
  * The first call on a device looks up the scratch address on that device (make it before any stream
  * capture).  The scratch is shared by all calls and keeps the last call's contents; each call resets
  * what must start at zero.  Calls whose work overlaps on the GPU (other streams or threads) race on
  * the scratch and must be serialised by the caller.  Errors: RHD_ERR_ARG, RHD_ERR_CFL, RHD_ERR_CUDA,
- * RHD_ERR_NONFINITE (with stats); the message is in rhd_last_error(NULL). */
+ * RHD_ERR_NONFINITE (non-finite results, with or without stats); the message is in
+ * rhd_last_error(NULL). */
 #define RHD_NOALLOC_MAX_CELLS 1048576
 rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double dirichlet[24], int n_sub, double chat,
                                 double dt, const double* E, const double* Fx, const double* Fy, const double* Fz,
@@ -397,6 +399,12 @@ rhd_status rhd_suggest_chat(double c, double v_max, double tau_max, double ratio
  * 2^31 - 1 subcycles). */
 rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, double* dt_gas, double* dt_rad,
                           int* n_sub);
+
+/* The radiation subcycles that span a given gas step dt_gas (Eq. algorithm:radtimestep, as in
+ * rhd_time_steps but with dt_gas chosen by the caller): n_sub = the smallest n with
+ * dt_gas / n <= cfl dx_min / chat, dt_rad = dt_gas / n_sub.  Pure host arithmetic.  Errors: RHD_ERR_ARG
+ * (non-positive or non-finite input, NULL output, more than 2^31 - 1 subcycles). */
+rhd_status rhd_subcycle_steps(double cfl, double dx_min, double chat, double dt_gas, double* dt_rad, int* n_sub);
 
 /* 1 for the debug library librhd_debug.so, whose kernels check every global-memory index and the
  * shared-memory indices of the two-pass kernels against their arrays' extents (a substitute for a

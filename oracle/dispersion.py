@@ -1,7 +1,8 @@
 """Linear waves of the coupled radiation-hydrodynamics system under the reduced speed of light
 approximation (Section 4.3.1, "RHD Linear Waves"): the temporal dispersion relation (the initial value
 problem, Eq. radlinearwave:ivp:dispersion), its modes and their eigenvectors, and the initial state of a
-single mode for a simulation.
+single mode for a simulation.  TEST INFRASTRUCTURE: the checker of the linear-wave runs (the oracle's
+and the library's); the product library never uses it.
 
 Units are those of the paper's analysis: density rho_0 = 1, wavelength lambda = 1, adiabatic sound
 speed a_0 = 1 (time unit lambda / a_0), background at rest in radiative equilibrium, T_0 = 1.  The

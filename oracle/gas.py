@@ -18,8 +18,7 @@ What it computes, in the paper's order:
   * after the radiation subcycles, the correction of the sources to second order,
         dt/2 [S_e,gas(U_gas^{n+1/2}, U_rad^{n+1}) - S_e,gas(U_gas^{n+1/2}, U_rad^n)].
 
-Readings where the paper leaves the hydrodynamics to its host code (each is listed with the others in
-the design notes):
+Readings where the paper leaves the hydrodynamics to its host code:
   * Riemann solver: HLLC (Toro, "Riemann Solvers and Numerical Methods for Fluid Dynamics", Sec. 10.4)
     with the Davis wave-speed estimates S_L = min(u_L - a_L, u_R - a_R), S_R = max(u_L + a_L, u_R + a_R);
     the left star state is used when S* = 0; where the contact-speed denominator is not negative

@@ -14,8 +14,15 @@
  *       U^{m+1/2}, direct theta updates over dt) -> implicit energy exchange -> realizability.
  *   - the quartic of Eq. (source:polynomial) is solved by plain bisection to adjacent doubles,
  *     not by the Newton iteration the CUDA path uses.
- * Where the paper is silent the readings are those listed in the design notes (limiter,
- * face-state realizability, split order, ghost rule); each is marked "reading" below.
+ * Where the paper is silent these readings are taken (each is marked "reading" below):
+ *   - limiter: componentwise on (E, G); minmod, monotonized central or the unlimited central slope;
+ *   - face-state realizability: a reconstructed face value with E <= 0 or |G|^2 > (1 + 1e-12) E^2
+ *     zeroes that cell's slope in that direction;
+ *   - split order: the predictor takes the explicit O(beta tau) and emissivity sources from U^m and
+ *     the theta updates over dt/2; the corrector the explicit sources from U^{m+1/2}, the theta
+ *     updates over dt, then the energy exchange once, then E >= E_floor and |G| <= E (rescaling G);
+ *   - ghost rule: per direction in the order x, y, z, periodic wraps, outflow clamps, reflect mirrors
+ *     (negating the normal G and v), Dirichlet returns the face state.
  *
  * Compile with -ffp-contract=off so that x86-64 and aarch64 give the same bits.
  */

@@ -38,8 +38,8 @@ __device__ __forceinline__ double f2d_exact(float f)
 // two of 1/x, not the correctly rounded quotient, which the FP64 path does not need (its bound
 // against the oracle is 1e-12) and which costs several more FP64 operations.  x = 0, +-inf and FP64
 // denormals (flushed) give NaN.
-__device__ __forceinline__ double rsq(double x) { return sqrt(x); }
-__device__ __forceinline__ float rsq(float x)
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_fast(float x)
 {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

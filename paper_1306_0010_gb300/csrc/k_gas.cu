@@ -134,7 +134,7 @@ template <typename R, int D>
 __device__ void hllc(const Consts<R>& k, const Prim<R>& L, const Prim<R>& Rt, R F[5])
 {
     const R irL = rcp(L.r), irR = rcp(Rt.r);
-    const R aL = rsq(k.gamma * L.P * irL), aR = rsq(k.gamma * Rt.P * irR);
+    const R aL = sqrt_fast(k.gamma * L.P * irL), aR = sqrt_fast(k.gamma * Rt.P * irR);
     const R uL = L.v[D], uR = Rt.v[D];
     const R SL = fmin(uL - aL, uR - aR), SR = fmax(uL + aL, uR + aR);
     R FL[5], FR[5], EL, ER;

@@ -1684,21 +1684,36 @@ rhd_status rhd_suggest_chat(double c, double v_max, double tau_max, double ratio
     return RHD_OK;
 }
 
+// the fewest subcycles of length <= dmax spanning dg (Eq. algorithm:radtimestep)
+static rhd_status span_subcycles(double dg, double dmax, double* dt_rad, int* n_sub)
+{
+    const double q = std::ceil(dg / dmax);
+    if (!(q < 2147483647.0)) return fail(nullptr, RHD_ERR_ARG, "more than 2^31 subcycles per gas step");
+    int n = std::max(1, (int)q);
+    while (dg / n > dmax) ++n;
+    *dt_rad = dg / n;
+    *n_sub = n;
+    return RHD_OK;
+}
+
 rhd_status rhd_time_steps(double cfl, double dx_min, double v_max, double chat, double* dt_gas, double* dt_rad,
                           int* n_sub)
 {
     if (!dt_gas || !dt_rad || !n_sub) return fail(nullptr, RHD_ERR_ARG, "dt_gas, dt_rad and n_sub are required");
     if (!finite_pos(cfl) || !finite_pos(dx_min) || !finite_pos(v_max) || !finite_pos(chat))
         return fail(nullptr, RHD_ERR_ARG, "cfl, dx_min, v_max and chat must be positive and finite");
-    const double dg = cfl * dx_min / v_max, dmax = cfl * dx_min / chat;
-    const double q = std::ceil(dg / dmax);
-    if (!(q < 2147483647.0)) return fail(nullptr, RHD_ERR_ARG, "more than 2^31 subcycles per gas step");
-    int n = std::max(1, (int)q);
-    while (dg / n > dmax) ++n;
-    *dt_gas = dg;
-    *dt_rad = dg / n;
-    *n_sub = n;
-    return RHD_OK;
+    const double dg = cfl * dx_min / v_max;
+    const rhd_status st = span_subcycles(dg, cfl * dx_min / chat, dt_rad, n_sub);
+    if (st == RHD_OK) *dt_gas = dg;
+    return st;
+}
+
+rhd_status rhd_subcycle_steps(double cfl, double dx_min, double chat, double dt_gas, double* dt_rad, int* n_sub)
+{
+    if (!dt_rad || !n_sub) return fail(nullptr, RHD_ERR_ARG, "dt_rad and n_sub are required");
+    if (!finite_pos(cfl) || !finite_pos(dx_min) || !finite_pos(chat) || !finite_pos(dt_gas))
+        return fail(nullptr, RHD_ERR_ARG, "cfl, dx_min, chat and dt_gas must be positive and finite");
+    return span_subcycles(dt_gas, cfl * dx_min / chat, dt_rad, n_sub);
 }
 
 rhd_status rhd_marshak_boundary(double tau, double eps, double F_inc, double c, int n_quad, double state[4])

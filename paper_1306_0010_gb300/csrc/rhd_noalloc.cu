@@ -160,10 +160,11 @@ extern "C" rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double 
     } else {
         for (int q = 0; q < 3; ++q) NA_CUDA(launch_scale_copy(B[1 + q], B[1 + q], -d->c, n, s));
     }
+    // the counters come back on every call, so that non-finite results are never reported as success
+    DevStats h;
+    NA_CUDA(cudaMemcpyAsync(&h, dstats, sizeof(h), cudaMemcpyDeviceToHost, s));
+    NA_CUDA(cudaStreamSynchronize(s));
     if (stats) {
-        DevStats h;
-        NA_CUDA(cudaMemcpyAsync(&h, dstats, sizeof(h), cudaMemcpyDeviceToHost, s));
-        NA_CUDA(cudaStreamSynchronize(s));
         std::memset(stats, 0, sizeof(*stats));
         stats->n_subcycles = n_sub;
         stats->n_realizability_fix = (int64_t)h.n_fix;
@@ -172,7 +173,7 @@ extern "C" rhd_status rhd_subcycle_noalloc(const rhd_grid_desc* d, const double 
         stats->n_newton_fallback = (int64_t)h.n_newton_fb;
         stats->n_nonfinite = (int64_t)h.n_nonfinite;
         stats->newton_iter_max = (int32_t)h.newton_iter_max;
-        if (h.n_nonfinite) return noalloc_fail(RHD_ERR_NONFINITE, "non-finite values were produced");
     }
+    if (h.n_nonfinite) return noalloc_fail(RHD_ERR_NONFINITE, "non-finite values were produced");
     return RHD_OK;
 }

@@ -133,13 +133,13 @@ __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R 
         // f = 1 along n = G/|G|, i.e. of the state (E, G/f), so mu f = gd/(E f) in the wave speeds and
         // b G G^T = E n n^T with b = 1/(E f^2).  Face states of the corrector have passed the
         // realizability test and never take this branch beyond its rounding allowance.
-        const R q = rcp(rsq(f2));
+        const R q = rcp(sqrt_fast(f2));
         invE = xmul(invE, q);
         invEb = xmul(invE, q);
         f2 = R(1);
     }
     k.invE = invE;
-    k.s = rsq(xfma(R(-3), f2, R(4)));
+    k.s = sqrt_fast(xfma(R(-3), f2, R(4)));
     k.inv2ps = rcp(xadd(R(2), k.s));
     k.cs = xmul(chat, rcp(k.s));
     if (p1) {
@@ -167,7 +167,7 @@ __device__ __forceinline__ void wave_speeds(const ClosureScalars<R>& k, R gd, R 
     const R fd = xmul(gd, k.invE);
     R rad = xmul(xmul(R(2.0 / 3.0), xadd(k.s, R(-1))), xfma(-xmul(xmul(R(3), fd), fd), k.inv2ps, k.s));
     rad = rmax(rad, R(0));
-    const R sr = rsq(rad);
+    const R sr = sqrt_fast(rad);
     l1 = xmul(xadd(fd, -sr), k.cs);
     l3 = xmul(xadd(fd, sr), k.cs);
 }
@@ -580,7 +580,7 @@ __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float 
     const float B = 1.0f + r * eta * th;
     const float C = eta * ((1.0f - th) * alpha * e4 - E);
     float b = fabsf(c0 * rcp(B));
-    if (A > 0.0f) b = fminf(b, rsq(rsq(fabsf(c0 * rcp(A)))));
+    if (A > 0.0f) b = fminf(b, sqrt_fast(sqrt_fast(fabsf(c0 * rcp(A)))));
     const float dhi = b - e, dlo = -e;
     float d = 0.0f;
     bool conv = false;

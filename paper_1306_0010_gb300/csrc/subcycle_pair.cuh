@@ -16,7 +16,7 @@ __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return _
 __device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 p_s(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 p_rcp(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
-__device__ __forceinline__ float2 p_sqrt(float2 a) { return make_float2(rsq(a.x), rsq(a.y)); }
+__device__ __forceinline__ float2 p_sqrt(float2 a) { return make_float2(sqrt_fast(a.x), sqrt_fast(a.y)); }
 __device__ __forceinline__ float2 p_lo(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 p_hi(float4 v) { return make_float2(v.z, v.w); }
 

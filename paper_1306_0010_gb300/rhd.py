@@ -183,6 +183,7 @@ _SIGS = {
     "rhd_suggest_chat": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)]),
     "rhd_time_steps": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double)] * 2
                        + [ctypes.POINTER(ctypes.c_int)]),
+    "rhd_subcycle_steps": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "rhd_bounds_checked": (ctypes.c_int, []),
     "rhd_marshak_boundary": (ctypes.c_int, [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rhd_marshak_advance": (ctypes.c_int, [_P, ctypes.c_int] + [ctypes.c_double] * 6 + [ctypes.c_int]),
@@ -346,8 +347,7 @@ class Grid:
         if dt_gas is None:
             dt_gas, dt_rad, n_sub = time_steps(cfl, dxm, self.max_signal_speed(), chat)
         else:
-            n_sub = max(1, int(np.ceil(dt_gas / (cfl * dxm / chat) * (1 - 1e-12))))
-            dt_rad = dt_gas / n_sub
+            dt_rad, n_sub = subcycle_steps(cfl, dxm, chat, dt_gas)
         self.gas_step(dt_gas)
         self.radiation_subcycle(n_sub, chat, dt_rad)
         self.gas_correct()
@@ -628,6 +628,15 @@ def time_steps(cfl, dx_min, v_max, chat):
     _check(None, lib().rhd_time_steps(float(cfl), float(dx_min), float(v_max), float(chat), ctypes.byref(dg),
                                       ctypes.byref(dr), ctypes.byref(n)))
     return dg.value, dr.value, n.value
+
+
+def subcycle_steps(cfl, dx_min, chat, dt_gas):
+    """(dt_rad, n_sub): the fewest subcycles of length <= cfl dx_min / chat spanning dt_gas (Eq.
+    algorithm:radtimestep)."""
+    dr, n = ctypes.c_double(), ctypes.c_int()
+    _check(None, lib().rhd_subcycle_steps(float(cfl), float(dx_min), float(chat), float(dt_gas), ctypes.byref(dr),
+                                          ctypes.byref(n)))
+    return dr.value, n.value
 
 
 def marshak_boundary(tau, eps, F_inc, c, n_quad=4096):

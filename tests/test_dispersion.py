@@ -9,7 +9,7 @@ import pytest
 
 from oracle import gas as ogas
 from oracle import oracle as orc
-from paper_1306_0010_gb300 import dispersion as dsp
+from oracle import dispersion as dsp
 from paper_1306_0010_gb300 import workloads as wl
 
 G = 5.0 / 3.0

@@ -5,8 +5,9 @@ Tolerance: the kernels and the oracle evaluate the same FP64 formulas; they diff
 (the kernels multiply by reciprocals of dx, gamma - 1 and mu/k_B, and the compiler contracts products
 and sums into fused multiply-adds).  One step is a few hundred operations per cell, each off by at most
 an ulp, and the branches of the Riemann solver and the limiter are continuous, so a flipped branch also
-costs only rounding: normwise errors stay near 1e-14.  The bound used is GAS_TOL = 1e-11 per field (rho
-by max rho, v by max(|v| + a), T by max T).
+costs only rounding: normwise errors stay near 1e-15 (measured up to 6e-16).  The bound used is the FP64
+path's, GAS_TOL = 1e-12 per field (rho by max rho, v by max(|v| + a), T by max T), also for a whole cycle
+(gas step, radiation subcycles, correction).
 
 Split grids compute the face fluxes in FP32 (inputs truncated to FP32, hardware reciprocal and square
 root approximations) and everything else in FP64.  A face flux then carries a relative error of at
@@ -25,7 +26,7 @@ from paper_1306_0010_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-GAS_TOL = 1e-11
+GAS_TOL = 1e-12
 SPLIT_GAS_TOL = 1e-4
 
 
@@ -112,7 +113,7 @@ def test_gas_step_and_correction_match_oracle(rhd, kw):
     print(name, "max normwise error", max(e.values()))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("split", SPLIT_GAS_TOL)])
+@pytest.mark.parametrize("precision,tol", [("fp64", GAS_TOL), ("split", SPLIT_GAS_TOL)])
 def test_whole_cycle_matches_oracle(rhd, precision, tol):
     """Section 3.1 steps 3-6: gas step, n_sub radiation subcycles with the new gas, source correction."""
     case = wl.gas_case("cycle", (12, 10, 8), bc=(["periodic", "outflow", "reflect"], ["periodic", "outflow", "outflow"]),

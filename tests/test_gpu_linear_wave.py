@@ -14,7 +14,7 @@ import math
 import numpy as np
 import pytest
 
-from paper_1306_0010_gb300 import dispersion as dsp
+from oracle import dispersion as dsp
 
 pytestmark = pytest.mark.gpu
 
