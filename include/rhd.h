@@ -112,6 +112,11 @@ typedef enum { RHD_FP64 = 0, RHD_SPLIT = 1 } rhd_precision;
  * then loaded, unless a context of the same shape and mode was tuned before in this process, whose
  * choice is reused. */
 #define RHD_FLAG_AUTOTUNE 4
+/* RHD_FLAG_EXCHANGE_ON_GAS_STEP: the paper's placement of the stiff energy exchange (Section 3.1 step 2,
+ * Section 3.4: S_i integrated once per gas step): with exchange = RHD_EX_FULL the subcycles carry no
+ * exchange term and rhd_gas_exchange integrates it over Delta t_gas before the gas step.  Single grids
+ * only; requires RHD_EX_FULL. */
+#define RHD_FLAG_EXCHANGE_ON_GAS_STEP 8
 
 typedef struct {
     int n[3];                   /* nx, ny, nz */
@@ -203,7 +208,8 @@ rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double d
  * arrays (starting at zero).  Ghost cells follow the grid's boundary conditions (a Dirichlet face
  * takes the nearest cell for the gas).  A negative internal energy is set to zero (counted in
  * rhd_stats.gas_energy_floors).  The step leaves a source correction pending: run the radiation
- * subcycles that span dt_gas, then rhd_gas_correct.  The energy exchange stays in the subcycles.
+ * subcycles that span dt_gas, then rhd_gas_correct.  The energy exchange stays in the subcycles unless
+ * the grid has RHD_FLAG_EXCHANGE_ON_GAS_STEP (then rhd_gas_exchange runs it once, before this step).
  * RHD_SPLIT grids compute the face fluxes (reconstruction, wave speeds, HLLC) and their differences in
  * FP32 and the rest in FP64.  Does not synchronise.  Scratch, allocated by the first call, for n cells
  * and m = (n0+4)(n1+4)(n2+4) (2D / 1D: no padding in inactive directions): 5 m + 8 n doubles, and 15 m
@@ -217,6 +223,17 @@ rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas);
  * (Section 3.4), where U_gas^{n+1/2} and U_rad^n are those the step used.  Does not synchronise.
  * Errors: RHD_ERR_STATE (no pending step, ensemble), RHD_ERR_CUDA. */
 rhd_status rhd_gas_correct(rhd_ctx* ctx);
+
+/* Section 3.1 step 2 with the paper's placement of the stiff exchange S_i (Eq. algorithm:source:implicit):
+ * integrate the gas-radiation energy exchange once over dt_gas, before the gas step, in every cell: E
+ * floored at E_floor, then the FULL quartic theta scheme of the subcycles (Eqs. source:energyupdate -
+ * source:polynomial, updating E and T, with the grid's theta_E, a_rad, gamma, mu_over_kB and kP) over
+ * dt_gas with this chat, then |F| <= c E by rescaling F.  FP64 on every grid (it runs once per gas step).
+ * The grid must have exchange = RHD_EX_FULL and RHD_FLAG_EXCHANGE_ON_GAS_STEP, whose subcycles then
+ * carry no exchange term.  Counts theta fallbacks, Newton fallbacks, flux rescalings and non-finite
+ * cells in rhd_stats.  Does not synchronise.  Errors: RHD_ERR_ARG (dt_gas < 0 or not finite, chat not in
+ * (0, c]), RHD_ERR_STATE (the flag is not set, ensemble, gas or moments not set), RHD_ERR_CUDA. */
+rhd_status rhd_gas_exchange(rhd_ctx* ctx, double dt_gas, double chat);
 
 /* Copy the gas state out: rho, vx, vy, vz, T (any may be NULL to skip it; an absent velocity component
  * reads as zero).  Layout as rhd_set_gas_state.  Synchronises the stream.  Errors: RHD_ERR_ARG,

@@ -1,4 +1,6 @@
 // k_fp64.cu -- FP64 instantiations of the fused subcycle kernel and of the ensemble kernel.
+#include <algorithm>
+
 #include "subcycle.cuh"
 
 namespace rhd {
@@ -78,6 +80,53 @@ cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream
 }
 
 int ensemble_ctas_per_sm_fp64() { return ens_occupancy<double, 16, 8, false>(); }
+
+// The stiff exchange integrated once per gas step (Section 3.1 step 2, the paper's placement of S_i): in
+// every cell, E floored at E_floor, then the FULL quartic theta scheme of the subcycles (exchange_fp64,
+// Eqs. source:energyupdate - source:polynomial) over dt = Delta t_gas, then |G| <= E by rescaling G.
+// FP64 on every grid: it runs once per gas step, not per subcycle.  One thread per cell, grid-stride.
+__global__ void __launch_bounds__(256) gas_exchange_kernel(const __grid_constant__ GasExchangeParams P)
+{
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0};
+    const GridParams& g = P.g;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (long long)gridDim.x * blockDim.x) {
+        double E = P.E[i], T = P.T[i];
+        const double rho = P.rho[i];
+        const double kP = P.kP ? P.kP[i] : kappa_law(g.kappa_P, g.kpow, rho);
+        if (E < g.E_floor) E = g.E_floor;
+        const ExchangeOut o = exchange_fp64(g, P.chat, P.dt, rho, kP, E, T);
+        cnt.theta += o.theta_fb;
+        cnt.newton_fb += o.newton_fb;
+        cnt.iter_max = max(cnt.iter_max, (unsigned)o.iters);
+        double G[3] = {P.G[0][i], P.G[1][i], P.G[2][i]};
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        if (g2 > E * E) {
+            const double sc = E / sqrt(g2);
+            G[0] *= sc;
+            G[1] *= sc;
+            G[2] *= sc;
+            cnt.fix += 1;
+        }
+        cnt.nonfinite += !(finite_d(E) && finite_d(T) && finite_d(G[0]) && finite_d(G[1]) && finite_d(G[2]));
+        P.E[i] = E;
+        P.T[i] = T;
+        P.G[0][i] = G[0];
+        P.G[1][i] = G[1];
+        P.G[2][i] = G[2];
+    }
+    add_counter(&P.stats->n_fix, cnt.fix);
+    add_counter(&P.stats->n_theta, cnt.theta);
+    add_counter(&P.stats->n_newton_fb, cnt.newton_fb);
+    add_counter(&P.stats->n_nonfinite, cnt.nonfinite);
+    max_counter(&P.stats->newton_iter_max, cnt.iter_max);
+}
+
+cudaError_t launch_gas_exchange(const GasExchangeParams& p, int num_sms, cudaStream_t s)
+{
+    const long long blocks = std::min<long long>((p.n + 255) / 256, (long long)num_sms * 8);
+    gas_exchange_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 // Out-of-range index record of this module's kernels (debug builds; the release build has none and
 // reports 0): copied to *out on stream s and, with reset, zeroed after the copy.

@@ -211,6 +211,8 @@ rhd_status validate_desc(rhd_ctx* ctx, const rhd_grid_desc* d)
     if (d->exchange < 0 || d->exchange > 4) return fail(ctx, RHD_ERR_ARG, "unknown exchange mode");
     if (d->exchange == RHD_EX_LINEAR && !finite_pos(d->linear_eps))
         return fail(ctx, RHD_ERR_ARG, "the linear exchange needs linear_eps > 0");
+    if ((d->flags & RHD_FLAG_EXCHANGE_ON_GAS_STEP) && d->exchange != RHD_EX_FULL)
+        return fail(ctx, RHD_ERR_ARG, "RHD_FLAG_EXCHANGE_ON_GAS_STEP needs exchange = RHD_EX_FULL");
     if (d->limiter < 0 || d->limiter > 2) return fail(ctx, RHD_ERR_ARG, "unknown limiter");
     if (d->closure < 0 || d->closure > 1) return fail(ctx, RHD_ERR_ARG, "unknown closure");
     if (d->speeds < 0 || d->speeds > 1) return fail(ctx, RHD_ERR_ARG, "unknown wave-speed option");
@@ -251,7 +253,8 @@ void fill_params(GridState& gs)
     g.kappa_P = d.kappa_P;
     g.kappa_F = d.kappa_F;
     g.kpow = d.kappa_rho_pow;
-    g.exchange = d.exchange;
+    // the paper's placement of the exchange: none in the subcycles (rhd_gas_exchange runs it once per gas step)
+    g.exchange = (d.flags & RHD_FLAG_EXCHANGE_ON_GAS_STEP) ? RHD_EX_EQUILIBRIUM : d.exchange;
     g.linear_eps = d.linear_eps;
     g.beta_tau = d.beta_tau ? 1 : 0;
     g.limiter = d.limiter;
@@ -633,14 +636,14 @@ rhd_status check_dt(rhd_ctx* ctx, const GridState& gs, double chat, double dt)
 // kernels reported by the kernel timer
 enum KernelId {
     K_FUSED_FP64 = 0, K_FUSED_SPLIT, K_PREDICTOR, K_CORRECTOR, K_ENS_FP64, K_ENS_SPLIT, K_ENS_PRED, K_ENS_CORR,
-    K_GAS_PRED_FLUX, K_GAS_PRED_UPDATE, K_GAS_CORR_FLUX, K_GAS_CORR_UPDATE, K_GAS_CORRECT,
+    K_GAS_PRED_FLUX, K_GAS_PRED_UPDATE, K_GAS_CORR_FLUX, K_GAS_CORR_UPDATE, K_GAS_CORRECT, K_GAS_EXCHANGE,
     K_COUNT
 };
 const char* const kKernelNames[K_COUNT] = {"subcycle_fused_fp64", "subcycle_fused_split", "twopass_predictor_split",
                                            "twopass_corrector_split", "ensemble_fp64", "ensemble_split",
                                            "ensemble_predictor_split", "ensemble_corrector_split",
                                            "gas_predictor_flux", "gas_predictor_update", "gas_corrector_flux",
-                                           "gas_corrector_update", "gas_source_correction"};
+                                           "gas_corrector_update", "gas_source_correction", "gas_step_exchange"};
 
 // Algorithmic bytes per interior cell of one launch of kernel k: every array the kernel reads, read
 // once, and every array it writes, written once.  Fused kernels: U^m and U^{m+1} (4 FP64 each), the
@@ -653,7 +656,7 @@ double alg_bytes_per_cell(const GridState& gs, int k)
     const double w = split ? 4.0 : 8.0;
     const double opt = w * ((gs.has_kP ? 1 : 0) + (gs.has_kF ? 1 : 0) + (gs.has_j ? 1 : 0));
     const double gas = w * (1 + (gs.has_v ? 3 : 0)) + opt;
-    const int ex = gs.desc.exchange;
+    const int ex = gs.gp.exchange;  // the subcycles' exchange (none with RHD_FLAG_EXCHANGE_ON_GAS_STEP)
     const bool tw = ex == RHD_EX_FULL || ex == RHD_EX_LINEAR;
     const double Tr = (tw || ex == RHD_EX_FROZEN_T) ? 8.0 : 0.0, Tw = tw ? 8.0 : 0.0;
     switch (k) {
@@ -1048,7 +1051,7 @@ std::string tune_key(rhd_ctx* ctx)
     for (auto& gs : ctx->grids) {
         const rhd_grid_desc& d = gs.desc;
         k += ":" + std::to_string(d.n[0]) + "x" + std::to_string(d.n[1]) + "x" + std::to_string(d.n[2]) + "/" +
-             std::to_string(d.precision) + std::to_string(d.exchange) + std::to_string(d.beta_tau) +
+             std::to_string(d.precision) + std::to_string(gs.gp.exchange) + std::to_string(d.beta_tau) +
              std::to_string(d.limiter) + std::to_string(d.closure) + std::to_string(d.speeds) +
              std::to_string(gs.has_v) + std::to_string(gs.has_kP) + std::to_string(gs.has_kF) +
              std::to_string(gs.has_j);
@@ -1617,6 +1620,40 @@ rhd_status rhd_gas_correct(rhd_ctx* ctx)
     return leave(ctx);
 }
 
+rhd_status rhd_gas_exchange(rhd_ctx* ctx, double dt_gas, double chat)
+{
+    ApiRange range_("rhd_gas_exchange");
+    rhd_status st = single_grid(ctx, "rhd_gas_exchange");
+    if (st) return st;
+    GridState& gs = ctx->grids[0];
+    if (!(gs.desc.flags & RHD_FLAG_EXCHANGE_ON_GAS_STEP))
+        return fail(ctx, RHD_ERR_STATE, "the grid exchanges in its subcycles (no RHD_FLAG_EXCHANGE_ON_GAS_STEP)");
+    if (!(std::isfinite(dt_gas) && dt_gas >= 0.0)) return fail(ctx, RHD_ERR_ARG, "dt_gas must be finite and >= 0");
+    if (!(chat > 0.0 && chat <= gs.desc.c)) return fail(ctx, RHD_ERR_ARG, "chat must lie in (0, c]");
+    if (!gs.has_moments || !gs.has_gas) return fail(ctx, RHD_ERR_STATE, "set the moments and the gas state first");
+    if ((st = enter(ctx))) return st;
+    GasExchangeParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.g = gs.gp;
+    p.g.exchange = RHD_EX_FULL;
+    double** U = gs.U[ctx->cur];
+    p.E = U[0];
+    for (int q = 0; q < 3; ++q) p.G[q] = U[1 + q];
+    p.T = gs.T;
+    p.rho = gs.rho;
+    p.kP = gs.has_kP ? gs.kP : nullptr;
+    p.chat = chat;
+    p.dt = dt_gas;
+    p.n = gs.ncell;
+    p.stats = ctx->dstats;
+    // E, G, T: read 40 B and written 40 B per cell; rho (and kP) read
+    const double bytes = (double)gs.ncell * (80.0 + 8.0 + (gs.has_kP ? 8.0 : 0.0));
+    if ((st = timed_launch(ctx, K_GAS_EXCHANGE, bytes, [&] { return launch_gas_exchange(p, ctx->num_sms, ctx->stream); })))
+        return st;
+    gs.um32_ok = false;  // the state changed: the two-pass path's FP32 mirror is rebuilt before the next subcycle
+    return leave(ctx);
+}
+
 rhd_status rhd_get_gas(rhd_ctx* ctx, double* rho, double* vx, double* vy, double* vz, double* T, int on_device)
 {
     ApiRange range_("rhd_get_gas");
@@ -1841,6 +1878,10 @@ rhd_status rhd_synchronize(rhd_ctx* ctx, int timeout_ms)
 rhd_status rhd_ensemble_create(rhd_ctx** out, int n_grids, const rhd_grid_desc* descs)
 {
     ApiRange range_("rhd_ensemble_create");
+    if (descs && n_grids > 0)
+        for (int g = 0; g < n_grids; ++g)
+            if (descs[g].flags & RHD_FLAG_EXCHANGE_ON_GAS_STEP)
+                return fail(nullptr, RHD_ERR_ARG, "RHD_FLAG_EXCHANGE_ON_GAS_STEP needs a single grid (ensembles have no gas step)");
     if (!out || !descs || n_grids < 1) return fail(nullptr, RHD_ERR_ARG, "out, descs and n_grids >= 1 are required");
     for (int i = 0; i < n_grids; ++i) {
         rhd_status st = validate_desc(nullptr, descs + i);

@@ -89,6 +89,19 @@ struct StepParams {
     CUtensorMap uh_map;         // staging 1: tensor map of uhalf as floats {4 (n0+4), n1+4, n2+4}, box {4 (32+4), 8+4, 1}
 };
 
+// The exchange once per gas step (rhd_gas_exchange): the current state and the gas, updated in place.
+struct GasExchangeParams {
+    GridParams g;               // exchange parameters (theta_E, a_rad, gamma, mu_over_kB, E_floor, kappa law)
+    double* E;
+    double* G[3];
+    double* T;
+    const double* rho;
+    const double* kP;           // NULL: the opacity law
+    double chat, dt;
+    long long n;
+    DevStats* stats;
+};
+
 // Ensemble work items: (grid, tile) pairs handed out by a global counter.
 struct EnsembleGrid {
     GridParams g;
@@ -160,6 +173,7 @@ cudaError_t launch_to_gas4(float4* dst, const float* rho32, const float* vx, con
 // missing or the encoding is refused.
 bool encode_uhalf_map(CUtensorMap* map, float4* uhalf, const GridParams& g);
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s);
+cudaError_t launch_gas_exchange(const GasExchangeParams& p, int num_sms, cudaStream_t s);
 cudaError_t launch_ensemble_split(const EnsembleParams& p, int n_ctas, cudaStream_t s);
 int ensemble_ctas_per_sm_fp64();
 int ensemble_ctas_per_sm_split();

@@ -33,6 +33,7 @@ PRECISION = {"fp64": 0, "split": 1}
 FLAG_NO_GRAPH = 1
 FLAG_SPLIT_FUSED = 2
 FLAG_AUTOTUNE = 4
+FLAG_EXCHANGE_ON_GAS_STEP = 8
 VARIANT = {"fused": 0, "twopass": 1}
 STAGING = {"cpasync": 0, "tma": 1}
 
@@ -151,6 +152,7 @@ _SIGS = {
     "rhd_radiation_subcycle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
     "rhd_gas_step": (ctypes.c_int, [_P, ctypes.c_double]),
     "rhd_gas_correct": (ctypes.c_int, [_P]),
+    "rhd_gas_exchange": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double]),
     "rhd_get_gas": (ctypes.c_int, [_P] + [_P] * 5 + [ctypes.c_int]),
     "rhd_get_moments": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
     "rhd_set_conserved": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
@@ -333,6 +335,11 @@ class Grid:
         _check(self._ctx, lib().rhd_gas_step(self._ctx, float(dt_gas)))
         self._gas_stepped = self._gas_pending = True
 
+    def gas_exchange(self, dt_gas, chat):
+        """Section 3.1 step 2 with the paper's placement of the stiff exchange (grids with
+        FLAG_EXCHANGE_ON_GAS_STEP): the FULL energy exchange integrated once over dt_gas in every cell."""
+        _check(self._ctx, lib().rhd_gas_exchange(self._ctx, float(dt_gas), float(chat)))
+
     def gas_correct(self):
         """Section 3.1 step 6: the pending gas step's sources corrected with the current radiation."""
         _check(self._ctx, lib().rhd_gas_correct(self._ctx))
@@ -340,14 +347,17 @@ class Grid:
 
     def gas_cycle(self, chat, cfl=None, ratio=None, dt_gas=None):
         """One whole cycle of Section 3.1: time steps (unless dt_gas is given: then the subcycles are
-        the fewest of length <= cfl min(dx) / chat spanning it), the gas step, the radiation subcycles
-        over dt_gas, the source correction.  Returns (dt_gas, n_sub)."""
+        the fewest of length <= cfl min(dx) / chat spanning it), on grids with FLAG_EXCHANGE_ON_GAS_STEP
+        the energy exchange over dt_gas (step 2), the gas step, the radiation subcycles over dt_gas, the
+        source correction.  Returns (dt_gas, n_sub)."""
         cfl = self.desc.get("cfl", 0.4) if cfl is None else cfl
         dxm = min(self.desc["dx"][d] for d in range(3) if self.desc["n"][d] > 1)
         if dt_gas is None:
             dt_gas, dt_rad, n_sub = time_steps(cfl, dxm, self.max_signal_speed(), chat)
         else:
             dt_rad, n_sub = subcycle_steps(cfl, dxm, chat, dt_gas)
+        if int(self.desc.get("flags", 0)) & FLAG_EXCHANGE_ON_GAS_STEP:
+            self.gas_exchange(dt_gas, chat)
         self.gas_step(dt_gas)
         self.radiation_subcycle(n_sub, chat, dt_rad)
         self.gas_correct()
