@@ -334,6 +334,15 @@ rhd_status rhd_get_launch_config(rhd_ctx* ctx, rhd_launch_config* out);
  * this grid's precision and dimension.  Drops captured graphs. */
 rhd_status rhd_set_launch_config(rhd_ctx* ctx, const rhd_launch_config* cfg);
 
+/* Poll limit of the waits on the TMA staging of the two-pass corrector (each plane's tensor copy is
+ * awaited on an mbarrier by at most `polls` try-wait polls): polls < 0 restores the default (2^22 polls,
+ * far beyond a copy's time), 0 makes every such wait give up at once.  For tests of the timeout path
+ * (failure detection without a GPU fault): a tile whose wait gives up abandons its work (its cells keep
+ * no new values), its one copy in flight is still awaited with the default bound before the block exits,
+ * and rhd_get_stats reports RHD_ERR_TIMEOUT with rhd_stats.wait_timeouts.  Applies to later calls (the
+ * context's captured graphs are dropped).  No paper counterpart.  Errors: RHD_ERR_ARG. */
+rhd_status rhd_set_wait_limit(rhd_ctx* ctx, long long polls);
+
 /* ---------------------------------------------------------------------------------------------
  * Kernel timer.  While enabled, subcycles are issued as plain launches (no graph) with a CUDA event
  * recorded on the context's stream before and after every kernel.  rhd_get_kernel_times

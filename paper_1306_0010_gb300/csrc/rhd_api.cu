@@ -105,6 +105,7 @@ struct rhd_ctx {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<GridState> grids;
     int cur = 0;  // buffer index holding the current state (shared by all grids)
+    unsigned wait_polls = 1u << 22;  // polls of the two-pass corrector's TMA plane waits (rhd_set_wait_limit)
     DevStats* dstats = nullptr;
     double* red_partials = nullptr;
     double* rsla_partial = nullptr;  // reduced-speed-of-light reductions: rsla_blocks() + 1 doubles
@@ -610,6 +611,7 @@ StepParams step_params(rhd_ctx* ctx, GridState& gs, int src, double chat, double
     p.f_dt = (float)dt;
     p.uhalf = gs.uhalf;
     p.staging = gs.staging;
+    p.wait_polls = ctx->wait_polls;
     if (gs.staging == RHD_STAGING_TMA) p.uh_map = gs.uh_map;
     p.z_chunk = gs.z_chunk;
     p.tx = gs.tx;
@@ -2097,6 +2099,16 @@ rhd_status rhd_get_launch_config(rhd_ctx* ctx, rhd_launch_config* out)
 {
     if (!ctx || !out) return fail(ctx, RHD_ERR_ARG, "ctx and out are required");
     *out = current_config(ctx->grids[0]);
+    return RHD_OK;
+}
+
+rhd_status rhd_set_wait_limit(rhd_ctx* ctx, long long polls)
+{
+    ApiRange range_("rhd_set_wait_limit");
+    if (!ctx) return fail(nullptr, RHD_ERR_ARG, "ctx is NULL");
+    if (polls > 0xffffffffLL) return fail(ctx, RHD_ERR_ARG, "polls must be below 2^32");
+    ctx->wait_polls = polls < 0 ? (1u << 22) : (unsigned)polls;
+    clear_graphs(ctx);  // the captured launches carry the limit
     return RHD_OK;
 }
 

@@ -85,6 +85,7 @@ struct StepParams {
     int tx, ty;                 // tile shape (selects the kernel instantiation)
     int tiles_x, tiles_y;       // tile grid in x, y
     int staging;                // two-pass corrector: 0 per-thread cp.async, 1 one TMA tile copy per plane
+    unsigned wait_polls;        // TMA staging: polls of each plane's mbarrier wait before the tile gives up
     DevStats* stats;
     CUtensorMap uh_map;         // staging 1: tensor map of uhalf as floats {4 (n0+4), n1+4, n2+4}, box {4 (32+4), 8+4, 1}
 };

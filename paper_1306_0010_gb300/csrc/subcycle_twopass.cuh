@@ -428,7 +428,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
                                                float chat, float dt, double chat_d, double dt_d, int x0, int y0,
                                                int z0, int z1, float4* sm,
                                                Counters& cnt, const CUtensorMap* map = nullptr,
-                                               uint64_t* mbar = nullptr)
+                                               uint64_t* mbar = nullptr, unsigned wait_polls = kMaxPolls)
 {
     using G = GeoCorr<TX, TY>;
     const int t = threadIdx.x;
@@ -583,7 +583,7 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
         if constexpr (TMA) {
             // completion of this plane's copy: buffer buf's ((k - z0) >> 1)-th use, phase parity = that & 1
             const unsigned ph = ((k - z0) >> 1) & 1;
-            const bool ok = mbar_wait(mbar + buf, ph, kMaxPolls);
+            const bool ok = mbar_wait(mbar + buf, ph, wait_polls);
             if (__syncthreads_or(!ok)) {
                 timed_out = true;
                 fail_buf = buf;
@@ -721,8 +721,9 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
     if constexpr (TMA) {
         if (timed_out) {
             // a copy did not complete in time: count it, give the one copy in flight (the awaited one; the
-            // next plane's copy is issued only after a successful wait) another bounded wait, and leave the
-            // tile; the host reports RHD_ERR_TIMEOUT
+            // next plane's copy is issued only after a successful wait) another wait with the full bound,
+            // so that it lands before the CTA's shared memory is released, and leave the tile; the host
+            // reports RHD_ERR_TIMEOUT
             if (t == 0) {
                 cnt.timeout += 1;
                 mbar_wait(mbar + fail_buf, fail_ph, kMaxPolls);
@@ -759,7 +760,7 @@ __global__ void __launch_bounds__(TX* TY, RHD_CORR_MIN_BLOCKS) corrector_kernel(
     float4* sm = reinterpret_cast<float4*>(smem_raw);
     if constexpr (TMA) sm = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     corrector_tile<TX, TY, TMA, LIMK>(P.g, P.a, P.uhalf, P.f_chat, P.f_dt, P.chat, P.dt, x0, y0, z0, z1, sm, cnt,
-                                      &P.uh_map, mbar);
+                                      &P.uh_map, mbar, P.wait_polls);
     add_counter(&P.stats->n_fix, cnt.fix);
     add_counter(&P.stats->n_face, cnt.face);
     add_counter(&P.stats->n_theta, cnt.theta);

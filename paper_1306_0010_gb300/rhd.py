@@ -153,6 +153,7 @@ _SIGS = {
     "rhd_gas_step": (ctypes.c_int, [_P, ctypes.c_double]),
     "rhd_gas_correct": (ctypes.c_int, [_P]),
     "rhd_gas_exchange": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double]),
+    "rhd_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
     "rhd_get_gas": (ctypes.c_int, [_P] + [_P] * 5 + [ctypes.c_int]),
     "rhd_get_moments": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
     "rhd_set_conserved": (ctypes.c_int, [_P] + [_P] * 4 + [ctypes.c_int]),
@@ -451,6 +452,11 @@ class Grid:
     def kernel_times(self):
         """{kernel name: {launches, total_ms, alg_bytes_per_launch}} since the timer was enabled or last read."""
         return _kernel_times(self._ctx)
+
+    def set_wait_limit(self, polls):
+        """Poll limit of the two-pass corrector's TMA plane waits (polls < 0: the default; 0: give up at
+        once, for tests of the timeout path)."""
+        _check(self._ctx, lib().rhd_set_wait_limit(self._ctx, int(polls)))
 
     def set_launch_config(self, cfg: dict):
         c = LaunchConfig.from_dict(cfg)

@@ -134,3 +134,46 @@ def test_subnormal_energy_floor_rejected(rhd):
         assert ei.value.status == rhd.ERR_ARG
     g = rhd.Grid(dict(case["desc"], precision="split", E_floor=2e-38))  # normal in FP32: accepted
     g.close()
+
+
+def test_tma_wait_timeout_is_reported_and_the_context_recovers(rhd):
+    """The bounded wait of the two-pass corrector's TMA staging, made to run out on the host's order
+    (rhd_set_wait_limit(0): every plane wait gives up at once; the copy in flight is still awaited with
+    the full bound before each block exits).  The timed-out tiles keep no new values, rhd_get_stats
+    reports RHD_ERR_TIMEOUT with the count, and the same context, with the state reloaded and the
+    default limit, steps to the oracle's result."""
+    import ctypes
+
+    case = wl.parity_case("timeout", (37, 11, 9), bc="outflow", exchange="full", beta_tau=True, n_sub=2, seed=23,
+                          precision="split")
+    g = rhd.Grid(case["desc"])
+    try:
+        g.set_launch_config(dict(variant="twopass", tile=(32, 8), z_chunk=4, staging="tma"))
+    except rhd.RhdError:
+        g.close()
+        pytest.skip("TMA staging unavailable (no tensor-map encoder in the driver)")
+    g.load_case(case)
+    g.set_wait_limit(0)
+    g.radiation_subcycle(1, case["chat"], case["dt"])
+    s = rhd.Stats()
+    status = rhd.lib().rhd_get_stats(g._ctx, ctypes.byref(s))
+    assert status == rhd.ERR_TIMEOUT
+    # one timed-out tile per (tile, z chunk) block: 2 x 2 tiles in x, y and 3 chunks of 4 planes
+    assert s.as_dict()["wait_timeouts"] == 2 * 2 * 3
+    # recovery in the same context: reload the state, restore the limit, clear the counters, step again
+    g.set_wait_limit(-1)
+    g.reset_stats()
+    g.load_case(case)
+    g.radiation_subcycle(case["n_sub"], case["chat"], case["dt"])
+    out = g.get_moments()
+    out["T"] = g.get_gas_state()
+    st = g.get_stats()
+    g.close()
+    assert st["wait_timeouts"] == 0 and st["n_nonfinite"] == 0
+    ref, _ = orc.subcycles(case)
+    sE = float(np.max(np.abs(ref["E"])))
+    tol = split_bound(case, case["n_sub"])
+    assert float(np.max(np.abs(out["E"] - ref["E"]))) <= tol * sE
+    for k in ("Fx", "Fy", "Fz"):
+        assert float(np.max(np.abs(out[k] - ref[k]))) <= tol * case["desc"]["c"] * sE, k
+    assert float(np.max(np.abs(out["T"] - ref["T"]))) <= tol * float(np.max(ref["T"]))
