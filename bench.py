@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (1D wave, 2D source, 3D shell, ensemble)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="throughput", choices=["throughput", "ensemble", "marshak"],
                     help="throughput: one 512^3 grid (the headline); ensemble: 64 independent grids of "
@@ -489,6 +491,127 @@ def time_per_grid(torch, rhd, cases, precision, n_sub, steps, warmup, stream):
     return ms
 
 
+# ----------------------------------------------------------------------------- the other configurations
+
+def _grid_run(torch, rhd, case, n_sub, stream, precision=None, flags=0):
+    """One timed call of n_sub subcycles (after one untimed warm-up call of the same length on a copy of
+    the state); returns (ms, moments, T, stats)."""
+    desc = dict(case["desc"], flags=flags)
+    if precision is not None:
+        desc["precision"] = precision
+    g = rhd.Grid(desc, stream=stream.cuda_stream)
+    g.load_case(case)
+    g.radiation_subcycle(n_sub, case["chat"], case["dt"])  # warm-up (graph capture, module loading)
+    g.load_case(case)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.radiation_subcycle(n_sub, case["chat"], case["dt"])
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = g.get_moments()
+    T = g.get_gas_state()
+    st = g.get_stats(allow_nonfinite=True)
+    g.close()
+    return ms, out, T, st
+
+
+def run_config1(torch, rhd, wl, stream):
+    """1D radiation linear wave (N = 512, periodic, chat = c = 10, CFL 0.4, 1000 subcycles, FP64) at
+    optical depths 0.01, 1, 100 per wavelength: the complex frequency measured from the k = 2 pi Fourier
+    amplitude of dE against the dispersion relation omega^2 + i chat k_F omega - chat^2 k^2 / 3 = 0."""
+    res = {}
+    for tau in (0.01, 1.0, 100.0):
+        case = wl.config1(tau=tau, mode="equilibrium", N=512, n_sub=1000)
+        ms, out, _, st = _grid_run(torch, rhd, case, 1000, stream)
+        N = case["desc"]["n"][0]
+        x = (np.arange(N) + 0.5) / N
+        k = case["k"]
+        a0 = np.mean((case["fields"]["E"][0, 0] - 1.0) * np.exp(-1j * k * x)) * 2
+        a1 = np.mean((out["E"][0, 0] - 1.0) * np.exp(-1j * k * x)) * 2
+        w = 1j * np.log(a1 / a0) / (1000 * case["dt"])
+        w_ex = case["omega"]
+        res[f"tau_{tau:g}"] = {
+            "cell_updates_per_s": N * 1000 / (ms * 1e-3), "ms_per_subcycle": ms / 1000,
+            "omega_measured": [float(w.real), float(w.imag)], "omega_relation": [float(w_ex.real), float(w_ex.imag)],
+            "phase_speed_rel_error": (abs(w.real - w_ex.real) / abs(w_ex.real)) if abs(w_ex.real) > 0 else None,
+            "damping_rel_error": abs(w.imag - w_ex.imag) / abs(w_ex.imag),
+            "n_nonfinite": st["n_nonfinite"]}
+    return {"workload": "1D radiation linear wave, N = 512 periodic, chat = c = 10, CFL 0.4, 1000 subcycles, FP64, "
+                        "EQUILIBRIUM mode, theta = 0.51, dE = 1e-6 cos(2 pi x) on the eigenmode",
+            "note": "latency-bound (512 cells): cell-updates/s only", "runs": res}
+
+
+def run_config2(torch, rhd, wl, stream):
+    """2D concentrated source (256^2 on [-1, 1]^2, outflow, Gaussian j of width 0.05 with L = 1, k_F = 1000
+    inside r < 0.1 and 0.1 outside, chat = c = 1, 2000 subcycles, FP64): the luminosity through circles
+    (the azimuthal mean of F.r_hat times 2 pi r) against L, and realizability fixes."""
+    case = wl.config2(N=256, n_sub=2000)
+    ms, out, _, st = _grid_run(torch, rhd, case, 2000, stream)
+    X, Y, _ = wl.cell_centres(case["desc"], x0=(-1.0, -1.0, 0.0))
+    r = np.sqrt(X ** 2 + Y ** 2)[0]
+    Fr = ((out["Fx"] * X + out["Fy"] * Y) / np.where(r > 0, r, 1))[0]
+    lum = {}
+    for r0 in (0.2, 0.3, 0.45, 0.6, 0.75, 0.9):
+        ring = np.abs(r - r0) < 0.5 * case["desc"]["dx"][0]
+        lum[f"r_{r0:g}"] = float(Fr[ring].mean() * 2 * np.pi * r0 / case["L"])
+    g = np.sqrt(out["Fx"] ** 2 + out["Fy"] ** 2) / case["desc"]["c"]
+    return {"workload": "2D concentrated source, 256^2 on [-1, 1]^2, outflow, Gaussian j (sigma 0.05, L = 1), "
+                        "k_F = 1000 (r < 0.1) / 0.1, chat = c = 1, 2000 subcycles, FP64, EQUILIBRIUM",
+            "cell_updates_per_s": 256 * 256 * 2000 / (ms * 1e-3), "ms_per_subcycle": ms / 2000,
+            "luminosity_over_L": lum, "realizability_fixes": st["n_realizability_fix"],
+            "max_G_over_E": float(np.max(g / out["E"])), "n_nonfinite": st["n_nonfinite"]}
+
+
+def run_config3(torch, rhd, wl, stream, hbm_peak):
+    """3D dusty shell (256^3, outflow, shell rho 100 with tau 10, Gaussian luminosity, FULL exchange, beta
+    tau on, chat = 50 v_max, c = 10 chat), 25 subcycles: split and FP64 throughput, and the split path's
+    normwise L1 / L-infinity errors against the FP64 path (which the parity tests hold to the oracle at
+    1e-12)."""
+    case = wl.config3(N=256, n_sub=25)
+    cells = 256 ** 3
+    out = {}
+    res = {}
+    for prec in ("split", "fp64"):
+        ms, mom, T, st = _grid_run(torch, rhd, case, 25, stream, precision=prec)
+        out[prec] = dict(mom, T=T)
+        res[prec] = {"cell_updates_per_s": cells * 25 / (ms * 1e-3), "ms_per_subcycle": ms / 25,
+                     "n_nonfinite": st["n_nonfinite"], "realizability_fixes": st["n_realizability_fix"]}
+    ref, sp = out["fp64"], out["split"]
+    sE = float(np.max(np.abs(ref["E"])))
+    err = {}
+    for k, sc in (("E", sE), ("Fx", case["desc"]["c"] * sE), ("Fy", case["desc"]["c"] * sE),
+                  ("Fz", case["desc"]["c"] * sE), ("T", float(np.max(np.abs(ref["T"]))))):
+        d = np.abs(sp[k] - ref[k]) / sc
+        err[k] = {"L1": float(np.mean(d)), "Linf": float(np.max(d))}
+    return {"workload": "3D dusty shell, 256^3, outflow, shell 0.3 <= r <= 0.35 with rho 100 (tau 10), Gaussian "
+                        "luminosity (sigma 2 dx, L = 1), FULL exchange, beta tau on, chat = 50 v_max, c = 10 chat",
+            "n_sub": 25, "split": res["split"], "fp64": res["fp64"],
+            "split_speedup": res["split"]["cell_updates_per_s"] / res["fp64"]["cell_updates_per_s"],
+            "split_error_vs_fp64_path": err}
+
+
+def run_config5(torch, rhd, wl, stream, hbm_peak, peak_kind, steps=3, warmup=1):
+    """Batched ensemble: 64 grids of sizes drawn from {32, 48, 64, 96, 128}^3, one persistent launch (pair)
+    per subcycle from a 50-subcycle CUDA graph, split (50 subcycles) and FP64 (10), against per-grid
+    plain launches."""
+    cases = wl.config5(n_grids=64, n_sub=50, precision="split")
+    cells = sum(int(np.prod(c["desc"]["n"])) for c in cases)
+    res = {"workload": "ensemble of 64 independent 3D grids, N from {32, 48, 64, 96, 128}, outflow, Gaussian j "
+                       "with L ~ logU(1e-2, 1e2), uniform tau ~ logU(0.1, 1e3), FULL, theta = 1, c = 10 chat",
+           "cells": cells}
+    for prec, ns in (("split", 50), ("fp64", 10)):
+        ms, chosen, kt, st = time_ensemble(torch, rhd, cases, prec, ns, steps, warmup, stream)
+        base_ms = time_per_grid(torch, rhd, cases, prec, ns, max(1, steps - 1), 1, stream)
+        res[prec] = {"n_sub_per_step": ns, "value": cells * ns * steps / (ms * 1e-3),
+                     "per_grid_plain_launches": cells * ns * max(1, steps - 1) / (base_ms * 1e-3),
+                     "launch": chosen, "roofline": kernel_roofline(kt, hbm_peak, peak_kind),
+                     "n_nonfinite": st["n_nonfinite"]}
+        res[prec]["speedup_vs_per_grid"] = res[prec]["value"] / res[prec]["per_grid_plain_launches"]
+    return res
+
+
 def run_marshak(args):
     """Section 4.2's benchmark: wall-clock time to reach tau on the Marshak wave (FP64 path, the host
     driver setting the boundary from the Su & Olson quadrature before every subcycle, as the paper's
@@ -680,6 +803,17 @@ def main():
     value = whole_job_rate(cells, args.n_sub, args.steps, ws, total_ms)
     sub_ms = total_ms / (args.steps * args.n_sub)
     roofline = kernel_roofline(kt, hbm_peak, peak_kind)
+    # the dominant kernel (the corrector, which completes every cell-update) against the method's own
+    # bytes per cell-update (B_alg of the split path: U^m read, U^{m+1} written, T read and written, the
+    # FP32 gas read) times the cells of one launch; the kernel's own design bytes (with U^{m+1/2} and the
+    # FP32 mirror the two-pass design adds) are reported beside it
+    design = roofline["alg_bytes_per_launch"]
+    roofline["alg_bytes_per_launch"] = float(B_ALG["split"] * cells)
+    roofline["achieved"] = roofline["alg_bytes_per_launch"] / (roofline["launch_ms"] * 1e-3) / 1e9
+    roofline["frac"] = roofline["achieved"] / hbm_peak
+    roofline["bytes_per_cell_update"] = B_ALG["split"]
+    roofline["design_bytes_per_launch"] = design
+    roofline["design_frac"] = design / (roofline["launch_ms"] * 1e-3) / 1e9 / hbm_peak
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_path):
         trj = json.load(open(traffic_path))
@@ -691,6 +825,12 @@ def main():
         if (tr and tr.get("N") == args.N and same_kernel(tr.get("launch", ""), launch_key(launch))
                 and trj.get("source_sha256") == kernel_source_hash()):
             roofline["traffic"] = tr["bytes_per_launch"]
+            roofline["traffic_over_alg"] = tr["bytes_per_launch"] / roofline["alg_bytes_per_launch"]
+            tp = trj.get("twopass_predictor_split")
+            if tp and tp.get("N") == args.N:
+                # the whole subcycle's DRAM traffic over the method's bytes (re-reads and the two-pass extras)
+                roofline["subcycle_traffic_over_alg"] = (tr["bytes_per_launch"] + tp["bytes_per_launch"]) / (
+                    B_ALG["split"] * cells)
     # the whole subcycle against the method's own bytes per cell-update (U^m, gas, T in; U^{m+1}, T out)
     sub_achieved = B_ALG["split"] * cells / (sub_ms * 1e-3) / 1e9
     subcycle_roofline = {"bound": "hbm", "achieved": sub_achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -718,6 +858,12 @@ def main():
     cpu = None
     if not args.no_cpu and rank == 0:
         cpu = cpu_baseline(case, args.cpu_seconds)
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = {"config1_linear_wave": run_config1(torch, rhd, wl, stream),
+                   "config2_source_2d": run_config2(torch, rhd, wl, stream),
+                   "config3_shell": run_config3(torch, rhd, wl, stream, hbm_peak),
+                   "config5_ensemble": run_config5(torch, rhd, wl, stream, hbm_peak, peak_kind)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -730,7 +876,7 @@ def main():
                 "gas_step": rsla.pop("gas_step", None) if rsla else None,
                 "stats": {k: st[k] for k in ("n_realizability_fix", "n_face_fallback", "n_theta_fallback",
                                              "n_nonfinite", "newton_iter_max")},
-                "per_step_ms": per_step}
+                "per_step_ms": per_step, "configs": configs}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -142,9 +142,11 @@ def test_fp64_conservation_on_gpu(rhd):
     assert s1["n_realizability_fix"] == 0
 
 
-def test_config1_linear_wave_fp64_full_run(rhd):
-    """Configuration 1 (1D, N = 512, tau = 1, chat = 10, 1000 subcycles) against the oracle."""
-    case = wl.config1(tau=1.0, mode="equilibrium", N=512, n_sub=1000)
+@pytest.mark.parametrize("tau", [0.01, 1.0, 100.0])
+def test_config1_linear_wave_fp64_full_run(rhd, tau):
+    """Configuration 1 (1D, N = 512, chat = 10, 1000 subcycles) at the three optical depths per
+    wavelength, against the oracle."""
+    case = wl.config1(tau=tau, mode="equilibrium", N=512, n_sub=1000)
     out, _ = run_gpu(rhd, case)
     ref, _ = orc.subcycles(case)
     e = errors(out, ref, case["desc"])
@@ -298,6 +300,48 @@ def test_config4_full_size_sampled(rhd, config4_full, precision, flags, launch):
         for k in ("Fx", "Fy", "Fz"):
             assert np.max(np.abs(out[k][sl] - ref[k][sl])) <= tol * c * sE, (k, lo)
         assert np.max(np.abs(out["T"][sl] - ref["T"][sl])) <= tol * float(np.max(ref["T"][sl]))
+
+
+def oracle_region(case, lo, hi, n_sub):
+    """The oracle's state after n_sub subcycles on the box [lo, hi) of a periodic grid: the box grown by
+    3 cells per subcycle on every side (the reach of one VL subcycle: the corrector's U^{m+1/2} at +-2,
+    which needs U^m at +-3), cut out with wrapped indices and run with outflow faces, whose influence
+    does not reach the box in n_sub subcycles."""
+    N = case["desc"]["n"]
+    h = 3 * n_sub
+    ix = [np.arange(lo[d] - h, hi[d] + h) % N[d] for d in range(3)]
+    sel = np.ix_(ix[2], ix[1], ix[0])
+    fields = {k: (None if v is None else np.ascontiguousarray(v[sel])) for k, v in case["fields"].items()}
+    desc = dict(case["desc"], n=tuple(hi[d] - lo[d] + 2 * h for d in range(3)), bc_lo=["outflow"] * 3,
+                bc_hi=["outflow"] * 3)
+    out, _ = orc.subcycles(dict(case, desc=desc, fields=fields), n_sub=n_sub)
+    inner = tuple(slice(h, h + hi[d] - lo[d]) for d in (2, 1, 0))
+    return {k: out[k][inner] for k in ("E", "Fx", "Fy", "Fz", "T")}
+
+
+@pytest.mark.parametrize("precision,flags,launch", [("fp64", 0, None), ("split", 0, BENCH_LAUNCH)],
+                         ids=["fp64", "split"])
+def test_config4_full_size_ten_subcycles_sampled(rhd, config4_full, precision, flags, launch):
+    """The 512^3 throughput configuration over 10 subcycles in the launch configuration the benchmark
+    times (graph replay of the two-pass pair for the split path), so that a drift that grows over
+    subcycles (the FP32 mirror, the split transport) is checked at full size; sampled 6^3 boxes (one at
+    the periodic corner) against the oracle's run on each box grown by its 30-cell reach."""
+    n_sub = 10
+    case = dict(config4_full)
+    case["desc"] = dict(case["desc"], precision=precision, flags=flags)
+    tol = FP64_TOL if precision == "fp64" else split_bound(case, n_sub)
+    out, st = run_gpu(rhd, case, n_sub=n_sub, launch=launch)
+    assert st["n_nonfinite"] == 0
+    c = case["desc"]["c"]
+    for lo in ((0, 0, 0), (506, 506, 506), (250, 31, 400)):
+        hi = tuple(v + 6 for v in lo)
+        ref = oracle_region(case, lo, hi, n_sub)
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        sE = float(np.max(np.abs(ref["E"])))
+        assert np.max(np.abs(out["E"][sl] - ref["E"])) <= tol * sE, lo
+        for k in ("Fx", "Fy", "Fz"):
+            assert np.max(np.abs(out[k][sl] - ref[k])) <= tol * c * sE, (k, lo)
+        assert np.max(np.abs(out["T"][sl] - ref["T"])) <= tol * float(np.max(ref["T"])), lo
 
 
 # ----------------------------------------------------------------------------- ensemble
