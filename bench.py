@@ -178,8 +178,8 @@ def run_reference(args):
 
 
 # the sources the split path's kernels (predictor, corrector) are compiled from
-SPLIT_KERNEL_SOURCES = ("fp_convert.cuh", "k_split.cu", "rhd_internal.h", "subcycle.cuh", "subcycle_pair.cuh",
-                        "subcycle_twopass.cuh")
+SPLIT_KERNEL_SOURCES = ("dfloat.cuh", "fp_convert.cuh", "k_split.cu", "rhd_internal.h", "subcycle.cuh",
+                        "subcycle_pair.cuh", "subcycle_twopass.cuh")
 
 
 def kernel_source_hash():
@@ -206,6 +206,8 @@ def record_traffic(csv_path, measured_N, target_N, launch_spec):
 
     names = {"predictor_kernel": "twopass_predictor_split", "corrector_kernel": "twopass_corrector_split"}
     rows = list(csv.reader(open(csv_path)))
+    first = next(i for i, r in enumerate(rows) if "Kernel Name" in r)  # ncu's own log lines come first
+    rows = rows[first:]
     hdr, units = rows[0], rows[1]
     scale = (target_N / measured_N) ** 3
     out = {"note": f"dram__bytes_read.sum + dram__bytes_write.sum per launch, ncu at {measured_N}^3, scaled to "

@@ -151,9 +151,12 @@ typedef struct {
     int64_t n_realizability_fix; /* cells rescaled onto |F| = cE (both stages, interior cells) */
     int64_t n_face_fallback;     /* (cell, direction) pairs whose limited slope was zeroed */
     int64_t n_theta_fallback;    /* energy-exchange solves redone with theta = 1 (no feasible root) */
-    int64_t n_newton_fallback;   /* energy-exchange solves finished by bisection */
-    int64_t n_nonfinite;         /* interior cells that produced a non-finite value */
-    int32_t newton_iter_max;     /* largest Newton iteration count of one solve */
+    int64_t n_newton_fallback;   /* energy-exchange solves finished by bisection (FP64 path) or by FP64
+                                    Newton steps (split path) */
+    int64_t n_nonfinite;         /* interior cells that produced a non-finite value (split grids: also a
+                                    state beyond the FP32 range of their transport) */
+    int32_t newton_iter_max;     /* largest Newton iteration count of one solve (split path: the FP32
+                                    iterations plus the double-float step) */
     int32_t wait_timeouts;       /* bounded device-side waits that ran out; nonzero makes rhd_get_stats
                                     return RHD_ERR_TIMEOUT (the affected tiles were not updated) */
     double sum_E;                /* sum of E over the interior (current state), FP64, fixed order */

@@ -107,6 +107,16 @@ __device__ __forceinline__ dfl d2df(double x)
     const float h = d2f_rn(x);
     return {h, d2f_rn(x - f2d_exact(h))};
 }
+// x as an unnormalised double-float for the FP32 normal range, cheaply: hi is x truncated toward zero
+// (its FP64 value is x with the 29 low mantissa bits cleared, one logic operation), lo = x - hi rounded
+// to nearest (the subtraction is exact); relative error below 2^-47 (|lo| < ulp(hi)).  Values below the
+// FP32 normal range become (0, 0).  The callers pass it to a double-float sum, which renormalises.
+__device__ __forceinline__ dfl d2df_fast(double x)
+{
+    const float h = d2f_trunc(x);
+    const double h64 = h != 0.0f ? __hiloint2double(__double2hiint(x), __double2loint(x) & (int)0xe0000000) : 0.0;
+    return {h, d2f_rn(x - h64)};
+}
 // a double-float of a host-side FP64 constant (per thread, outside the loops)
 __device__ __forceinline__ dfl dconst(double x) { return d2df(x); }
 // hi + lo in FP64 (one FP64 addition)

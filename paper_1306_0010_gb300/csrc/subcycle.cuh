@@ -843,10 +843,10 @@ __device__ __forceinline__ void split_stiff(const GridParams& g, const GridArray
         return;
     }
     // FULL.  E_in = U0 + d, floored (transport is not positivity preserving)
-    dfl Ein = dadd(d2df(U0[0]), d[0]);
+    dfl Ein = dadd(d2df_fast(U0[0]), d[0]);
     const bool floored = Ein.hi < k.Efl.hi || (Ein.hi == k.Efl.hi && Ein.lo < k.Efl.lo);
     if (floored) Ein = k.Efl;
-    const dfl Td = d2df(T);
+    const dfl Td = d2df_fast(T);
     ExchangeOut o;
     float qv;
     const float del = exchange_delta_fp32(g, chat, dt, rho, gc.kP, Ein.hi, Td.hi, o, qv);

@@ -703,8 +703,10 @@ __device__ __forceinline__ void corrector_tile(const GridParams& g, const GridAr
                 cnt.fix += fx;
                 m = make_float4(d2f_trunc(Un[0]), d2f_trunc(Un[1]), d2f_trunc(Un[2]), d2f_trunc(Un[3]));
             }
-            const bool bad = !(finite_d(Un[0]) && finite_d(Un[1]) && finite_d(Un[2]) && finite_d(Un[3]) &&
-                               (!full || finite_d(Tn)));
+            // non-finite, or beyond the FP32 range the split transport works in (the truncation maps both
+            // to infinity): checked on the mirror's FP32 values
+            const bool bad = !(isfinite(m.x) && isfinite(m.y) && isfinite(m.z) && isfinite(m.w)) ||
+                             (full && !finite_d(Tn));
             cnt.nonfinite += bad;
             a.Eo[lo] = Un[0];
             a.Go[0][lo] = Un[1];
