@@ -14,7 +14,7 @@ static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
     cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(p.tiles_x * p.tiles_y), DIM == 3 ? (unsigned)((p.g.n[2] + p.z_chunk - 1) / p.z_chunk) : 1u);
-    k<<<grid, TX * TY, smem, s>>>(p);
+    k<<<grid, Geo<TX, TY, DIM>::NT, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -44,7 +44,7 @@ static int ens_occupancy()
 void tile_shape(int precision, int nact, int* tx, int* ty)
 {
     if (nact == 1) {
-        *tx = 128;
+        *tx = 122;  // 128 threads: the tile and its 3-cell halo on each side
         *ty = 1;
     } else if (precision == 0) {
         *tx = 16;
@@ -68,7 +68,7 @@ bool tile_supported(int precision, int nact, int tx, int ty)
 cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s)
 {
     switch (p.g.nact) {
-    case 1: return launch_tile_kernel<double, 128, 1, 1, false>(p, s);
+    case 1: return launch_tile_kernel<double, 122, 1, 1, false>(p, s);
     case 2: return launch_tile_kernel<double, 16, 8, 2, false>(p, s);
     default: return launch_tile_kernel<double, 16, 8, 3, false>(p, s);
     }

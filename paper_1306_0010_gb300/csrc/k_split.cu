@@ -14,7 +14,7 @@ static cudaError_t launch_tile_kernel(const StepParams& p, cudaStream_t s)
     cudaError_t e = smem_once.set(k, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(p.tiles_x * p.tiles_y), DIM == 3 ? (unsigned)((p.g.n[2] + p.z_chunk - 1) / p.z_chunk) : 1u);
-    k<<<grid, TX * TY, smem, s>>>(p);
+    k<<<grid, Geo<TX, TY, DIM>::NT, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -45,7 +45,7 @@ static int ens_occupancy()
 cudaError_t launch_subcycle_split(const StepParams& p, cudaStream_t s)
 {
     switch (p.g.nact) {
-    case 1: return launch_tile_kernel<float, 128, 1, 1, true>(p, s);
+    case 1: return launch_tile_kernel<float, 122, 1, 1, true>(p, s);
     case 2: return launch_tile_kernel<float, 32, 8, 2, true>(p, s);
     default:
         if (p.ty == 16) return launch_tile_kernel<float, 32, 16, 3, true>(p, s);

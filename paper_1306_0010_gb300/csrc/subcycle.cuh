@@ -545,13 +545,15 @@ __device__ __forceinline__ void exchange_linear_fp64(const GridParams& g, double
                                                      double& T)
 {
     const double eps = g.linear_eps, c = g.c;
-    double v = g.a_rad * T * T * T * T;
+    const double T2 = T * T;
+    double v = g.a_rad * T2 * T2;
     const double dtau = eps * c * kP * dt;
-    const double dv = -(v - E) * dtau / (1.0 + g.theta_E * (1.0 + chat / (eps * c)) * dtau);
-    E = E + (-(chat / (eps * c)) * dv);
+    const double r = chat * g.inv_eps_c;  // chat / (eps c), 1/(eps c) from the host
+    const double dv = -(v - E) * dtau / (1.0 + g.theta_E * (1.0 + r) * dtau);
+    E = E + (-r * dv);
     v = v + dv;
     if (v < 0.0) v = 0.0;
-    T = sqrt(sqrt(v / g.a_rad));
+    T = sqrt(sqrt(v * g.inv_a_rad));
 }
 
 // FP32 Newton for delta with the same iteration, which also stops once a step is small enough that
@@ -630,7 +632,12 @@ __device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float 
 // ------------------------------------------------------------------------------------------------
 template <int TX, int TY, int DIM>
 struct Geo {
-    static constexpr int NT = TX * TY;
+    // threads of the CTA: one per tile cell in 2D and 3D; in 1D one per cell of the widest per-phase set
+    // (the 3-cell halo on each side: TX + 6 predictor cells, TX + 5 faces), so no phase takes a second
+    // round.  A 1D subcycle on a short grid is bound by its longest dependent chain, and each FP64
+    // instruction occupies a warp's pipe for as long with 2 active lanes as with 32, so a second round
+    // for the halo would nearly double the kernel's time.
+    static constexpr int NT = DIM == 1 ? ((TX + 6 + 31) / 32) * 32 : TX * TY;
     static constexpr int HY = DIM >= 2 ? 1 : 0;
     static constexpr int W3 = TX + 6, H3 = TY + 6 * HY;
     static constexpr int W2 = TX + 4, H2 = TY + 4 * HY;
@@ -1434,7 +1441,8 @@ constexpr size_t tile_smem_bytes()
 }
 
 template <typename R, int TX, int TY, int DIM, bool SPLIT>
-__global__ void __launch_bounds__(TX* TY, (TX * TY > 256) ? 1 : 2) subcycle_kernel(const __grid_constant__ StepParams P)
+__global__ void __launch_bounds__(Geo<TX, TY, DIM>::NT, (Geo<TX, TY, DIM>::NT > 256) ? 1 : 2)
+    subcycle_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);

@@ -203,6 +203,53 @@ def stiff_case(name, n, uniform=False, exchange="full", K=2.0e4, x_abs=20.0, rho
     return {"name": name, "desc": desc, "fields": fields, "chat": chat, "dt": dt, "n_sub": n_sub}
 
 
+# cgs constants of the physical-units cases
+A_RAD_CGS = 7.5657e-15        # erg cm^-3 K^-4
+C_CGS = 2.99792458e10         # cm s^-1
+MU_OVER_KB_CGS = 0.6 * 1.6726e-24 / 1.380649e-16  # mean mass per particle over k_B (mu = 0.6), g K erg^-1
+
+# (density g cm^-3, gas temperature K, cell size cm, opacity cm^2 g^-1, c / chat, velocity dispersion cm s^-1)
+PHYSICAL_REGIMES = {
+    "protostellar_disk": (1e-10, 300.0, 1.496e13 / 8, 1.0, 100.0, 1e5),
+    "stellar_envelope": (1e-7, 1e5, 7e9, 0.4, 30.0, 1e6),
+    "molecular_cloud": (1e-22, 20.0, 3.086e17, 10.0, 1000.0, 1e5),
+}
+
+
+def physical_units_case(name, n, regime, precision="split", n_sub=4, seed=0, fmax=0.6):
+    """A state in cgs units (a_R, c and mu/k_B of an ionised gas with mu = 0.6), for the ranges of the
+    split path's FP32 arithmetic: rho = rho0 exp(N(0, 0.5^2)), T = T0 exp(N(0, 0.2^2)), radiation
+    temperature T U(0.6, 1.3) (E = a_R T_rad^4), F = c E f n with f ~ U(0, fmax), v ~ N(0, sigma_v^2) per
+    component, the opacity law k = kappa rho, FULL exchange with beta tau terms, chat = c / (c / chat)
+    and dt at CFL 0.4.  Density and velocity are rounded to FP32 (the split path's copies of them are
+    then exact).  The regimes span optically thick and stiff (disk: chat k dt ~ 75; stellar envelope ~
+    110) to optically thin (molecular cloud, chat k dt ~ 1e-4), with E from 1e-9 to 1e6 erg cm^-3."""
+    rho0, T0, dx0, kappa, c_over_chat, sig_v = PHYSICAL_REGIMES[regime]
+    g = rng(7000 + seed)
+    n = tuple(n)
+    dx = tuple(dx0 for _ in n)
+    desc = base_desc(n, dx, c=C_CGS, a_rad=A_RAD_CGS, mu_over_kB=MU_OVER_KB_CGS, exchange="full",
+                     beta_tau=True, kappa_P=kappa, kappa_F=kappa, kappa_rho_pow=1, E_floor=1e-30,
+                     precision=precision)
+    chat = C_CGS / c_over_chat
+    shp = _shape(desc)
+    rho = (rho0 * np.exp(g.normal(0.0, 0.5, size=shp))).astype(np.float32).astype(np.float64)
+    T = T0 * np.exp(g.normal(0.0, 0.2, size=shp))
+    E = A_RAD_CGS * (T * g.uniform(0.6, 1.3, size=shp)) ** 4
+    f = g.uniform(0.0, fmax, size=shp)
+    dirs = list(random_directions(g, shp))
+    act = [n[d] > 1 for d in range(3)]
+    comps = [dirs[d] if act[d] else np.zeros(shp) for d in range(3)]
+    norm = np.sqrt(sum(cc ** 2 for cc in comps))
+    norm = np.where(norm > 0, norm, 1.0)
+    fields = {"E": E, "T": T, "rho": rho, "kP": None, "kF": None, "j": None}
+    for d, k in enumerate(("Fx", "Fy", "Fz")):
+        fields[k] = C_CGS * E * f * comps[d] / norm
+    for k in ("vx", "vy", "vz"):
+        fields[k] = g.normal(0.0, sig_v, size=shp).astype(np.float32).astype(np.float64)
+    return {"name": name, "desc": desc, "fields": fields, "chat": chat, "dt": cfl_dt(desc, chat), "n_sub": n_sub}
+
+
 def gas_case(name, n, bc="periodic", limiter="minmod", beta_tau=True, kappa=2.0, kappa_rho_pow=1, kF_array=False,
              seed=0, precision="fp64", dirichlet=None, exchange="full", n_sub=4, with_v=True, c=10.0, gamma=5.0 / 3.0):
     """A gas-step case: the random gas and radiation of parity_case (rho = exp(N(0, 0.5^2)), T = exp(N(0,

@@ -74,6 +74,10 @@ FP64_CASES = [
          dirichlet=([[1.0, 5.0, 3.0, 0.0], [0.0] * 4, [0.0] * 4], [[0.0] * 4] * 3)),
     dict(name="1d_periodic_absorb", n=(200, 1, 1), bc="periodic", exchange="absorb", with_j=True),
     dict(name="1d_reflect_full", n=(130, 1, 1), bc="reflect", exchange="full", beta_tau=True),
+    # 1D tiles are 122 cells: three full tiles and a one-cell tail, Dirichlet on the low face
+    dict(name="1d_three_tiles_one_cell_tail", n=(367, 1, 1), exchange="full", limiter="mc",
+         bc=(["dirichlet", "periodic", "periodic"], ["outflow", "periodic", "periodic"]),
+         dirichlet=([[1.0, 0.6, 0.0, 0.0], [0.0] * 4, [0.0] * 4], [[0.0] * 4] * 3)),
 ]
 
 
@@ -187,6 +191,23 @@ def test_split_error_bound_small(rhd, kw, variant, flags):
     n = kw.pop("n")
     case = wl.parity_case(name, n, n_sub=4, seed=zlib.crc32(name.encode()) % 1000, precision="split", **kw)
     out, st = run_gpu(rhd, case, desc_over={"flags": flags})
+    ref, _ = orc.subcycles(case)
+    e = errors(out, ref, case["desc"])
+    assert max(e.values()) <= split_bound(case, 4), e
+    assert st["n_nonfinite"] == 0
+
+
+ONE_TWO_D = [c for c in FP64_CASES if c["n"][2] == 1]
+
+
+@pytest.mark.parametrize("kw", ONE_TWO_D, ids=[c["name"] for c in ONE_TWO_D])
+def test_split_error_bound_1d_2d(rhd, kw):
+    """1D and 2D split grids (always the fused kernel; 1D tiles of 122 cells on 128 threads)."""
+    kw = dict(kw)
+    name = kw.pop("name")
+    n = kw.pop("n")
+    case = wl.parity_case(name, n, n_sub=4, seed=zlib.crc32(name.encode()) % 1000, precision="split", **kw)
+    out, st = run_gpu(rhd, case)
     ref, _ = orc.subcycles(case)
     e = errors(out, ref, case["desc"])
     assert max(e.values()) <= split_bound(case, 4), e
