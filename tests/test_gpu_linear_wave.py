@@ -52,11 +52,19 @@ def gpu_wave(rhd, N, P0, C, Ch, tau, periods=1.0):
     return Z, dsp.measured_Z(times, np.array(rows))
 
 
-def test_linear_wave_equals_the_oracle_run(rhd):
+# (P_0, Chat, tau) points of the paper's sweep (C = 1e4): the gas-energy-dominated case with strong
+# energy exchange (P_0 C tau = 10), both reduced speeds of light, the radiation-pressure-dominated
+# cases P_0 = 1 and 10, an optically thin and an optically thick wave
+SWEEP = [(1e-3, 10.0, 1.0), (1e-3, 100.0, 1.0), (1.0, 10.0, 1.0), (10.0, 10.0, 1.0), (1e-3, 10.0, 0.1),
+         (1e-3, 10.0, 100.0)]
+
+
+@pytest.mark.parametrize("P0,Ch,tau", SWEEP, ids=[f"P{p:g}_Ch{c:g}_tau{t:g}" for p, c, t in SWEEP])
+def test_linear_wave_equals_the_oracle_run(rhd, P0, Ch, tau):
     from test_dispersion import oracle_wave
 
-    Z, Zg = gpu_wave(rhd, 64, 1e-3, 1e4, 10.0, 1.0)
-    _, Zo = oracle_wave(64, 1e-3, 1e4, 10.0, 1.0)
+    Z, Zg = gpu_wave(rhd, 64, P0, 1e4, Ch, tau)
+    _, Zo = oracle_wave(64, P0, 1e4, Ch, tau)
     assert abs(Zg - Zo) <= 1e-6, (Zg, Zo)
 
 
@@ -64,3 +72,14 @@ def test_linear_wave_at_the_papers_resolution(rhd):
     Z, Zg = gpu_wave(rhd, 512, 1e-3, 1e4, 10.0, 1.0)
     assert abs(Zg.real - Z.real) <= 1e-4 * Z.real, (Z, Zg)
     assert abs(Zg.imag - Z.imag) <= 1e-2 * abs(Z.imag), (Z, Zg)
+
+
+@pytest.mark.parametrize("P0", [1.0, 10.0])
+def test_linear_wave_phase_speed_radiation_pressure_dominated(rhd, P0):
+    """P_0 = 1 and 10 (Chat = 10, tau = 1): the phase speed at 512 cells within 1e-4 of the relation (the
+    oracle's run at 64 cells is off by 1.1e-4, converging at first order).  The damping rate is not
+    compared: the relation's is about 1e-4 of the real part, below the first-order scheme's own
+    dissipation at this resolution (about 5e-4)."""
+    Z, Zg = gpu_wave(rhd, 512, P0, 1e4, 10.0, 1.0)
+    assert abs(Zg.real - Z.real) <= 1e-4 * Z.real, (Z, Zg)
+    assert Zg.imag < 0.0  # damped
