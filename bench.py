@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--traffic-from", default=None,
                     help="write profiles/traffic.json from this ncu raw CSV (measured at --N, scaled to 512^3; "
                          "--launch names the configuration) and exit")
+    ap.add_argument("--fp64-ops-from", default=None,
+                    help="write profiles/fp64_ops.json (FP64 instructions per cell-update of the FP64 fused "
+                         "kernel) from this ncu raw CSV of one launch at --N and exit")
     ap.add_argument("--ens-n-sub", type=int, default=50, help="subcycles per step of the ensemble workload")
     return ap.parse_args()
 
@@ -185,15 +188,15 @@ SPLIT_KERNEL_SOURCES = ("dfloat.cuh", "fp_convert.cuh", "k_split.cu", "rhd_inter
                         "subcycle_pair.cuh", "subcycle_twopass.cuh")
 
 
-def kernel_source_hash():
-    """SHA-256 over the code of the split path's kernels (comments and whitespace removed): ncu
-    traffic recorded for other kernel code is stale."""
+def kernel_source_hash(sources=SPLIT_KERNEL_SOURCES):
+    """SHA-256 over the code of a path's kernels (comments and whitespace removed): ncu figures
+    recorded for other kernel code are stale."""
     import hashlib
     import re
 
     d = os.path.join(ROOT, "paper_1306_0010_gb300", "csrc")
     h = hashlib.sha256()
-    for name in SPLIT_KERNEL_SOURCES:
+    for name in sources:
         text = open(os.path.join(d, name), encoding="utf-8").read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)
@@ -232,6 +235,51 @@ def record_traffic(csv_path, measured_N, target_N, launch_spec):
         json.dump(out, f, indent=1)
         f.write("\n")
     print(json.dumps(out, indent=1))
+
+
+# the sources the FP64 fused kernel is compiled from
+FP64_KERNEL_SOURCES = ("dfloat.cuh", "fp_convert.cuh", "k_fp64.cu", "rhd_internal.h", "subcycle.cuh",
+                       "subcycle_pair.cuh", "subcycle_twopass.cuh")
+# FP64 issue peak from unit counts and the maximum SM clock: 152 SMs x 2 FP64 operations per cycle (the
+# ncu peak of sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle) x 2.07 GHz
+FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
+
+
+def record_fp64_ops(csv_path, N):
+    """Write profiles/fp64_ops.json from an `ncu --page raw --csv` export of one FP64 fused-kernel launch
+    over N^3 cells: thread-level dadd + dfma + dmul instructions per cell-update."""
+    import csv
+
+    rows = list(csv.reader(open(csv_path)))
+    first = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr, rows = rows[first], rows[first + 2:]
+    r = next(r for r in rows if "subcycle_kernel<double" in r[hdr.index("Kernel Name")])
+    ops = {}
+    for op in ("dadd", "dfma", "dmul"):
+        ops[op] = float(r[hdr.index(f"smsp__sass_thread_inst_executed_op_{op}_pred_on.sum")].replace(",", "")) / N ** 3
+    out = {"note": f"FP64 thread instructions per cell-update of the FP64 fused kernel, ncu at {N}^3 (one launch)",
+           "source_sha256": kernel_source_hash(FP64_KERNEL_SOURCES), "N": N, "per_cell_update": ops,
+           "fp64_ops_per_cell_update": sum(ops.values())}
+    with open(os.path.join(ROOT, "profiles", "fp64_ops.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out, indent=1))
+
+
+def fp64_pipe_roofline(rate):
+    """The FP64 path against the FP64 issue peak: its kernel's FP64 instructions per cell-update (ncu,
+    profiles/fp64_ops.json, dropped when the kernel's sources have changed since) times the rate."""
+    path = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_sha256") != kernel_source_hash(FP64_KERNEL_SOURCES):
+        return None
+    ops = float(rec["fp64_ops_per_cell_update"])
+    achieved = ops * rate / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TOPS, "unit": "T FP64 instr/s",
+            "frac": achieved / FP64_PEAK_TOPS, "fp64_ops_per_cell_update": ops,
+            "peak_kind": "derived: 152 SMs x 2 FP64 operations per cycle x 2.07 GHz"}
 
 
 def launch_key(launch):
@@ -808,6 +856,8 @@ def main():
     args = parse()
     if args.traffic_from:
         return record_traffic(args.traffic_from, args.N, 512, args.launch)
+    if args.fp64_ops_from:
+        return record_fp64_ops(args.fp64_ops_from, args.N)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "ensemble":
@@ -895,7 +945,8 @@ def main():
         f_launch = fp_ms / (fn * args.fp64_n_sub)
         extra["fp64_path"] = {"value": fv, "unit": UNIT, "n_sub_per_step": args.fp64_n_sub,
                               "launch_ms": f_launch, "split_speedup": value / fv, "launch": flaunch,
-                              "roofline": kernel_roofline(fkt, hbm_peak, peak_kind)}
+                              "roofline": kernel_roofline(fkt, hbm_peak, peak_kind),
+                              "fp64_pipe_roofline": fp64_pipe_roofline(fv / ws)}
     e2e = None
     if not args.no_e2e and rank == 0:
         el, h2d, d2h = time_e2e(torch, rhd, case, "split", args.n_sub, max(2, args.steps // 2), 1, args.launch)
