@@ -449,36 +449,49 @@ def kernel_roofline(kt, peak, peak_kind):
 
 def time_e2e(torch, rhd, case, precision, n_sub, steps, warmup, launch_spec="auto"):
     """Same metric through the public API with host (pinned) buffers: per step, H2D of the moments and
-    gas state, the subcycles, D2H of the moments and temperature.  The launch configuration is the
-    autotuner's (RHD_FLAG_AUTOTUNE: reused from the device-resident run's tuning of the same shape)
-    or the one given."""
+    gas state, the subcycles, D2H of the moments and temperature.  Two grids on two streams take the
+    steps in turn, so one step's copies run while the other grid computes (the upload and the
+    subcycles are asynchronous on a grid's stream; reading the results waits for that grid only).  The
+    launch configuration is the autotuner's (RHD_FLAG_AUTOTUNE: reused from the device-resident run's
+    tuning of the same shape) or the one given."""
     desc = dict(case["desc"], precision=precision, flags=rhd.FLAG_AUTOTUNE if launch_spec == "auto" else 0)
-    g = rhd.Grid(desc)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    grids = [rhd.Grid(desc, stream=st.cuda_stream) for st in streams]
     if launch_spec != "auto":
-        g.set_launch_config(parse_launch(launch_spec))
+        for g in grids:
+            g.set_launch_config(parse_launch(launch_spec))
     f = case["fields"]
     pin = {k: (None if f[k] is None else torch.from_numpy(f[k]).pin_memory()) for k in f}
-    outs = [torch.empty(f["E"].shape, dtype=torch.float64).pin_memory() for _ in range(5)]
+    outs = [[torch.empty(f["E"].shape, dtype=torch.float64).pin_memory() for _ in range(5)] for _ in grids]
     h2d = sum(v.numel() * 8 for k, v in pin.items() if v is not None and k in
               ("E", "Fx", "Fy", "Fz", "rho", "T", "vx", "vy", "vz", "kP", "kF", "j"))
-    d2h = sum(o.numel() * 8 for o in outs)
+    d2h = sum(o.numel() * 8 for o in outs[0])
 
-    def step():
+    def issue(s):  # step s: its inputs in, its subcycles (asynchronous on its grid's stream)
+        g = grids[s % 2]
         g.set_gas_state(pin["rho"], pin["T"], pin["vx"], pin["vy"], pin["vz"], pin["kP"], pin["kF"], pin["j"])
         g.set_moments(pin["E"], pin["Fx"], pin["Fy"], pin["Fz"])
         g.radiation_subcycle(n_sub, case["chat"], case["dt"])
-        g.get_moments(outs[0], outs[1], outs[2], outs[3])
-        g.get_gas_state(outs[4])
 
-    for _ in range(warmup):
-        step()
+    def read(s):  # step s: its results out (waits for its grid's stream)
+        g, o = grids[s % 2], outs[s % 2]
+        g.get_moments(o[0], o[1], o[2], o[3])
+        g.get_gas_state(o[4])
+
+    for s in range(max(warmup, 2)):  # both grids warm (module loading, tuning, graph capture)
+        issue(s)
+        read(s)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        step()
+    issue(0)
+    for s in range(steps):
+        if s + 1 < steps:
+            issue(s + 1)
+        read(s)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    g.close()
+    for g in grids:
+        g.close()
     return el, h2d, d2h
 
 
@@ -949,10 +962,12 @@ def main():
                               "fp64_pipe_roofline": fp64_pipe_roofline(fv / ws)}
     e2e = None
     if not args.no_e2e and rank == 0:
-        el, h2d, d2h = time_e2e(torch, rhd, case, "split", args.n_sub, max(2, args.steps // 2), 1, args.launch)
-        n_e = max(2, args.steps // 2)
+        n_e = max(4, args.steps)
+        el, h2d, d2h = time_e2e(torch, rhd, case, "split", args.n_sub, n_e, 1, args.launch)
         e2e = {"value": cells * args.n_sub * n_e / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h, "steps": n_e,
+               "pipelining": "two grids on two streams take the steps in turn: one step's copies overlap "
+                             "the other grid's subcycles"}
     cpu = None
     if not args.no_cpu and rank == 0:
         cpu = cpu_baseline(case, args.cpu_seconds)
