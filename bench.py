@@ -342,7 +342,7 @@ def time_rsla(torch, g, case, stream, hbm_peak, reps=5):
     return out
 
 
-def time_gas(torch, g, case, stream, hbm_peak, reps=3):
+def time_gas(torch, g, case, stream, hbm_peak, peak_kind, reps=3):
     """The gas step (Section 3.1 step 3) and its source correction (step 6) on the same grid, after the
     radiation legs: dt_gas = 0.1 min(dx) (a Courant number near 0.2 for this gas), one untimed step
     (scratch allocation), then `reps` timed (step, correction) pairs with CUDA events on the library's
@@ -365,13 +365,13 @@ def time_gas(torch, g, case, stream, hbm_peak, reps=3):
     kt = g.kernel_times()
     st = g.get_stats(allow_nonfinite=True)
     return {"value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_gas_step": ms, "dt_gas": dt,
-            "kernels": kt, "roofline": kernel_roofline(kt, hbm_peak, "measured"),
+            "kernels": kt, "roofline": kernel_roofline(kt, hbm_peak, peak_kind),
             "gpu_launches": sum(v["launches"] for v in kt.values()) // reps,
             "gas_energy_floors": st["gas_energy_floors"], "gas_nonfinite": st["gas_nonfinite"]}
 
 
 def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=True, launch_spec="auto",
-              rsla_peak=None):
+              rsla_peak=None, peak_kind="measured"):
     """Device-resident run: autotune the launch configuration (untimed), warm up, then time `steps`
     calls of n_sub subcycles with CUDA events on the library's stream.  The kernel timer brackets
     every kernel of the timed region with events on the same stream (plain launches)."""
@@ -410,7 +410,7 @@ def time_path(torch, rhd, case, precision, n_sub, steps, warmup, stream, tune=Tr
     rsla = time_rsla(torch, g, case, stream, rsla_peak) if rsla_peak else None
     if rsla is not None:
         g.set_kernel_timing(True)
-        rsla["gas_step"] = time_gas(torch, g, case, stream, rsla_peak)
+        rsla["gas_step"] = time_gas(torch, g, case, stream, rsla_peak, peak_kind)
         g.set_kernel_timing(False)
     g.close()
     del dev
@@ -905,7 +905,7 @@ def main():
     clk.start()
     total_ms, per_step, st, kt, launch, tuning, rsla = time_path(torch, rhd, case, "split", args.n_sub, args.steps,
                                                                  args.warmup, stream, launch_spec=args.launch,
-                                                                 rsla_peak=hbm_peak)
+                                                                 rsla_peak=hbm_peak, peak_kind=peak_kind)
     clocks = clk.stop()
     if ws > 1:
         total_ms = max_over_ranks(total_ms, dist, device="cuda")

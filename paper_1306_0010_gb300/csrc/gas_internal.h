@@ -25,10 +25,11 @@ struct GasParams {
     double kappa_F;           // opacity law k_F = kappa_F rho^kpow where no kF array is given
     int kpow, beta_tau, limiter;
     double dt;
-    // split grids: the face fluxes (reconstruction, wave speeds, HLLC) in FP32 with these FP32 copies;
-    // conversions, accumulation and sources stay FP64
+    // split grids: the face fluxes (reconstruction, wave speeds, HLLC), the sources and the increments
+    // in FP32 with these FP32 copies; the state (rho, v, T) accumulates them in FP64
     int split;
     float f_gamma, f_inv_gm1, f_inv_mu, f_inv_dx[3];
+    float f_gm1, f_gm1_mu, f_inv_gm1_mu, f_inv_c, f_kappa_F;  // gamma - 1, (gamma - 1) mu/k_B, its inverse
 };
 
 struct GasArrays {
@@ -41,7 +42,9 @@ struct GasArrays {
     const double* E;          // radiation at t^n (step) or t^{n+1} (correction), G = F/c
     const double* G[3];
     double* wh[5];            // W^{n+1/2} = (rho, vx, vy, vz, P) on the extended grid m[0] x m[1] x m[2]
-    float* wh32[5];           // split grids: its FP32 copy (read by the corrector's FP32 fluxes)
+                              // (FP64 grids; NULL on split grids)
+    float* wh32[5];           // split grids: W^{n+1/2} in FP32 (an intermediate of the step, like the
+                              // radiation's U^{m+1/2})
     double* flux[3][5];       // face fluxes of direction d (predictor layout (m_d + 1) x m_e, corrector
                               // layout (n_d + 1) x n_e), components (rho, Mx, My, Mz, E_gas); FP32 values
                               // (the first half of each buffer) on split grids

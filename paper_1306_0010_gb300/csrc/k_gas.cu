@@ -14,10 +14,16 @@
 // Methods for Fluid Dynamics, Sec. 10.4) uses the Davis wave-speed estimates; the left star state when
 // S* = 0; HLL where the contact speed's denominator is not negative.
 //
-// Precision: the flux kernels are templates on the arithmetic type R.  FP64 grids: R = double.  Split
-// grids: R = float for reconstruction, wave speeds and HLLC (inputs truncated to FP32 by integer bit
-// operations, FP32 fluxes stored) and for the flux differences, while the accumulation, the sources and
-// the conversions between primitive and conserved variables are FP64 on both.  Divisions are reciprocals (FP64: the hardware
+// Precision: the kernels are templates on the arithmetic type R.  FP64 grids: R = double throughout.
+// Split grids: R = float for reconstruction, wave speeds and HLLC (inputs truncated to FP32 by integer
+// bit operations, FP32 fluxes stored), the flux differences and the sources; the half step W^{n+1/2} is
+// an FP32 intermediate; the state (rho, v, T) accumulates FP32 increments in FP64, the pattern of the
+// radiation's split path.  The increments of the primitive variables follow from those of the conserved
+// ones (d rho, dM, dE) without cancellation: with rho' = rho + d rho,
+//     dv = (dM - v d rho) / rho',   dK = (M.dv + dM.v') / 2   (the kinetic energy's change),
+//     dT = ((gamma - 1) mu/k_B (dE - dK) - T d rho) / rho',
+// so each is accurate relative to the increment itself, whatever the ratio of kinetic to internal
+// energy, and the FP64 state gains FP64 additions only.  Divisions are reciprocals (FP64: the hardware
 // approximation refined by Newton-Raphson; FP32: the hardware approximation) times the numerator.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -202,6 +208,54 @@ __device__ __forceinline__ void gas_source(const GasParams& p, double k, const d
     }
 }
 
+// split grids: the same sources in FP32 (k from the FP64 array truncated, or the law in FP32)
+__device__ __forceinline__ float absorption32(const GasParams& p, const double* kF, long long i, float rho)
+{
+    if (kF) return d2f_trunc(kF[i]);
+    return p.kpow == 0 ? p.f_kappa_F : (p.kpow == 1 ? p.f_kappa_F * rho : (p.f_kappa_F * rho) * rho);
+}
+__device__ __forceinline__ void gas_source32(const GasParams& p, float k, const float v[3], float E, const float G[3],
+                                             float S[5])
+{
+    S[0] = 0.0f;
+    if (p.beta_tau) {
+        for (int d = 0; d < 3; ++d) S[1 + d] = k * (G[d] - (4.0f / 3.0f) * v[d] * E * p.f_inv_c);
+        S[4] = -k * (v[0] * G[0] + v[1] * G[1] + v[2] * G[2]);
+    } else {
+        for (int d = 0; d < 3; ++d) S[1 + d] = k * G[d];
+        S[4] = 0.0f;
+    }
+}
+
+// Tests of FP64 values by their bits, on the integer pipes (an FP64 comparison occupies the FP64 pipe,
+// which the split kernels otherwise leave to the accumulation): finite, and below zero (not -0, not NaN)
+__device__ __forceinline__ bool finite_bits(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ bool below_zero_bits(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && b != (long long)0x8000000000000000ull && finite_bits(x);
+}
+
+// Increments of the primitive variables from those of the conserved ones, D = (d rho, dMx, dMy, dMz,
+// dE), at a state (r, v, T) in FP32: dv, dT and rho' = r + d rho (see the precision note above).
+struct PrimInc {
+    float r1, dv[3], dT;
+};
+__device__ __forceinline__ PrimInc prim_increment(const GasParams& p, float r, const float v[3], float T,
+                                                  const float D[5])
+{
+    PrimInc o;
+    o.r1 = r + D[0];
+    const float inv = rcp(o.r1);
+    float dK2 = 0.0f;  // 2 dK = M.dv + dM.v'
+    for (int d = 0; d < 3; ++d) {
+        o.dv[d] = (D[1 + d] - v[d] * D[0]) * inv;
+        dK2 += r * v[d] * o.dv[d] + D[1 + d] * (v[d] + o.dv[d]);
+    }
+    o.dT = (p.f_gm1_mu * (D[4] - 0.5f * dK2) - T * D[0]) * inv;
+    return o;
+}
+
 __device__ __forceinline__ bool finite_prim(const Prim<double>& w)
 {
     return isfinite(w.r) && isfinite(w.v[0]) && isfinite(w.v[1]) && isfinite(w.v[2]) && isfinite(w.P);
@@ -210,8 +264,7 @@ __device__ __forceinline__ bool finite_prim(const Prim<double>& w)
 __device__ __forceinline__ long long first_index() { return (long long)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ long long index_stride() { return (long long)gridDim.x * blockDim.x; }
 
-// minus the divergence of the stored face fluxes: FP64 fluxes in FP64; FP32 fluxes (split grids) in
-// FP32, then widened (their differences carry far less error than the FP32 fluxes themselves)
+// minus the divergence of the stored FP64 face fluxes (FP64 grids)
 template <typename R>
 __device__ __forceinline__ void flux_divergence(const GasParams& p, const GasArrays& a, const long long lo[3],
                                                 const long long hi[3], double dU[5]);
@@ -225,19 +278,19 @@ __device__ __forceinline__ void flux_divergence<double>(const GasParams& p, cons
         for (int q = 0; q < 5; ++q) dU[q] -= (a.flux[d][q][hi[d]] - a.flux[d][q][lo[d]]) * p.inv_dx[d];
     }
 }
-template <>
-__device__ __forceinline__ void flux_divergence<float>(const GasParams& p, const GasArrays& a, const long long lo[3],
-                                                       const long long hi[3], double dU[5])
+
+// split grids: minus the divergence of the stored FP32 face fluxes, in FP32
+__device__ __forceinline__ void flux_divergence32(const GasParams& p, const GasArrays& a, const long long lo[3],
+                                                  const long long hi[3], float dU[5])
 {
-    float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int q = 0; q < 5; ++q) dU[q] = 0.0f;
     for (int d = 0; d < 3; ++d) {
         if (p.n[d] <= 1) continue;
         for (int q = 0; q < 5; ++q) {
             const float* F = reinterpret_cast<const float*>(a.flux[d][q]);
-            acc[q] -= (F[hi[d]] - F[lo[d]]) * p.f_inv_dx[d];
+            dU[q] -= (F[hi[d]] - F[lo[d]]) * p.f_inv_dx[d];
         }
     }
-    for (int q = 0; q < 5; ++q) dU[q] = f2d_exact(acc[q]);
 }
 
 // ---------------------------------------------------------------------------------------- predictor
@@ -266,28 +319,56 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_pred_update_kernel(GasParams 
     const long long ne = gas_count(p.m);
     const double hdt = 0.5 * p.dt;
     unsigned long long floors = 0;
-    for (long long i = first_index(); i < ne; i += index_stride()) {
-        long long k, lo[3], hi[3];
-        int s[3];
-        bool inside;
-        gas_pred_update_cells(p, i, &k, s, &inside, lo, hi);
-        const Prim<double> W = load_prim(p, a, k, s);
-        double U[5], dU[5];
-        to_cons(p, W, U);
-        flux_divergence<R>(p, a, lo, hi, dU);
-        const double G[3] = {flip(a.G[0][k], s[0]), flip(a.G[1][k], s[1]), flip(a.G[2][k], s[2])};
-        double S[5];
-        gas_source(p, absorption(p, a.kF, k, W.r), W.v, a.E[k], G, S);
-        double Uh[5], inv_r;
-        for (int q = 0; q < 5; ++q) Uh[q] = U[q] + hdt * dU[q] + hdt * S[q];
-        Prim<double> Wh;
-        if (to_prim(p, Uh, Wh, inv_r) && inside) ++floors;
-        const double w5[5] = {Wh.r, Wh.v[0], Wh.v[1], Wh.v[2], Wh.P};
-        for (int q = 0; q < 5; ++q) a.wh[q][i] = w5[q];
-        if (a.wh32[0])
-            for (int q = 0; q < 5; ++q) a.wh32[q][i] = d2f_trunc(w5[q]);
+    if constexpr (sizeof(R) == 4) {
+        // split grids: W^{n+1/2} in FP32 from the FP32 copies of W^n and FP32 increments
+        const float fh = (float)hdt;
+        for (long long i = first_index(); i < ne; i += index_stride()) {
+            long long k, lo[3], hi[3];
+            int s[3];
+            bool inside;
+            gas_pred_update_cells(p, i, &k, s, &inside, lo, hi);
+            const float r = a.rho32[k], T = d2f_trunc(a.T[k]);
+            const float v[3] = {flip(a.v32[0][k], s[0]), flip(a.v32[1][k], s[1]), flip(a.v32[2][k], s[2])};
+            float dU[5], S[5];
+            flux_divergence32(p, a, lo, hi, dU);
+            const float G[3] = {flip(d2f_trunc(a.G[0][k]), s[0]), flip(d2f_trunc(a.G[1][k]), s[1]),
+                                flip(d2f_trunc(a.G[2][k]), s[2])};
+            gas_source32(p, absorption32(p, a.kF, k, r), v, d2f_trunc(a.E[k]), G, S);
+            float D[5];
+            for (int q = 0; q < 5; ++q) D[q] = fh * (dU[q] + S[q]);
+            const PrimInc o = prim_increment(p, r, v, T, D);
+            float Th = T + o.dT;
+            if (Th < 0.0f) {
+                Th = 0.0f;
+                if (inside) ++floors;
+            }
+            a.wh32[0][i] = o.r1;
+            for (int d = 0; d < 3; ++d) a.wh32[1 + d][i] = v[d] + o.dv[d];
+            a.wh32[4][i] = o.r1 * Th * p.f_inv_mu;
+        }
+        if (floors) atomicAdd(&a.counters[0], floors);
+    } else {
+        for (long long i = first_index(); i < ne; i += index_stride()) {
+            long long k, lo[3], hi[3];
+            int s[3];
+            bool inside;
+            gas_pred_update_cells(p, i, &k, s, &inside, lo, hi);
+            const Prim<double> W = load_prim(p, a, k, s);
+            double U[5], dU[5];
+            to_cons(p, W, U);
+            flux_divergence<R>(p, a, lo, hi, dU);
+            const double G[3] = {flip(a.G[0][k], s[0]), flip(a.G[1][k], s[1]), flip(a.G[2][k], s[2])};
+            double S[5];
+            gas_source(p, absorption(p, a.kF, k, W.r), W.v, a.E[k], G, S);
+            double Uh[5], inv_r;
+            for (int q = 0; q < 5; ++q) Uh[q] = U[q] + hdt * dU[q] + hdt * S[q];
+            Prim<double> Wh;
+            if (to_prim(p, Uh, Wh, inv_r) && inside) ++floors;
+            const double w5[5] = {Wh.r, Wh.v[0], Wh.v[1], Wh.v[2], Wh.P};
+            for (int q = 0; q < 5; ++q) a.wh[q][i] = w5[q];
+        }
+        if (floors) atomicAdd(&a.counters[0], floors);
     }
-    if (floors) atomicAdd(&a.counters[0], floors);
 }
 
 // ---------------------------------------------------------------------------------------- corrector
@@ -352,67 +433,144 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_corr_update_kernel(GasParams 
 {
     const long long nc = gas_count(p.n);
     unsigned long long floors = 0, bad = 0;
-    for (long long i = first_index(); i < nc; i += index_stride()) {
-        long long x, lo[3], hi[3];
-        gas_corr_update_cells(p, i, &x, lo, hi);
-        const int one[3] = {1, 1, 1};
-        const Prim<double> W = load_prim(p, a, i, one);
-        double U[5], dU[5];
-        to_cons(p, W, U);
-        flux_divergence<R>(p, a, lo, hi, dU);
-        const double rh = a.wh[0][x];
-        const double vh[3] = {a.wh[1][x], a.wh[2][x], a.wh[3][x]};
-        const double kh = absorption(p, a.kF, i, rh);
-        const double E = a.E[i];
-        const double G[3] = {a.G[0][i], a.G[1][i], a.G[2][i]};
-        double S[5];
-        gas_source(p, kh, vh, E, G, S);
-        double U1[5], inv_r;
-        for (int q = 0; q < 5; ++q) U1[q] = U[q] + p.dt * dU[q] + p.dt * S[q];
-        Prim<double> W1;
-        if (to_prim(p, U1, W1, inv_r)) ++floors;
-        if (!finite_prim(W1)) ++bad;
-        a.rho[i] = W1.r;
-        for (int d = 0; d < 3; ++d) a.v[d][i] = W1.v[d];
-        a.T[i] = W1.P * p.mu_over_kB * inv_r;
-        a.pend[0][i] = kh;
-        for (int d = 0; d < 3; ++d) a.pend[1 + d][i] = vh[d];
-        a.pend[4][i] = E;
-        for (int d = 0; d < 3; ++d) a.pend[5 + d][i] = G[d];
+    if constexpr (sizeof(R) == 4) {
+        // split grids: FP32 increments (fluxes, sources at W^{n+1/2}) accumulated into the FP64 state
+        const float fdt = (float)p.dt;
+        for (long long i = first_index(); i < nc; i += index_stride()) {
+            long long x, lo[3], hi[3];
+            gas_corr_update_cells(p, i, &x, lo, hi);
+            const double rho = a.rho[i], T = a.T[i];
+            const double v[3] = {a.v[0][i], a.v[1][i], a.v[2][i]};
+            const float v32[3] = {d2f_trunc(v[0]), d2f_trunc(v[1]), d2f_trunc(v[2])};
+            float dU[5], S[5];
+            flux_divergence32(p, a, lo, hi, dU);
+            const float rh = a.wh32[0][x];
+            const float vh[3] = {a.wh32[1][x], a.wh32[2][x], a.wh32[3][x]};
+            const float kh = absorption32(p, a.kF, i, rh);
+            const double E = a.E[i];
+            const double G[3] = {a.G[0][i], a.G[1][i], a.G[2][i]};
+            const float G32[3] = {d2f_trunc(G[0]), d2f_trunc(G[1]), d2f_trunc(G[2])};
+            gas_source32(p, kh, vh, d2f_trunc(E), G32, S);
+            float D[5];
+            for (int q = 0; q < 5; ++q) D[q] = fdt * (dU[q] + S[q]);
+            const PrimInc o = prim_increment(p, d2f_trunc(rho), v32, d2f_trunc(T), D);
+            const double rho1 = rho + f2d_exact(D[0]);
+            double T1 = T + f2d_exact(o.dT);
+            if (below_zero_bits(T1)) {
+                T1 = 0.0;
+                ++floors;
+            }
+            double v1[3];
+            for (int d = 0; d < 3; ++d) v1[d] = v[d] + f2d_exact(o.dv[d]);
+            if (!(finite_bits(rho1) && finite_bits(v1[0]) && finite_bits(v1[1]) && finite_bits(v1[2]) &&
+                  finite_bits(T1)))
+                ++bad;
+            a.rho[i] = rho1;
+            for (int d = 0; d < 3; ++d) a.v[d][i] = v1[d];
+            a.T[i] = T1;
+            a.pend[0][i] = f2d_exact(kh);
+            for (int d = 0; d < 3; ++d) a.pend[1 + d][i] = f2d_exact(vh[d]);
+            a.pend[4][i] = E;
+            for (int d = 0; d < 3; ++d) a.pend[5 + d][i] = G[d];
+        }
+        if (floors) atomicAdd(&a.counters[0], floors);
+        if (bad) atomicAdd(&a.counters[1], bad);
+    } else {
+        for (long long i = first_index(); i < nc; i += index_stride()) {
+            long long x, lo[3], hi[3];
+            gas_corr_update_cells(p, i, &x, lo, hi);
+            const int one[3] = {1, 1, 1};
+            const Prim<double> W = load_prim(p, a, i, one);
+            double U[5], dU[5];
+            to_cons(p, W, U);
+            flux_divergence<R>(p, a, lo, hi, dU);
+            const double rh = a.wh[0][x];
+            const double vh[3] = {a.wh[1][x], a.wh[2][x], a.wh[3][x]};
+            const double kh = absorption(p, a.kF, i, rh);
+            const double E = a.E[i];
+            const double G[3] = {a.G[0][i], a.G[1][i], a.G[2][i]};
+            double S[5];
+            gas_source(p, kh, vh, E, G, S);
+            double U1[5], inv_r;
+            for (int q = 0; q < 5; ++q) U1[q] = U[q] + p.dt * dU[q] + p.dt * S[q];
+            Prim<double> W1;
+            if (to_prim(p, U1, W1, inv_r)) ++floors;
+            if (!finite_prim(W1)) ++bad;
+            a.rho[i] = W1.r;
+            for (int d = 0; d < 3; ++d) a.v[d][i] = W1.v[d];
+            a.T[i] = W1.P * p.mu_over_kB * inv_r;
+            a.pend[0][i] = kh;
+            for (int d = 0; d < 3; ++d) a.pend[1 + d][i] = vh[d];
+            a.pend[4][i] = E;
+            for (int d = 0; d < 3; ++d) a.pend[5 + d][i] = G[d];
+        }
+        if (floors) atomicAdd(&a.counters[0], floors);
+        if (bad) atomicAdd(&a.counters[1], bad);
     }
-    if (floors) atomicAdd(&a.counters[0], floors);
-    if (bad) atomicAdd(&a.counters[1], bad);
 }
 
 // ---------------------------------------------------------------------------------------- correction
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(GAS_THREADS) gas_correct_kernel(GasParams p, GasArrays a)
 {
     const long long nc = gas_count(p.n);
     const double hdt = 0.5 * p.dt;
     unsigned long long floors = 0, bad = 0;
-    for (long long i = first_index(); i < nc; i += index_stride()) {
-        const int one[3] = {1, 1, 1};
-        const Prim<double> W = load_prim(p, a, i, one);
-        double U[5];
-        to_cons(p, W, U);
-        // S_e,gas is linear in the radiation state: S(W^{n+1/2}, U_rad^{n+1}) - S(W^{n+1/2}, U_rad^n) is S of
-        // the radiation's change
-        const double kh = a.pend[0][i];
-        const double vh[3] = {a.pend[1][i], a.pend[2][i], a.pend[3][i]};
-        const double dG[3] = {a.G[0][i] - a.pend[5][i], a.G[1][i] - a.pend[6][i], a.G[2][i] - a.pend[7][i]};
-        double dS[5];
-        gas_source(p, kh, vh, a.E[i] - a.pend[4][i], dG, dS);
-        for (int q = 1; q < 5; ++q) U[q] = U[q] + hdt * dS[q];
-        Prim<double> W1;
-        double inv_r;
-        if (to_prim(p, U, W1, inv_r)) ++floors;
-        if (!finite_prim(W1)) ++bad;
-        for (int d = 0; d < 3; ++d) a.v[d][i] = W1.v[d];
-        a.T[i] = W1.P * p.mu_over_kB * inv_r;
+    if constexpr (SPLIT) {
+        // split grids: the change of the sources in FP32 (the radiation's change as the difference of its
+        // FP32 copies: its error is that of the FP32 sources themselves), its momentum and energy
+        // increments accumulated into the FP64 state
+        const float fh = (float)hdt;
+        for (long long i = first_index(); i < nc; i += index_stride()) {
+            const double rho = a.rho[i], T = a.T[i];
+            const double v[3] = {a.v[0][i], a.v[1][i], a.v[2][i]};
+            const float v32[3] = {d2f_trunc(v[0]), d2f_trunc(v[1]), d2f_trunc(v[2])};
+            const float kh = d2f_trunc(a.pend[0][i]);
+            const float vh[3] = {d2f_trunc(a.pend[1][i]), d2f_trunc(a.pend[2][i]), d2f_trunc(a.pend[3][i])};
+            float dG[3];
+            for (int d = 0; d < 3; ++d) dG[d] = d2f_trunc(a.G[d][i]) - d2f_trunc(a.pend[5 + d][i]);
+            float dS[5];
+            gas_source32(p, kh, vh, d2f_trunc(a.E[i]) - d2f_trunc(a.pend[4][i]), dG, dS);
+            const float D[5] = {0.0f, fh * dS[1], fh * dS[2], fh * dS[3], fh * dS[4]};
+            const PrimInc o = prim_increment(p, d2f_trunc(rho), v32, d2f_trunc(T), D);
+            double T1 = T + f2d_exact(o.dT);
+            if (below_zero_bits(T1)) {
+                T1 = 0.0;
+                ++floors;
+            }
+            double v1[3];
+            for (int d = 0; d < 3; ++d) v1[d] = v[d] + f2d_exact(o.dv[d]);
+            if (!(finite_bits(v1[0]) && finite_bits(v1[1]) && finite_bits(v1[2]) && finite_bits(T1))) ++bad;
+            for (int d = 0; d < 3; ++d) a.v[d][i] = v1[d];
+            a.T[i] = T1;
+        }
+        if (floors) atomicAdd(&a.counters[0], floors);
+        if (bad) atomicAdd(&a.counters[1], bad);
+    } else {
+        for (long long i = first_index(); i < nc; i += index_stride()) {
+            const int one[3] = {1, 1, 1};
+            const Prim<double> W = load_prim(p, a, i, one);
+            double U[5];
+            to_cons(p, W, U);
+            // S_e,gas is linear in the radiation state: S(W^{n+1/2}, U_rad^{n+1}) - S(W^{n+1/2}, U_rad^n) is S of
+            // the radiation's change
+            const double kh = a.pend[0][i];
+            const double vh[3] = {a.pend[1][i], a.pend[2][i], a.pend[3][i]};
+            const double dG[3] = {a.G[0][i] - a.pend[5][i], a.G[1][i] - a.pend[6][i], a.G[2][i] - a.pend[7][i]};
+            double dS[5];
+            gas_source(p, kh, vh, a.E[i] - a.pend[4][i], dG, dS);
+            for (int q = 1; q < 5; ++q) U[q] = U[q] + hdt * dS[q];
+            Prim<double> W1;
+            double inv_r;
+            if (to_prim(p, U, W1, inv_r)) ++floors;
+            if (!finite_prim(W1)) ++bad;
+            for (int d = 0; d < 3; ++d) a.v[d][i] = W1.v[d];
+            a.T[i] = W1.P * p.mu_over_kB * inv_r;
+        }
+        if (floors) atomicAdd(&a.counters[0], floors);
+        if (bad) atomicAdd(&a.counters[1], bad);
     }
-    if (floors) atomicAdd(&a.counters[0], floors);
-    if (bad) atomicAdd(&a.counters[1], bad);
 }
 
 int blocks_for(long long n)
@@ -477,7 +635,8 @@ cudaError_t launch_gas_corr_update(const GasParams& p, const GasArrays& a, cudaS
 
 cudaError_t launch_gas_correct(const GasParams& p, const GasArrays& a, cudaStream_t s)
 {
-    gas_correct_kernel<<<blocks_for(gas_count(p.n)), GAS_THREADS, 0, s>>>(p, a);
+    if (p.split) gas_correct_kernel<true><<<blocks_for(gas_count(p.n)), GAS_THREADS, 0, s>>>(p, a);
+    else gas_correct_kernel<false><<<blocks_for(gas_count(p.n)), GAS_THREADS, 0, s>>>(p, a);
     return cudaGetLastError();
 }
 

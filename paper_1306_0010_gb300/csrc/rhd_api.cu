@@ -1464,6 +1464,11 @@ GasParams gas_params(const GridState& gs, double dt)
     p.f_inv_gm1 = (float)p.inv_gm1;
     p.f_inv_mu = (float)p.inv_mu;
     for (int d = 0; d < 3; ++d) p.f_inv_dx[d] = (float)p.inv_dx[d];
+    p.f_gm1 = (float)p.gm1;
+    p.f_gm1_mu = (float)(p.gm1 * p.mu_over_kB);
+    p.f_inv_gm1_mu = (float)(1.0 / (p.gm1 * p.mu_over_kB));
+    p.f_inv_c = (float)p.inv_c;
+    p.f_kappa_F = (float)p.kappa_F;
     return p;
 }
 
@@ -1495,10 +1500,11 @@ GasArrays gas_arrays(rhd_ctx* ctx, GridState& gs)
 rhd_status gas_prepare(rhd_ctx* ctx, GridState& gs, const GasParams& p)
 {
     rhd_status st;
-    if (!gs.gas_wh[0]) {
+    if (!gs.gas_wh[0] && !gs.gas_wh32[0]) {
         const size_t fb = p.split ? sizeof(float) : sizeof(double);
         for (int q = 0; q < 5; ++q) {
-            if ((st = dalloc(ctx, (void**)&gs.gas_wh[q], sizeof(double) * (size_t)gas_count(p.m)))) return st;
+            if (!p.split && (st = dalloc(ctx, (void**)&gs.gas_wh[q], sizeof(double) * (size_t)gas_count(p.m))))
+                return st;
             if (p.split && (st = dalloc(ctx, (void**)&gs.gas_wh32[q], sizeof(float) * (size_t)gas_count(p.m))))
                 return st;
         }
@@ -1540,18 +1546,18 @@ rhd_status gas_refresh_copies(rhd_ctx* ctx, GridState& gs)
 }
 
 // bytes per cell of each gas kernel (each array read or written once per launch): the gas state is
-// 40 B (rho, T, v; the split predictor's fluxes read the FP32 rho, v and the FP64 T, 24 B), W^{n+1/2}
-// 40 B (+ its 20 B FP32 copy on split grids, which the corrector's fluxes read instead), one
-// face-flux array 40 B per cell (20 B split), the radiation 32 B, the correction's record 64 B
+// 40 B (rho, T, v; on split grids the predictor reads the FP32 rho, v and the FP64 T, 24 B), W^{n+1/2}
+// 40 B (20 B in FP32 on split grids), one face-flux array 40 B per cell (20 B split), the radiation
+// 32 B, the correction's record 64 B
 double gas_alg_bytes(const GridState& gs, int k, int nact)
 {
     const bool split = gs.desc.precision == RHD_SPLIT;
     const double kf = gs.has_kF ? 8.0 : 0.0, fl = split ? 20.0 : 40.0;
     switch (k) {
     case K_GAS_PRED_FLUX: return (split ? 24.0 : 40.0) + fl;
-    case K_GAS_PRED_UPDATE: return 40.0 + 32.0 + kf + fl * nact + 40.0 + (split ? 20.0 : 0.0);
+    case K_GAS_PRED_UPDATE: return (split ? 24.0 : 40.0) + 32.0 + kf + fl * nact + (split ? 20.0 : 40.0);
     case K_GAS_CORR_FLUX: return (split ? 20.0 : 40.0) + fl;
-    case K_GAS_CORR_UPDATE: return 40.0 + fl * nact + 32.0 + 32.0 + kf + 40.0 + 64.0;
+    case K_GAS_CORR_UPDATE: return 40.0 + fl * nact + (split ? 16.0 : 32.0) + 32.0 + kf + 40.0 + 64.0;
     default: return 40.0 + 64.0 + 32.0 + 32.0;  // K_GAS_CORRECT
     }
 }

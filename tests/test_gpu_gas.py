@@ -9,12 +9,16 @@ costs only rounding: normwise errors stay near 1e-15 (measured up to 6e-16).  Th
 path's, GAS_TOL = 1e-12 per field (rho by max rho, v by max(|v| + a), T by max T), also for a whole cycle
 (gas step, radiation subcycles, correction).
 
-Split grids compute the face fluxes in FP32 (inputs truncated to FP32, hardware reciprocal and square
-root approximations) and everything else in FP64.  A face flux then carries a relative error of at
-most about 50 FP32 ulps (2^-24 each: the truncated inputs and some 25 dependent operations), 3e-6 of
-the flux scale rho (|v| + a)^2; a step adds the differences of 2 faces in each of 3 directions times
-dt/dx (below the Courant number, 1/2) in each of two stages, and the flux scale is up to (|v| + a)^2 ~ 4
-times the field scales above: 2 x 6 x 0.5 x 3e-6 x 4 = 7e-5.  The bound used is SPLIT_GAS_TOL = 1e-4."""
+Split grids compute the face fluxes, the sources, the half step W^{n+1/2} and the increments in FP32
+(inputs truncated to FP32, hardware reciprocal and square root approximations) and add the increments
+to the FP64 state.  A face flux carries a relative error of at most about 50 FP32 ulps (2^-24 each: the
+truncated inputs and some 25 dependent operations), 3e-6 of the flux scale rho (|v| + a)^2; a step adds
+the differences of 2 faces in each of 3 directions times dt/dx (below the Courant number, 1/2) in each
+of two stages, and the flux scale is up to (|v| + a)^2 ~ 4 times the field scales above:
+2 x 6 x 0.5 x 3e-6 x 4 = 7e-5.  The increments of v and T are formed from those of rho, M and E
+without cancellation (k_gas.cu), each a few FP32 ulps of the increment itself, and W^{n+1/2} in FP32 is
+within the truncation the FP32 fluxes apply to their inputs anyway.  The bound used is SPLIT_GAS_TOL =
+1e-4."""
 import math
 
 import numpy as np
