@@ -213,10 +213,12 @@ rhd_status rhd_radiation_subcycle(rhd_ctx* ctx, int n_sub, double chat, double d
  * rhd_stats.gas_energy_floors).  The step leaves a source correction pending: run the radiation
  * subcycles that span dt_gas, then rhd_gas_correct.  The energy exchange stays in the subcycles unless
  * the grid has RHD_FLAG_EXCHANGE_ON_GAS_STEP (then rhd_gas_exchange runs it once, before this step).
- * RHD_SPLIT grids compute the face fluxes (reconstruction, wave speeds, HLLC) and their differences in
- * FP32 and the rest in FP64.  Does not synchronise.  Scratch, allocated by the first call, for n cells
- * and m = (n0+4)(n1+4)(n2+4) (2D / 1D: no padding in inactive directions): 5 m + 8 n doubles, and 15 m
- * face values (doubles; floats plus 5 m more floats on RHD_SPLIT grids).  Single grids only.  Errors: RHD_ERR_ARG (dt_gas), RHD_ERR_STATE
+ * RHD_SPLIT grids compute the face fluxes (reconstruction, wave speeds, HLLC), their differences, the
+ * sources, the half step and the increments of (rho, v, T) in FP32 and add the increments to the FP64
+ * state in FP64 (rhd_gas_correct likewise).  Does not synchronise.  Scratch, allocated by the first
+ * call, for n cells and m = (n0+4)(n1+4)(n2+4) (2D / 1D: no padding in inactive directions): 8 n
+ * doubles; 5 m doubles and 15 m face doubles (FP64 grids) or 5 m floats and 15 m face floats
+ * (RHD_SPLIT grids).  Single grids only.  Errors: RHD_ERR_ARG (dt_gas), RHD_ERR_STATE
  * (ensemble, gas or moments not set), RHD_ERR_OOM, RHD_ERR_CUDA. */
 rhd_status rhd_gas_step(rhd_ctx* ctx, double dt_gas);
 
