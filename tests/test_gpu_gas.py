@@ -253,3 +253,37 @@ def test_checkpoint_after_gas_cycles_resumes_bitwise(rhd, tmp_path):
         assert np.array_equal(ma[k], mb[k]), k
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_config3_shell_coupled_cycles_reduced(rhd, precision):
+    """The dusty shell of the 256^3 coupled benchmark at 40^3: two whole cycles of 25 radiation subcycles
+    each (Delta t_gas = 25 radiation steps, gas Courant number 0.2) against the oracle's cycles
+    (tests/oracle_cycles.py).  FP64: 1e-12.  Split: the gas bound per step for the gas, the derived
+    radiation bound over the 50 subcycles for the moments."""
+    from oracle_cycles import run_cycles
+    from split_bounds import split_bound
+
+    case = wl.config3(N=40, n_sub=25, precision=precision)
+    dt_gas = 25 * case["dt"]
+    g = rhd.Grid(case["desc"])
+    g.load_case(case)
+    subs = [g.gas_cycle(case["chat"], dt_gas=dt_gas)[1] for _ in range(2)]
+    out, mom, st = g.get_gas(), g.get_moments(), g.get_stats()
+    g.close()
+    assert subs == [25, 25]
+    ref_gas, ref_rad, n = run_cycles(case, 2 * dt_gas, dt_fixed=dt_gas)
+    assert n == 2
+    if precision == "fp64":
+        tol_gas = tol_rad = GAS_TOL
+    else:
+        tol_gas, tol_rad = 2 * SPLIT_GAS_TOL, split_bound(case, 50)
+    e = gas_errors(out, ref_gas, case["desc"])
+    assert max(e.values()) <= tol_gas, e
+    sE = float(np.max(np.abs(ref_rad["E"])))
+    er = {"E": float(np.max(np.abs(mom["E"] - ref_rad["E"]))) / sE}
+    for k in ("Fx", "Fy", "Fz"):
+        er[k] = float(np.max(np.abs(mom[k] - ref_rad[k]))) / (case["desc"]["c"] * sE)
+    assert max(er.values()) <= tol_rad, er
+    assert st["n_nonfinite"] == 0 and st["gas_nonfinite"] == 0
+    print(precision, "config3 coupled 40^3: gas", max(e.values()), "radiation", max(er.values()))
