@@ -469,3 +469,25 @@ def test_reruns_are_bitwise_identical(rhd):
     for i in range(len(cases)):
         for k in runs[0][i]:
             assert np.array_equal(runs[0][i][k], runs[1][i][k]), (i, k)
+
+
+SMALLEST = [((3, 3, 3), "periodic"), ((3, 3, 3), "reflect"), ((3, 4, 3), "outflow"), ((3, 3, 1), "periodic"),
+            ((3, 1, 1), "reflect")]
+
+
+@pytest.mark.parametrize("precision,flags", [("fp64", 0), ("split", 0), ("split", 2)],
+                         ids=["fp64", "split_twopass", "split_fused"])
+@pytest.mark.parametrize("n,bc", SMALLEST, ids=[f"{n[0]}x{n[1]}x{n[2]}_{bc}" for n, bc in SMALLEST])
+def test_smallest_grids(rhd, n, bc, precision, flags):
+    """Grids of three cells per active direction (the smallest accepted): one ragged tile whose halo
+    wraps, mirrors or clamps onto the same few cells in every direction."""
+    if flags and n[2] == 1:
+        pytest.skip("1D and 2D split grids always run the fused kernel")
+    case = wl.parity_case(f"small_{bc}", n, bc=bc, exchange="full", beta_tau=True, with_j=True, n_sub=5,
+                          seed=sum(n) + len(bc), precision=precision)
+    out, st = run_gpu(rhd, case, desc_over={"flags": flags})
+    ref, rst = orc.subcycles(case)
+    e = errors(out, ref, case["desc"])
+    tol = FP64_TOL if precision == "fp64" else split_bound(case, 5)
+    assert max(e.values()) <= tol, e
+    assert st["n_nonfinite"] == 0
