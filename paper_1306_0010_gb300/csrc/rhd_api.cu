@@ -489,6 +489,15 @@ rhd_status set_gas(rhd_ctx* ctx, GridState& gs, const double* rho, const double*
     if (!rho || !T) return fail(ctx, RHD_ERR_ARG, "rho and T are required");
     rhd_status st = enter(ctx);
     if (st) return st;
+    // the arrays the captured subcycle graphs point at, and which of them are present: the graphs stay
+    // valid when a new state arrives in the same arrays
+    auto layout = [&gs] {
+        return std::vector<const void*>{gs.v[0], gs.v[1], gs.v[2], gs.v32[0], gs.v32[1], gs.v32[2], gs.kP, gs.kP32,
+                                        gs.kF, gs.kF32, gs.j, gs.j32,
+                                        (const void*)(uintptr_t)(gs.has_v | gs.has_kP << 1 | gs.has_kF << 2 |
+                                                                 gs.has_j << 3 | gs.has_gas << 4)};
+    };
+    const std::vector<const void*> before = layout();
     if ((st = put(ctx, gs.rho, rho, gs.ncell, on_device))) return st;
     if ((st = put(ctx, gs.T, T, gs.ncell, on_device))) return st;
     if (gs.desc.precision == RHD_SPLIT) RHD_CUDA(ctx, launch_to_float(gs.rho32, gs.rho, gs.ncell, ctx->stream));
@@ -509,7 +518,7 @@ rhd_status set_gas(rhd_ctx* ctx, GridState& gs, const double* rho, const double*
     gs.has_gas = true;
     gs.gas4_ok = false;
     gs.gas_pending = false;  // a pending source correction belongs to the replaced state
-    clear_graphs(ctx);  // array pointers may have changed
+    if (layout() != before) clear_graphs(ctx);  // the kernels' array pointers changed
     return leave(ctx);
 }
 

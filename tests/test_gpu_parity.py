@@ -491,3 +491,32 @@ def test_smallest_grids(rhd, n, bc, precision, flags):
     tol = FP64_TOL if precision == "fp64" else split_bound(case, 5)
     assert max(e.values()) <= tol, e
     assert st["n_nonfinite"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_new_gas_state_in_the_same_arrays_reuses_the_graph(rhd, precision):
+    """A new gas state given in the same layout keeps the captured subcycle graph, and the replay reads
+    the new values: the result equals a fresh grid's bit for bit.  A changed layout (a velocity component
+    dropped) rebuilds it."""
+    a = wl.parity_case("graph_a", (20, 13, 9), bc="periodic", exchange="full", beta_tau=True, n_sub=3, seed=31,
+                       precision=precision)
+    b = wl.parity_case("graph_b", (20, 13, 9), bc="periodic", exchange="full", beta_tau=True, n_sub=3, seed=32,
+                       precision=precision)
+    g = rhd.Grid(a["desc"])
+    g.load_case(a)
+    g.radiation_subcycle(3, a["chat"], a["dt"])  # captures the graph
+    g.load_case(b)
+    g.radiation_subcycle(3, a["chat"], a["dt"])  # replays it on b's values
+    out = g.get_moments()
+    out["T"] = g.get_gas_state()
+    c = dict(b, fields=dict(b["fields"], vz=None))  # without vz: a different layout
+    g.load_case(c)
+    g.radiation_subcycle(3, a["chat"], a["dt"])
+    out_c = g.get_moments()
+    g.close()
+    fresh, _ = run_gpu(rhd, dict(b, dt=a["dt"], chat=a["chat"]))
+    fresh_c, _ = run_gpu(rhd, dict(c, dt=a["dt"], chat=a["chat"]))
+    for k in ("E", "Fx", "Fy", "Fz", "T"):
+        assert np.array_equal(out[k], fresh[k]), k
+    for k in ("E", "Fx", "Fy", "Fz"):
+        assert np.array_equal(out_c[k], fresh_c[k]), k
