@@ -263,6 +263,7 @@ void fill_params(GridState& gs)
     g.speeds = d.speeds;
     g.inv_c = 1.0 / d.c;
     g.gm1_mu = (d.gamma - 1.0) * d.mu_over_kB;
+    g.inv_gm1_mu = 1.0 / g.gm1_mu;
     g.inv_eps_c = 1.0 / (d.linear_eps * d.c);
     g.inv_a_rad = 1.0 / d.a_rad;
     g.f_inv_c = (float)g.inv_c;

@@ -38,9 +38,9 @@ struct GridParams {
     double linear_eps;          // EX_LINEAR: retardation eps = 4 a_R / alpha of the material c_v = alpha T^3
     int kpow;
     int exchange, beta_tau, limiter, closure, speeds;
-    // derived on the host: 1/c, (gamma - 1) mu/k_B, 1/(eps c) and 1/a_R of the linear exchange, and
-    // FP32 copies used by the split path
-    double inv_c, gm1_mu, inv_eps_c, inv_a_rad;
+    // derived on the host: 1/c, (gamma - 1) mu/k_B and its inverse, 1/(eps c) and 1/a_R of the linear
+    // exchange, and FP32 copies used by the split path
+    double inv_c, gm1_mu, inv_gm1_mu, inv_eps_c, inv_a_rad;
     float f_inv_c, f_gm1_mu, f_c, f_a_rad, f_theta_F, f_theta_E, f_E_floor, f_kappa_P, f_kappa_F;
     float f_inv_dx[3];
     // two-pass split path: ghost layers of U^{m+1/2} stored per direction, 2, or 0 where both faces are

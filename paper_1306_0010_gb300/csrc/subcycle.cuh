@@ -474,18 +474,23 @@ struct ExchangeOut {
     int theta_fb, newton_fb, iters;
 };
 
+__device__ __forceinline__ float exchange_delta_fp32(const GridParams& g, float chat, float dt, float rho, float kP,
+                                                     float E, float T, ExchangeOut& o, float& qout);
+
 __device__ __forceinline__ ExchangeOut exchange_fp64(const GridParams& g, double chat, double dt, double rho,
                                                      double kP, double& E, double& T)
 {
     ExchangeOut o = {0, 0, 0};
+    // divisions as Newton-refined reciprocals times the numerator (within an ulp or two; the iteration
+    // below converges to its own rounding fixed point either way)
     const double c = g.c;
-    const double q = (g.gamma - 1.0) * g.mu_over_kB / rho;
-    const double e = (rho * T / g.mu_over_kB) / (g.gamma - 1.0);
+    const double q = g.gm1_mu * rcp(rho);
+    const double e = rho * T * g.inv_gm1_mu;
     const double alpha = g.a_rad * (q * q) * (q * q);
     const double eta = c * kP * dt;
-    const double r = chat / c;
+    const double r = chat * g.inv_c;
     double th = g.theta_E;
-    double Ebar = e + (c / chat) * E;
+    double Ebar = e + E * rcp(r);
     double e4 = (e * e) * (e * e);
     double c0 = (1.0 - th) * eta * (alpha * e4 - E) - (e + r * eta * th * Ebar);
     if (c0 > 0.0) {
@@ -496,11 +501,21 @@ __device__ __forceinline__ ExchangeOut exchange_fp64(const GridParams& g, double
     const double A = eta * th * alpha;
     const double B = 1.0 + r * eta * th;
     const double C = eta * ((1.0 - th) * alpha * e4 - E);
-    double b = fabs(c0 / B);
-    if (A > 0.0) b = fmin(b, sqrt(sqrt(fabs(c0 / A))));
+    double b = fabs(c0 * rcp(B));
+    if (A > 0.0) b = fmin(b, sqrt(sqrt(fabs(c0 * rcp(A)))));
     const double dhi = b - e;   // delta upper bound
     const double dlo = -e;      // x >= 0
+    // start from the same iteration in FP32 (within 2^-25 of the root, on the FP32 pipe; values outside
+    // the FP32 range give a non-finite seed and the start d = 0): one or two FP64 steps then reach the
+    // FP64 rounding fixed point, against up to about fifteen from d = 0 on states far from equilibrium
     double d = 0.0;
+    {
+        ExchangeOut o32;
+        float q32;
+        const float d32 = exchange_delta_fp32(g, (float)chat, (float)dt, (float)rho, (float)kP, (float)E, (float)T,
+                                              o32, q32);
+        if (isfinite(d32) && !o32.newton_fb) d = fmin(fmax((double)d32, dlo), dhi);
+    }
     bool conv = false;
     int it;
     for (it = 0; it < 100; ++it) {
@@ -508,7 +523,7 @@ __device__ __forceinline__ ExchangeOut exchange_fp64(const GridParams& g, double
         double x2 = x * x;
         double gv = A * x2 * x2 + B * d + C;
         double gp = 4.0 * A * x2 * x + B;
-        double dn = d - gv / gp;
+        double dn = d - gv * rcp(gp);
         if (dn > dhi) dn = dhi;
         if (dn < dlo) dn = dlo;
         if (it > 0 && !(dn < d)) {
@@ -549,7 +564,7 @@ __device__ __forceinline__ void exchange_linear_fp64(const GridParams& g, double
     double v = g.a_rad * T2 * T2;
     const double dtau = eps * c * kP * dt;
     const double r = chat * g.inv_eps_c;  // chat / (eps c), 1/(eps c) from the host
-    const double dv = -(v - E) * dtau / (1.0 + g.theta_E * (1.0 + r) * dtau);
+    const double dv = -(v - E) * dtau * rcp(1.0 + g.theta_E * (1.0 + r) * dtau);
     E = E + (-r * dv);
     v = v + dv;
     if (v < 0.0) v = 0.0;
