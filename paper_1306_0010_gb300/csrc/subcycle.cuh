@@ -139,9 +139,17 @@ __device__ __forceinline__ ClosureScalars<R> closure_scalars(R E, R gx, R gy, R 
         f2 = R(1);
     }
     k.invE = invE;
-    k.s = sqrt_fast(xfma(R(-3), f2, R(4)));
+    const R x4 = xfma(R(-3), f2, R(4));  // in [1, 4]
+    R inv_s;
+    if constexpr (sizeof(R) == 8) {
+        inv_s = rsqrt_nr(x4);  // s and 1/s from one refined inverse square root
+        k.s = xmul(x4, inv_s);
+    } else {
+        k.s = sqrt_fast(x4);
+        inv_s = rcp(k.s);
+    }
     k.inv2ps = rcp(xadd(R(2), k.s));
-    k.cs = xmul(chat, rcp(k.s));
+    k.cs = xmul(chat, inv_s);
     if (p1) {
         k.a = xmul(E, R(1.0 / 3.0));
         k.b = R(0);

@@ -1,5 +1,7 @@
-"""GPU: the FP64 path's reciprocal (two Newton-Raphson steps on the hardware approximation) is within
-two units in the last place of CUDA's correctly rounded 1.0 / x."""
+"""GPU: the FP64 path's reciprocal and inverse square root (two Newton-Raphson steps on the hardware
+approximations) are within two units in the last place of CUDA's correctly rounded 1.0 / x and within
+three of 1.0 / sqrt(x) (itself two roundings); x rsqrt(x) on [1, 4], the closure's square root, within
+two of sqrt(x)."""
 import os
 import subprocess
 
@@ -24,3 +26,5 @@ def test_fp64_reciprocal_within_two_ulp():
     out = subprocess.run([exe], check=True, capture_output=True, text=True, timeout=120).stdout
     fields = dict(zip(out.split()[0::2], (int(v) for v in out.split()[1::2])))
     assert fields["max_ulp"] <= 2, out
+    assert fields["max_ulp_rsqrt"] <= 3, out
+    assert fields["max_ulp_sqrt14"] <= 2, out
