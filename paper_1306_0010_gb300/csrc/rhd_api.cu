@@ -823,9 +823,12 @@ rhd_status ens_prepare(rhd_ctx* ctx, double chat, const double* dt_per_grid, dou
             eg[i].a = p.a;
             eg[i].dt = dt_per_grid[i];
             eg[i].f_dt = (float)dt_per_grid[i];
-            // corrector (two-pass) or fused items: tiles of the interior; the two-pass kernels use 32 x 8
-            eg[i].tiles_x = twopass ? (gs.desc.n[0] + 31) / 32 : gs.tiles_x;
-            eg[i].tiles_y = twopass ? (gs.desc.n[1] + 7) / 8 : gs.tiles_y;
+            // corrector (two-pass) or fused items: tiles of the interior; the two-pass kernels use 32 x 8,
+            // the fused ensemble kernels their own tile
+            int etx = 32, ety = 8;
+            if (!twopass) ensemble_tile_shape(gs.desc.precision == RHD_SPLIT ? 1 : 0, &etx, &ety);
+            eg[i].tiles_x = (gs.desc.n[0] + etx - 1) / etx;
+            eg[i].tiles_y = (gs.desc.n[1] + ety - 1) / ety;
             eg[i].tiles_z = (gs.desc.n[2] + gs.z_chunk - 1) / gs.z_chunk;
             eg[i].first_item = first;
             first += (long long)eg[i].tiles_x * eg[i].tiles_y * eg[i].tiles_z;
@@ -965,7 +968,7 @@ std::vector<rhd_launch_config> grid_candidates(const GridState& gs)
         rhd_launch_config c = current_config(gs);
         add(c.variant, c.tile_x, c.tile_y, c.z_chunk, c.staging);
     } else if (gs.desc.precision == RHD_FP64) {
-        for (int zc : {8, 16, 32, 64, 128, 256, 512}) add(RHD_VARIANT_FUSED, 16, 8, zc, RHD_STAGING_CPASYNC);
+        for (int zc : {8, 16, 32, 64, 128, 256, 512}) add(RHD_VARIANT_FUSED, 16, 16, zc, RHD_STAGING_CPASYNC);
     } else {
         for (int stg : {RHD_STAGING_CPASYNC, RHD_STAGING_TMA})
             for (int zc : {16, 32, 64, 128}) add(RHD_VARIANT_TWOPASS, 32, 8, zc, stg);

@@ -186,6 +186,7 @@ int ensemble_ctas_per_sm_corrector();
 
 // Tile geometry: the default per precision and dimensionality, and the shapes compiled for 3D.
 void tile_shape(int precision, int nact, int* tx, int* ty);
+void ensemble_tile_shape(int precision, int* tx, int* ty);  // the fused ensemble kernels' tile (3D)
 bool tile_supported(int precision, int nact, int tx, int ty);
 
 // Auxiliary kernels (k_aux.cu).

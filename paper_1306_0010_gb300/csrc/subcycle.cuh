@@ -1464,7 +1464,8 @@ constexpr size_t tile_smem_bytes()
 }
 
 template <typename R, int TX, int TY, int DIM, bool SPLIT>
-__global__ void __launch_bounds__(Geo<TX, TY, DIM>::NT, (Geo<TX, TY, DIM>::NT > 256) ? 1 : 2)
+__global__ void __launch_bounds__(Geo<TX, TY, DIM>::NT,
+                                  (Geo<TX, TY, DIM>::NT > 256 || (sizeof(R) == 8 && Geo<TX, TY, DIM>::NT >= 256)) ? 1 : 2)
     subcycle_kernel(const __grid_constant__ StepParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

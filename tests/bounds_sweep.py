@@ -33,7 +33,7 @@ CASES = [
     ((33, 9, 5), (["reflect", "periodic", "outflow"], ["outflow", "periodic", "reflect"]), "split",
      {"variant": "fused", "tile": (32, 8), "z_chunk": 32, "staging": "cpasync"}),
     ((33, 9, 5), "outflow", "split", {"variant": "fused", "tile": (64, 8), "z_chunk": 32, "staging": "cpasync"}),
-    ((19, 13, 11), "outflow", "fp64", {"variant": "fused", "tile": (16, 8), "z_chunk": 8, "staging": "cpasync"}),
+    ((19, 13, 11), "outflow", "fp64", {"variant": "fused", "tile": (16, 16), "z_chunk": 8, "staging": "cpasync"}),
     ((9, 4, 3), "outflow", "split", None),
     ((33, 9, 5), "outflow", "split", {"variant": "twopass", "tile": (32, 8), "z_chunk": 3, "staging": "cpasync"}),
 ]

@@ -102,7 +102,7 @@ def test_fp64_tuned_parity(rhd):
     g = rhd.Grid(case["desc"])
     g.load_case(case)
     chosen, table = g.autotune(case["chat"], case["dt"], reps=2)
-    assert chosen["variant"] == "fused" and chosen["tile"] == (16, 8)
+    assert chosen["variant"] == "fused" and chosen["tile"] == (16, 16)
     assert sorted({c["z_chunk"] for c in table}) == [8, 16, 32, 40]
     g.radiation_subcycle(case["n_sub"], case["chat"], case["dt"])
     e = errors(snapshot(g), ref, case["desc"])
@@ -189,8 +189,9 @@ def test_unsupported_launch_config_rejected(rhd):
     g = rhd.Grid(case["desc"])
     for cfg in (dict(variant="twopass", tile=(32, 8), z_chunk=16, staging="cpasync"),
                 dict(variant="fused", tile=(32, 16), z_chunk=16, staging="cpasync"),
-                dict(variant="fused", tile=(16, 8), z_chunk=0, staging="cpasync"),
-                dict(variant="fused", tile=(16, 8), z_chunk=8, staging="tma")):
+                dict(variant="fused", tile=(16, 8), z_chunk=16, staging="cpasync"),
+                dict(variant="fused", tile=(16, 16), z_chunk=0, staging="cpasync"),
+                dict(variant="fused", tile=(16, 16), z_chunk=8, staging="tma")):
         with pytest.raises(rhd.RhdError) as ei:
             g.set_launch_config(cfg)
         assert ei.value.status == rhd.ERR_ARG
