@@ -64,7 +64,7 @@ void ensemble_tile_shape(int precision, int* tx, int* ty)
 {
     // the tiles ensemble_kernel is instantiated with (launch_ensemble_fp64, launch_ensemble_split)
     *tx = precision == 0 ? 16 : 32;
-    *ty = 8;
+    *ty = precision == 0 ? 16 : 8;
 }
 
 bool tile_supported(int precision, int nact, int tx, int ty)
@@ -88,10 +88,10 @@ cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s)
 
 cudaError_t launch_ensemble_fp64(const EnsembleParams& p, int n_ctas, cudaStream_t s)
 {
-    return launch_ens_kernel<double, 16, 8, false>(p, n_ctas, s);
+    return launch_ens_kernel<double, 16, 16, false>(p, n_ctas, s);
 }
 
-int ensemble_ctas_per_sm_fp64() { return ens_occupancy<double, 16, 8, false>(); }
+int ensemble_ctas_per_sm_fp64() { return ens_occupancy<double, 16, 16, false>(); }
 
 // The stiff exchange integrated once per gas step (Section 3.1 step 2, the paper's placement of S_i): in
 // every cell, E floored at E_floor, then the FULL quartic theta scheme of the subcycles (exchange_fp64,

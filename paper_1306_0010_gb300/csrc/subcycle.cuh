@@ -1491,7 +1491,8 @@ __global__ void __launch_bounds__(Geo<TX, TY, DIM>::NT,
 // Persistent ensemble kernel: CTAs pull (grid, tile) items from a global counter until the queue is
 // empty; the item-to-grid map is a prefix sum over the grids' tile counts (binary search).
 template <typename R, int TX, int TY, bool SPLIT>
-__global__ void __launch_bounds__(TX* TY, (TX * TY > 256) ? 1 : 2) ensemble_kernel(const __grid_constant__ EnsembleParams P)
+__global__ void __launch_bounds__(TX* TY, (TX * TY > 256 || (sizeof(R) == 8 && TX * TY >= 256)) ? 1 : 2)
+    ensemble_kernel(const __grid_constant__ EnsembleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
