@@ -46,14 +46,11 @@ void tile_shape(int precision, int nact, int* tx, int* ty)
     if (nact == 1) {
         *tx = 122;  // 128 threads: the tile and its 3-cell halo on each side
         *ty = 1;
-    } else if (precision == 0 && nact == 3) {
+    } else if (precision == 0) {
         // one CTA of 256 threads per SM (255 registers each): against 16x8 tiles (two CTAs of 128) it
         // recomputes the predictor on 1.89 instead of 2.41 times the tile's cells, which the FP64 pipe pays
         *tx = 16;
         *ty = 16;
-    } else if (precision == 0) {
-        *tx = 16;
-        *ty = 8;
     } else {
         *tx = 32;
         *ty = 8;
@@ -81,7 +78,7 @@ cudaError_t launch_subcycle_fp64(const StepParams& p, cudaStream_t s)
 {
     switch (p.g.nact) {
     case 1: return launch_tile_kernel<double, 122, 1, 1, false>(p, s);
-    case 2: return launch_tile_kernel<double, 16, 8, 2, false>(p, s);
+    case 2: return launch_tile_kernel<double, 16, 16, 2, false>(p, s);
     default: return launch_tile_kernel<double, 16, 16, 3, false>(p, s);
     }
 }
