@@ -313,8 +313,10 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_pred_flux_kernel(GasParams p,
     }
 }
 
+// split grids (R = float): memory-bound, so more resident warps (6 and 5 CTAs of 256 per SM) keep more loads
+// in flight than the few registers they cost; FP64 grids: bound by the FP64 pipe
 template <typename R>
-__global__ void __launch_bounds__(GAS_THREADS) gas_pred_update_kernel(GasParams p, GasArrays a)
+__global__ void __launch_bounds__(GAS_THREADS, sizeof(R) == 4 ? 6 : 1) gas_pred_update_kernel(GasParams p, GasArrays a)
 {
     const long long ne = gas_count(p.m);
     const double hdt = 0.5 * p.dt;
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(GAS_THREADS) gas_corr_flux_kernel(GasParams p,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(GAS_THREADS) gas_corr_update_kernel(GasParams p, GasArrays a)
+__global__ void __launch_bounds__(GAS_THREADS, sizeof(R) == 4 ? 5 : 1) gas_corr_update_kernel(GasParams p, GasArrays a)
 {
     const long long nc = gas_count(p.n);
     unsigned long long floors = 0, bad = 0;
